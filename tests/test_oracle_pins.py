@@ -1,0 +1,472 @@
+"""Pins for the CPU oracle: checks against what the mathematics fixes.
+
+Each test compares the oracle with something other than itself: a closed
+form derived separately from the defining density, a textbook value, an
+analytic distribution (chi-square on sampled histograms), an exact
+invariant, or a special case with a known answer.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import oracle as O
+from paper_1107_3355_gb300 import workloads as W
+from tests._stats import chi2_pvalue, sigma_over_dmax, t_test
+
+MC2 = 0.51099895
+RE = 2.8179403262e-13
+NA = 6.02214076e23
+ALPHA = 1 / 137.035999084
+
+
+def water_problem(**kw):
+    p = W.tiny_problem(n_histories=1000)
+    return p.with_(**kw) if kw else p
+
+
+# --------------------------------------------------------------------- RNG
+
+def test_philox_uniformity_and_avalanche():
+    key = np.array([12345, 0], np.uint32)
+    out = np.array([O.philox([i, 1, 0, 0], key) for i in range(20000)], np.uint64)
+    u = (out.astype(np.float64) + 0.5) / 2 ** 32
+    h, _ = np.histogram(u.ravel(), bins=64, range=(0, 1))
+    p, _ = chi2_pvalue(h, np.full(64, u.size / 64))
+    assert p > 1e-3
+    bits = np.unpackbits(out.astype(np.uint32).view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 0.005
+    # flipping one counter bit changes about half of the 128 output bits
+    flips = []
+    for i in range(2000):
+        a = O.philox([i, 7, 0, 3], key)
+        b = O.philox([i ^ (1 << (i % 32)), 7, 0, 3], key)
+        flips.append(np.unpackbits((a ^ b).view(np.uint8)).sum())
+    assert abs(np.mean(flips) - 64) < 1.0
+    # distinct keys give unrelated streams
+    a = np.array([O.philox([i, 1, 0, 0], [1, 0]) for i in range(2000)])
+    b = np.array([O.philox([i, 1, 0, 0], [2, 0]) for i in range(2000)])
+    assert abs(np.corrcoef(a[:, 0].astype(float), b[:, 0].astype(float))[0, 1]) < 0.1
+
+
+def test_child_ids_distinct():
+    ids = {O.child_id(1, k) for k in range(10000)}
+    assert len(ids) == 10000 and 1 not in ids
+    grand = {O.child_id(c, k) for c in list(ids)[:100] for k in range(100)}
+    assert len(grand) == 10000 and not (grand & ids)
+
+
+# --------------------------------------------------------------------- photons
+
+def kn_dsigma_domega(E, cost):
+    """Klein-Nishina angular cross section per electron (cm2/sr)."""
+    k = E / MC2
+    r = 1.0 / (1.0 + k * (1.0 - cost))
+    return 0.5 * RE ** 2 * r * r * (r + 1.0 / r - (1.0 - cost ** 2))
+
+
+@pytest.mark.parametrize("E", [0.01, 0.1, 1.0, 6.0, 20.0])
+def test_kn_total_matches_angular_integral(E):
+    """Closed-form sigma_KN equals 2*pi*int dsigma/dOmega dcos(theta)."""
+    p = water_problem()
+    tot, _ = integrate.quad(lambda c: 2 * math.pi * kn_dsigma_domega(E, c), -1, 1,
+                            epsabs=0, epsrel=1e-12)
+    got = O.evaluate(p, 0, O.OF_SIGMA_KN, E)[0]
+    assert got == pytest.approx(tot, rel=1e-9)
+
+
+def test_water_compton_mu_1mev():
+    p = water_problem()
+    assert O.evaluate(p, 0, O.OF_MU_C, 1.0)[0] == pytest.approx(0.07060, abs=2e-4)
+
+
+def test_photoelectric_scaling_and_calibration():
+    p = water_problem()
+    a, b = O.evaluate(p, 0, O.OF_MU_PE, [0.05, 0.1])
+    assert b == pytest.approx(a / 8.0, rel=1e-12)                 # Z^4/E^3
+    pe30 = O.evaluate(p, 0, O.OF_MU_PE, 0.03)[0]
+    c30 = O.evaluate(p, 0, O.OF_MU_C, 0.03)[0]
+    assert pe30 == pytest.approx(c30, rel=1e-6)                   # calibration reading
+
+
+def test_pair_threshold_and_high_energy_limit():
+    p = W.slab_photon_problem(n_histories=1000)
+    assert O.evaluate(p, 2, O.OF_MU_PAIR, 1.0)[0] == 0.0
+    assert O.evaluate(p, 2, O.OF_MU_PAIR, 2 * MC2)[0] == 0.0
+    # k -> infinity: complete-screening Bethe-Heitler per atom
+    # 4 alpha re^2 Z(Z+1) [7/9 ln(183 Z^-1/3) - 1/54]
+    for m, mat in enumerate(p.phantom.materials):
+        bh = sum(NA * w / A * 4 * ALPHA * RE ** 2 * Z * (Z + 1) *
+                 (7 / 9 * math.log(183 * Z ** (-1 / 3)) - 1 / 54) for Z, A, w in mat.elements)
+        E = 1e5
+        k = E / MC2
+        got = O.evaluate(p, m, O.OF_MU_PAIR, E)[0]
+        assert got == pytest.approx(bh * ((k - 2) / k) ** 3, rel=1e-10)
+        assert O.evaluate(p, m, O.OF_MU_PAIR, 3.0)[0] > 0
+
+
+@pytest.mark.parametrize("E", [0.1, 1.0, 6.0])
+def test_kn_sampler_chi2(E):
+    """Sampled eps = E'/E follows dsigma/deps (from the angular form)."""
+    n = 200_000
+    eps, cost = O.sample(O.OS_KN, E, 0.0, n, seed=11)
+    k = E / MC2
+    e0 = 1 / (1 + 2 * k)
+    assert eps.min() >= e0 - 1e-12 and eps.max() <= 1 + 1e-12
+    # kinematics: cos(theta) = 1 - (1/eps - 1)/k
+    np.testing.assert_allclose(cost, 1 - (1 / eps - 1) / k, atol=1e-12)
+
+    def dens(e):                 # dsigma/deps = 2 pi dsigma/dOmega |dcos/deps|
+        c = 1 - (1 / e - 1) / k
+        return 2 * math.pi * kn_dsigma_domega(E, c) / (k * e * e)
+
+    edges = np.linspace(e0, 1, 41)
+    expect = np.array([integrate.quad(dens, a, b)[0] for a, b in zip(edges[:-1], edges[1:])])
+    h, _ = np.histogram(eps, edges)
+    pv, _ = chi2_pvalue(h, expect * n / expect.sum())
+    assert pv > 1e-3
+
+
+def test_compton_electron_momentum():
+    """|E u - E' u'| equals the recoil momentum sqrt(T(T+2mc2))."""
+    E = 2.0
+    eps, cost = O.sample(O.OS_KN, E, 0.0, 5000, seed=3)
+    Ep = eps * E
+    T = E - Ep
+    pmag2 = E ** 2 + Ep ** 2 - 2 * E * Ep * cost
+    np.testing.assert_allclose(pmag2, T * (T + 2 * MC2), rtol=1e-10)
+
+
+def test_rotation_convention():
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        u = rng.normal(size=3); u /= np.linalg.norm(u)
+        c = rng.uniform(-1, 1); ph = rng.uniform(0, 2 * math.pi)
+        v = O.rotate(u, c, ph)
+        assert np.linalg.norm(v) == pytest.approx(1, abs=1e-12)
+        assert v @ u == pytest.approx(c, abs=1e-12)
+    # phi measured from e1 = (ux uz, uy uz, -(1-uz^2))/s
+    u = np.array([0.6, 0.0, 0.8])
+    v = O.rotate(u, 0.0, 0.0)
+    np.testing.assert_allclose(v, [0.8, 0.0, -0.6], atol=1e-12)
+    v = O.rotate(u, 0.0, math.pi / 2)
+    np.testing.assert_allclose(v, [0.0, 1.0, 0.0], atol=1e-12)
+    np.testing.assert_allclose(O.rotate([0, 0, 1], 0.0, 0.0), [1, 0, 0], atol=1e-12)
+
+
+def _depth_survival(prob, n, layers, E):
+    """Compare P(first real interaction deeper than x) with exp(-int mu)."""
+    z, t = O.first_interaction(prob, n)
+    zmax = prob.phantom.extent[2]
+    checks = 0
+    for x in np.linspace(0.5, zmax - 0.5, 12):
+        tau = 0.0
+        lo = 0.0
+        for up, mu in layers:
+            seg = max(0.0, min(x, up) - lo)
+            tau += mu * seg
+            lo = up
+            if up >= x:
+                break
+        pexp = math.exp(-tau)
+        surv = np.mean((z > x) | (t < 0))
+        sd = math.sqrt(pexp * (1 - pexp) / n)
+        assert abs(surv - pexp) <= 3.5 * sd + 1e-12, (x, surv, pexp, sd)
+        checks += 1
+    return checks
+
+
+def test_uncollided_fluence_water():
+    E = 1.0
+    p = W.tiny_problem(n_histories=1)
+    mu = (O.lookup(p, 0, O.OT_MU_C, E)[0] + O.lookup(p, 0, O.OT_MU_PE, E)[0] +
+          O.lookup(p, 0, O.OT_MU_PAIR, E)[0]) * 1.0
+    assert _depth_survival(p, 40000, [(1e9, mu)], E) == 12
+
+
+def test_uncollided_fluence_slab_woodcock():
+    """Heterogeneous slab: most flights in water/lung are virtual; the
+    interaction depths must still follow exp(-sum mu_i x_i)."""
+    E = 2.0
+    prob = W.slab_photon_problem(n_histories=1, shape=(16, 16, 128))
+    prob = prob.with_(source=W.pencil_source(prob.phantom, E))
+    mus = []
+    for m, rho in [(0, 1.0), (1, 0.26), (2, 1.85)]:
+        mus.append(rho * sum(O.lookup(prob, m, w, E)[0]
+                             for w in (O.OT_MU_C, O.OT_MU_PE, O.OT_MU_PAIR)))
+    layers = [(3.0, mus[0]), (10.0, mus[1]), (12.0, mus[2]), (1e9, mus[0])]
+    assert _depth_survival(prob, 40000, layers, E) == 12
+
+
+def test_first_interaction_type_fractions():
+    E = 0.04                      # photoelectric is a large share here
+    p = W.tiny_problem(n_histories=1)
+    p = p.with_(source=W.pencil_source(p.phantom, E), e_min=0.005, eabs_photon=0.01)
+    z, t = O.first_interaction(p, 30000)
+    muc = O.lookup(p, 0, O.OT_MU_C, E)[0]
+    mupe = O.lookup(p, 0, O.OT_MU_PE, E)[0]
+    f = mupe / (muc + mupe)
+    got = np.mean(t[t >= 0] == 1)
+    n = np.sum(t >= 0)
+    assert abs(got - f) < 4 * math.sqrt(f * (1 - f) / n)
+
+
+def test_compton_only_first_collision_exponential():
+    p = W.tiny_problem(n_histories=1).with_(flags=W.FLAG_COMPTON_ONLY)
+    E = 1.0
+    mu = O.lookup(p, 0, O.OT_MU_C, E)[0]
+    assert O.lookup(p, 0, O.OT_MU_PE, E)[0] == 0.0
+    z, t = O.first_interaction(p, 30000)
+    assert set(np.unique(t)) <= {-1, 0}
+    assert _depth_survival(p, 30000, [(1e9, mu)], E) == 12
+
+
+# --------------------------------------------------------------------- electrons
+
+def test_bethe_textbook_value():
+    p = water_problem()
+    assert O.evaluate(p, 0, O.OF_SCOL, 1.0)[0] == pytest.approx(1.85, rel=0.03)
+
+
+def _moller_closed(T, wcc, ne):
+    """Analytic hard-Moller cross section and energy loss (antiderivatives
+    of the Moller density in eps = W/T on [W_cc/T, 1/2])."""
+    tau = T / MC2
+    b2 = tau * (tau + 2) / (tau + 1) ** 2
+    c1 = (tau / (tau + 1)) ** 2
+    c2 = (2 * tau + 1) / (tau + 1) ** 2
+    K = ne * 2 * math.pi * RE ** 2 * MC2 / b2
+    ec = wcc / T
+    sig = K / T * (1 / ec - 1 / (1 - ec) + c1 * (0.5 - ec) - c2 * math.log((1 - ec) / ec))
+    loss = K * (math.log(1 / (2 * ec)) + 2 - math.log(2) - 1 / (1 - ec) - math.log(1 - ec)
+                + c1 * (1 / 8 - ec ** 2 / 2) - c2 * math.log(2 * (1 - ec)))
+    return sig, loss
+
+
+@pytest.mark.parametrize("T", [0.5, 1.0, 5.0, 20.0])
+def test_moller_quadrature_vs_closed_form(T):
+    p = water_problem()
+    ne = O.evaluate(p, 0, O.OF_NE, 0)[0]
+    sig, loss = _moller_closed(T, p.eabs_electron, ne)
+    assert O.evaluate(p, 0, O.OF_SIG_MOLLER, T)[0] == pytest.approx(sig, rel=1e-8)
+    assert O.evaluate(p, 0, O.OF_LOSS_MOLLER, T)[0] == pytest.approx(loss, rel=1e-8)
+    assert O.evaluate(p, 0, O.OF_SIG_MOLLER, 0.39)[0] == 0.0     # T <= 2 W_cc
+
+
+@pytest.mark.parametrize("T", [1.0, 10.0])
+def test_moller_sampler_chi2(T):
+    wcc = 0.2
+    n = 200_000
+    eps, _ = O.sample(O.OS_MOLLER, T, wcc, n, seed=5)
+    ec = wcc / T
+    assert eps.min() >= ec - 1e-12 and eps.max() <= 0.5 + 1e-12
+    tau = T / MC2
+    c1 = (tau / (tau + 1)) ** 2
+    c2 = (2 * tau + 1) / (tau + 1) ** 2
+
+    def dens(e):
+        return 1 / e ** 2 + 1 / (1 - e) ** 2 + c1 - c2 / (e * (1 - e))
+
+    edges = np.geomspace(ec, 0.5, 41)
+    expect = np.array([integrate.quad(dens, a, b)[0] for a, b in zip(edges[:-1], edges[1:])])
+    h, _ = np.histogram(eps, edges)
+    pv, _ = chi2_pvalue(h, expect * n / expect.sum())
+    assert pv > 1e-3
+
+
+def test_brems_sampler_one_over_k():
+    T, wcb = 5.0, 0.05
+    k, _ = O.sample(O.OS_BREMS, T, wcb, 100_000, seed=9)
+    assert k.min() >= wcb and k.max() <= T
+    edges = np.geomspace(wcb, T, 31)                # 1/k: equal counts per log bin
+    h, _ = np.histogram(k, edges)
+    pv, _ = chi2_pvalue(h, np.full(30, len(k) / 30))
+    assert pv > 1e-3
+
+
+@pytest.mark.parametrize("A", [1e-3, 0.05, 1.0])
+def test_screened_rutherford_sampler(A):
+    mu, _ = O.sample(O.OS_SR, A, 0.0, 200_000, seed=13)
+
+    def dens(m):
+        return 1.0 / (1 - m + 2 * A) ** 2
+
+    edges = 1 - np.geomspace(2, 1e-6, 41)[::-1]    # dense near mu = 1
+    edges = np.sort(np.concatenate([[-1.0], 1 - np.geomspace(1e-7, 2, 40)]))
+    expect = np.array([integrate.quad(dens, a, b)[0] for a, b in zip(edges[:-1], edges[1:])])
+    h, _ = np.histogram(mu, edges)
+    pv, _ = chi2_pvalue(h, expect * len(mu) / expect.sum())
+    assert pv > 1e-3
+
+
+@pytest.mark.parametrize("G1", [1e-5, 1e-3, 0.05, 0.5, 0.99])
+def test_screening_parameter_matches_first_moment(G1):
+    p = water_problem()
+    A = O.evaluate(p, 0, O.OF_SOLVE_A, G1)[0]
+    num, _ = integrate.quad(lambda m: (1 - m) / (1 - m + 2 * A) ** 2, -1, 1,
+                            points=[1 - 10 * A, 1 - A], epsrel=1e-11, limit=200)
+    den, _ = integrate.quad(lambda m: 1 / (1 - m + 2 * A) ** 2, -1, 1,
+                            points=[1 - 10 * A, 1 - A], epsrel=1e-11, limit=200)
+    assert num / den == pytest.approx(G1, rel=1e-7)
+
+
+def test_range_table_vs_quadrature():
+    """Tabulated CSDA range = int_{E_abs}^{E} dT/S_r by scipy quadrature."""
+    p = W.slab_photon_problem(n_histories=1, shape=(4, 4, 4)).with_(e_max=21.0, n_energy=512)
+    tb = O.tables(p)
+    for m in range(len(p.phantom.materials)):
+        for E in [0.3, 1.0, 4.0, 20.0]:
+            i = np.argmin(np.abs(tb["E"] - E))
+            Ei = tb["E"][i]
+            ref, _ = integrate.quad(
+                lambda t: 1.0 / O.lib().orc_eval(O._Prepared(p).c, m, O.OF_SREST, t),
+                p.eabs_electron, Ei, epsrel=1e-10, limit=200)
+            assert tb["range"][m, i] == pytest.approx(ref, rel=1e-7)
+        # inverse of the interpolated range is exact on its own interpolant
+        T = np.geomspace(0.25, 19.0, 50)
+        r = O.lookup(p, m, O.OT_RANGE, T)
+        np.testing.assert_allclose(O.lookup(p, m, O.OT_RANGE_INV, r), T, rtol=1e-10)
+
+
+def test_interpolation_error_small():
+    """Linear interpolation in ln E between 512 grid points stays within
+    1e-4 of the exact functions at mid-interval points."""
+    p = W.slab_photon_problem(n_histories=1, shape=(4, 4, 4))
+    tb = O.tables(p)
+    mid = np.sqrt(tb["E"][1:] * tb["E"][:-1])[::17]
+    mid = mid[(mid > 0.02) & (mid < 6.0)]
+    for m in range(3):
+        np.testing.assert_allclose(O.lookup(p, m, O.OT_MU_C, mid),
+                                   O.evaluate(p, m, O.OF_MU_C, mid), rtol=1e-4)
+        sel = mid > 0.45
+        np.testing.assert_allclose(O.lookup(p, m, O.OT_SIG_M, mid[sel]),
+                                   O.evaluate(p, m, O.OF_SIG_MOLLER, mid[sel]), rtol=2e-3)
+
+
+def test_majorant_bounds_every_material():
+    p = W.slab_photon_problem(n_histories=1, shape=(4, 4, 128))
+    E = np.geomspace(0.006, 6.4, 997)
+    mm = O.lookup(p, 0, O.OT_MUMAX, E)
+    for m, rho in [(0, 1.0), (1, 0.26), (2, 1.85)]:
+        mu = sum(O.lookup(p, m, w, E) for w in (O.OT_MU_C, O.OT_MU_PE, O.OT_MU_PAIR)) * rho
+        assert np.all(mm >= mu)
+
+
+@pytest.mark.parametrize("T0", [1.0, 5.0])
+def test_csda_track_length(T0):
+    """With hard events off, an electron's mass path from T0 to E_abs equals
+    the CSDA range int dT/S_r (independent quadrature), within 0.5%."""
+    ph = W.homogeneous_phantom((40, 40, 40), (0.5, 0.5, 0.5), W.WATER, 1.0)
+    src = W.Source(W.ELECTRON, W.mono_spectrum(T0), "pencil", (10.0, 10.0, 10.0), (0.0, 0.0, 1.0))
+    p = W.Problem(ph, src, 200, 2, eabs_photon=0.05, eabs_electron=0.2, e_min=0.005,
+                  e_max=T0 * 1.05, flags=W.FLAG_NO_HARD)
+    dose, sigma, led, hrec, hrecd = O.run(p, per_history=True)
+    prep = O._Prepared(p)
+    ref, _ = integrate.quad(lambda t: 1.0 / O.lib().orc_eval(prep.c, 0, O.OF_SREST, t),
+                            p.eabs_electron, T0, epsrel=1e-10, limit=200)
+    path = hrecd[:, O.HD_EL_MASSPATH]
+    assert np.mean(path) == pytest.approx(ref, rel=5e-3)
+    assert led["escaped"] == 0.0
+    assert led["deposited"] == pytest.approx(led["source_energy"], rel=1e-12)
+
+
+# --------------------------------------------------------------------- whole runs
+
+def _check_ledger(led, n_hist, tol=1e-9):
+    bal = led["deposited"] + led["escaped"] + led["discarded"]
+    assert bal == pytest.approx(led["source_energy"], rel=tol)
+    assert led["n_primary"] == n_hist
+    assert led["ph_created"] == led["ph_terminated"]
+    assert led["el_created"] == led["el_terminated"]
+
+
+def test_energy_balance_tiny():
+    p = W.tiny_problem(n_histories=5000, n_batches=10)
+    _, _, led = O.run(p)
+    _check_ledger(led, 5000)
+    assert led["compton"] > 0 and led["el_steps"] > 0
+
+
+def test_energy_balance_slab_photon_and_electron():
+    p = W.slab_photon_problem(n_histories=2000, n_batches=10, shape=(32, 32, 128))
+    _, _, led = O.run(p)
+    _check_ledger(led, 2000)
+    assert led["pair"] > 0 and led["annihilations"] > 0
+    p = W.slab_electron_problem(n_histories=300, n_batches=10, shape=(32, 32, 128))
+    _, _, led = O.run(p)
+    _check_ledger(led, 300)
+    assert led["brems"] > 0 and led["moller"] > 0
+
+
+def test_annihilation_off_discards_rest_mass():
+    p = W.slab_photon_problem(n_histories=3000, n_batches=10, shape=(16, 16, 128))
+    src = p.source
+    src = W.Source(src.particle, W.mono_spectrum(6.0), src.kind, src.origin, src.direction,
+                   src.center, src.axis_u, src.axis_v, src.half_u, src.half_v,
+                   annihilation=False)
+    _, _, led = O.run(p.with_(source=src))
+    _check_ledger(led, 3000)
+    assert led["annihilations"] == 0
+    assert led["pair"] > 0
+    assert led["discarded"] == pytest.approx(2 * MC2 * led["pair"], rel=1e-12)
+
+
+def test_vacuum_like_phantom_gives_no_dose():
+    ph = W.homogeneous_phantom((8, 8, 8), (1.0, 1.0, 1.0), W.WATER, 1e-6)
+    p = W.Problem(ph, W.pencil_source(ph, 6.0), 10000, 10, e_min=0.005, e_max=6.5)
+    dose, _, led = O.run(p)
+    assert led["deposited"] == 0.0 and np.all(dose == 0)
+    assert led["escaped"] == pytest.approx(6.0 * 10000, rel=1e-12)
+
+
+def test_subcutoff_electron_deposits_in_first_voxel():
+    ph = W.homogeneous_phantom((8, 8, 8), (0.5, 0.5, 0.5), W.WATER, 1.0)
+    src = W.Source(W.ELECTRON, W.mono_spectrum(0.15), "pencil", (2.1, 2.3, 0.0), (0, 0, 1))
+    p = W.Problem(ph, src, 100, 2, eabs_electron=0.2, e_min=0.005, e_max=1.0)
+    dose, _, led = O.run(p)
+    edep = dose * ph.rho * 0.125
+    v = 4 + 8 * (4 + 8 * 0)
+    assert edep[v] == pytest.approx(0.15, rel=1e-12)
+    assert np.count_nonzero(edep) == 1
+
+
+def test_spectrum_allotment():
+    p = W.slab_photon_problem(n_histories=1)
+    w = p.source.spectrum.weights
+    for nb in [1, 7, 1000, 999_983]:
+        c = O.allot(p, nb).astype(np.int64)
+        assert c.sum() == nb
+        assert np.all(np.abs(c - nb * w) < 1.0)
+        assert np.all(c[w == 0] == 0)
+
+
+def test_batch_uncertainty_is_calibrated():
+    """Two independent oracle runs: |t| <= 2 should hold in ~95% of the
+    high-dose voxels if sigma is the right standard error; sigma scales as
+    N^-1/2."""
+    a = W.tiny_problem(n_histories=40000, seed=1)
+    b = W.tiny_problem(n_histories=40000, seed=2)
+    d1, s1, l1 = O.run(a)
+    d2, s2, l2 = O.run(b)
+    r = t_test(d1, s1, d2, s2, high_frac=0.1)
+    assert r["n_high"] > 50
+    assert 0.88 <= r["P_high"] <= 0.995
+    d4, s4, _ = O.run(W.tiny_problem(n_histories=160000, seed=3))
+    ratio = sigma_over_dmax(d4, s4) / sigma_over_dmax(d1, s1)
+    assert ratio == pytest.approx(0.5, rel=0.12)
+
+
+def test_pencil_dose_xy_swap_symmetry():
+    """The pencil enters at the voxel corner (16, 16) along +z, so the setup
+    is symmetric under swapping x and y (azimuthal isotropy of scattering)."""
+    p = W.tiny_problem(n_histories=60000, seed=4)
+    d, s, _ = O.run(p)
+    g = p.phantom.grid3(d)
+    gs = p.phantom.grid3(s)
+    off = ~np.eye(32, dtype=bool)[None, :, :].repeat(32, 0)
+    m = np.swapaxes(g, 1, 2)
+    ms = np.swapaxes(gs, 1, 2)
+    r = t_test(g[off], gs[off], m[off], ms[off], high_frac=0.05)
+    assert r["n_high"] > 30
+    assert r["P_high"] > 0.9
