@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 gDPM engine.
+
+Workload (default): the 128^3 water/lung/bone/water slab phantom at 0.25 cm,
+6 MV-like photon beam (Kramers thick-target spectrum, 24 equal intervals),
+10x10 cm field at SSD 100 cm, cutoffs 50 keV / 200 keV, 1e8 histories in
+100 batches, FP32 transport with FP64 tallies.  One step = one full dose
+calculation of that workload (all batches, statistics and sigma/Dmax).
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
+Under torchrun each rank runs the same workload with its own Philox key
+(independent histories, no data exchange): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1107_3355_gb300 import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    "slab128_6MV": lambda n, nb: W.slab_photon_problem(n_histories=n, n_batches=nb),
+    "slab128_e20MeV": lambda n, nb: W.slab_electron_problem(n_histories=n, n_batches=nb),
+    "water32_1MeV_pencil": lambda n, nb: W.tiny_problem(n_histories=n, n_batches=nb),
+}
+
+# Algorithmic ALU operations per unit of work (FP32 arithmetic, integer
+# arithmetic of the Philox rounds and index math, and special-function calls,
+# one each; counted from the algorithm's steps).  Units come from the
+# engine's own event counters.
+OPS_PER_DRAW = 72          # Philox4x32-10 (10 rounds x 6 ops) + 4 uniform conversions x 3
+OPS = {
+    "ph_flights": 32 + OPS_PER_DRAW + 10,     # Woodcock flight: lerps, log, move, voxel, test
+    "compton": 96 + int(1.4 * OPS_PER_DRAW),  # KN sampling (~1.4 trials), rotation, recoil
+    "el_steps": 143 + OPS_PER_DRAW + 12,      # CH step: limits, range inverse, MS angle, hinge
+    "crossings": 23 + 8,                      # DDA voxel crossing with its deposit
+    "moller": 120 + int(2.5 * OPS_PER_DRAW),  # candidate + Moller sampling + two rotations
+    "brems": 25 + OPS_PER_DRAW,               # candidate + 1/k sampling
+}
+LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gdpm", choices=["gdpm", "reference"])
+    ap.add_argument("--workload", default="slab128_6MV", choices=sorted(WORKLOADS))
+    ap.add_argument("--histories", type=float, default=1e8)
+    ap.add_argument("--batches", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.path = tempfile.mktemp(prefix="gdpm_clk_", suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_rate(prob_fn, seconds, first_n=2000):
+    """Time the CPU oracle (single thread) on a bounded sample of the workload."""
+    from oracle import oracle as O
+    O.build()
+    n = first_n
+    while True:
+        t0 = time.perf_counter()
+        O.run(prob_fn(n))
+        dt = time.perf_counter() - t0
+        if dt >= seconds or n >= 10_000_000:
+            return n, dt
+        n = int(max(n * 2, n * seconds / max(dt, 1e-3) * 1.1))
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    n_hist = int(args.histories)
+    make = WORKLOADS[args.workload]
+    config = {"workload": args.workload, "histories_per_step": n_hist, "batches": args.batches,
+              "phantom": "128x128x128 @0.25cm" if "slab" in args.workload else "32^3 @0.5cm",
+              "l2": "flushed between steps (256 MB write)",
+              "parallelism": "replicas" if world > 1 else "single GPU"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        sample = 0
+        vals = []
+        for _ in range(args.steps):
+            n, dt = oracle_rate(lambda k: make(k, 10), max(args.cpu_seconds / 2, 1.0))
+            vals.append(n / dt)
+            sample = n
+        v = statistics.median(vals)
+        line = {"impl": "reference", "metric": "histories/s", "value": v, "unit": "histories/s",
+                "n_gpus": 0, "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * sample / v,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": "histories/s", "cores": 1, "kind": "oracle",
+                                 "sample": "%d histories of the workload, 10 batches" % sample},
+                "e2e": {"value": v, "unit": "histories/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    from paper_1107_3355_gb300 import gdpm as G
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    prob = make(n_hist, args.batches).with_(request_id=rank)
+    eng = G.Engine(prob, device=local, params={G.GDPM_PARAM_PROFILE: 1})
+    V = prob.phantom.n_voxels
+    dose = torch.empty(V, dtype=torch.float64, device=dev)
+    sigma = torch.empty(V, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        eng.run(dose=dose, sigma=sigma)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    stream = torch.cuda.current_stream(dev)
+    total_ms = 0.0
+    agg = {}
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, st = eng.run(dose=dose, sigma=sigma)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        for key, v in st.items():
+            if isinstance(v, list):
+                agg[key] = [a + b for a, b in zip(agg.get(key, [0] * len(v)), v)]
+            elif isinstance(v, (int, float)):
+                agg[key] = agg.get(key, 0) + v
+        last = st
+    barrier()
+    clk = clocks.stop()
+    t_max = total_ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps * n_hist / (t_max / 1e3)
+
+    # end to end through the C ABI with host buffers: tables, phantom upload
+    # (pinned host), source, simulate into host outputs
+    import numpy as np
+    mat_h = torch.from_numpy(np.ascontiguousarray(prob.phantom.mat)).pin_memory()
+    rho_h = torch.from_numpy(np.ascontiguousarray(prob.phantom.rho)).pin_memory()
+    dose_h = torch.empty(V, dtype=torch.float64).pin_memory()
+    sig_h = torch.empty(V, dtype=torch.float64).pin_memory()
+    ctx = eng.ctx
+    e2e_s = 0.0
+    for k in range(args.e2e_steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        tb = G.gdpm_tables_build(ctx, prob.phantom.materials, prob.e_min, prob.e_max, prob.n_energy,
+                                 prob.eabs_photon, prob.eabs_electron, prob.ms_loss_fraction, 0)
+        ph = G.gdpm_phantom_create(ctx, prob.phantom.shape, prob.phantom.voxel, mat_h, rho_h)
+        G.gdpm_source_set(ctx, prob.source)
+        G.gdpm_simulate(ctx, ph, tb, n_hist, args.batches, dose_h, sig_h)
+        G.gdpm_phantom_destroy(ph)
+        G.gdpm_tables_destroy(tb)
+        e2e_s += time.perf_counter() - t0
+    e2e_value = world * args.e2e_steps * n_hist / e2e_s
+
+    # roofline of the dominant kernel kind, from its live event time
+    kinds = ["photon phase", "electron phase", "batch fold"]
+    kms = agg.get("kernel_ms", [0, 0, 0])
+    dom = max(range(3), key=lambda i: kms[i])
+    if dom == 0:
+        ops = agg["ph_flights"] * OPS["ph_flights"] + agg["compton"] * OPS["compton"]
+    else:
+        ops = (agg["el_steps"] * OPS["el_steps"] + agg["crossings"] * OPS["crossings"] +
+               agg["moller"] * OPS["moller"] + agg["brems"] * OPS["brems"])
+    launches_dom = max(1, agg.get("kernel_launches", [1, 1, 1])[dom])
+    achieved = ops / (kms[dom] / 1e3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    peak = props.multi_processor_count * LANES_PER_SM * sm_mhz * 1e6 / 1e12
+
+    sig = last["sigma_over_dmax"]
+    n_to_1pct = n_hist * (sig / 0.01) ** 2 if sig > 0 else float("nan")
+    t_to_1pct = n_to_1pct / (value / world) if value > 0 else float("nan")
+
+    line = {"metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config,
+            "time_to_1pct_s": t_to_1pct,
+            "sigma_over_dmax": sig, "histories_for_1pct": n_to_1pct,
+            "e2e": {"value": e2e_value, "unit": "histories/s",
+                    "h2d_bytes_per_step": int(V * 5), "d2h_bytes_per_step": int(V * 16)},
+            "gpu_launches": int(agg.get("launches", 0)),
+            "roofline": {"bound": "alu", "kernel": kinds[dom], "achieved": achieved,
+                         "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "note": "ALU lane-operations/s vs SMs x 128 lanes x sampled SM clock"},
+            "kernel_ms_per_step": [k / args.steps for k in kms],
+            "events_per_history": {k: agg[k] / (args.steps * n_hist) for k in
+                                   ("ph_flights", "compton", "el_steps", "crossings", "moller",
+                                    "brems")},
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, dt = oracle_rate(lambda k: make(k, 10), args.cpu_seconds)
+        line["cpu_baseline"] = {"value": n / dt, "unit": "histories/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "%d histories of %s, 10 batches, single thread"
+                                          % (n, args.workload)}
+    if rank == 0:
+        print(json.dumps(line))
+    eng.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,264 @@
+/*
+ * gdpm.h -- C ABI of the GB300 (sm_103a) gDPM dose engine.
+ *
+ * The engine computes radiotherapy dose by coupled photon/electron Monte
+ * Carlo transport through a voxel phantom, following gDPM v2.0 (Jia et al.,
+ * arXiv:1107.3355): Woodcock-tracked photons with Compton, photoelectric
+ * and pair events; condensed-history electrons with CSDA energy loss,
+ * discrete (hard) Moller and bremsstrahlung events and hinge multiple
+ * scattering (Sec. 2.1); histories split into N_b batches whose spread
+ * gives the per-voxel uncertainty (Sec. 2.2.1); cross sections tabulated
+ * and linearly interpolated (Sec. 2.2.2); spectrum stratified into equal
+ * energy intervals (Sec. 2.3.2); fluence-map beamlets (Sec. 2.3.1).
+ *
+ * Conventions for every entry point:
+ *   - Return value: GDPM_OK (0) or a negative GDPM_E_* code.  No entry point
+ *     aborts the process; a device-side fault condition (queue overflow,
+ *     iteration cap) is reported as a status code, never by a trap.
+ *   - Handles are opaque.  The library owns the device memory it allocates
+ *     and frees it in the matching *_destroy call.
+ *   - Caller buffers are owned by the caller and are only read or written
+ *     during the call.  Unless stated otherwise an input array may live in
+ *     host or device memory (the library asks the CUDA runtime which).
+ *   - A context binds one CUDA device and one stream.  Calls on a context
+ *     are not thread-safe, except gdpm_request_submit/gdpm_request_poll.
+ *   - Units: MeV, cm, g/cm3.  Voxel (ix,iy,iz) has flat index
+ *     ix + nx*(iy + ny*iz); the phantom spans [0,nx*dx]x[0,ny*dy]x[0,nz*dz].
+ */
+#ifndef GDPM_H
+#define GDPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define GDPM_OK 0
+#define GDPM_E_ARG (-1)            /* invalid argument or size */
+#define GDPM_E_NOMEM (-2)          /* device allocation failed or refused */
+#define GDPM_E_QUEUE_OVERFLOW (-3) /* a secondary-particle queue overflowed */
+#define GDPM_E_TIMEOUT (-4)        /* a phase or iteration cap was reached */
+#define GDPM_E_CUDA (-5)           /* a CUDA runtime call failed */
+#define GDPM_E_STATE (-6)          /* call not valid in the current state */
+#define GDPM_E_BUSY (-7)           /* request not admitted (memory or slots) */
+
+typedef struct gdpm_ctx gdpm_ctx;
+typedef struct gdpm_phantom gdpm_phantom;
+typedef struct gdpm_tables gdpm_tables;
+
+#define GDPM_MAX_ELEMENTS 16
+#define GDPM_MAX_MATERIALS 8
+#define GDPM_MAX_BINS 256
+
+/* Material by composition.  Cross sections are built per unit density and
+ * scaled by each voxel's density (Sec. 2.1 materials "by mass"). */
+typedef struct {
+    int n_elements;
+    int Z[GDPM_MAX_ELEMENTS];
+    double A[GDPM_MAX_ELEMENTS];               /* g/mol */
+    double mass_fraction[GDPM_MAX_ELEMENTS];   /* need not sum to 1; normalised */
+    double mean_excitation_MeV;                /* Bethe I value */
+} gdpm_material_desc;
+
+enum { GDPM_PHOTON = 0, GDPM_ELECTRON = 1 };
+enum { GDPM_GEO_PENCIL = 0, GDPM_GEO_POINT_FIELD = 1, GDPM_GEO_BEAMLETS = 2 };
+
+/* Table/transport flags (gdpm_tables_build). */
+#define GDPM_FLAG_COMPTON_ONLY 2   /* zero photoelectric and pair cross sections */
+#define GDPM_FLAG_NO_HARD 4        /* no hard Moller/bremsstrahlung events */
+
+/* Source description (Sec. 2.3): particle, energy spectrum, geometry.
+ *   GDPM_GEO_PENCIL: all primaries start at `origin` along `direction`.
+ *   GDPM_GEO_POINT_FIELD: point source at `origin`; each primary aims at a
+ *     point uniform in the rectangle centre `center`, unit axes `axis_u`,
+ *     `axis_v`, half widths `half_u`, `half_v`.
+ *   GDPM_GEO_BEAMLETS: fluence map (Sec. 2.3.1); `beamlets` holds
+ *     n_beamlets rows of 17 doubles: source(3) centre(3) axis_u(3) axis_v(3)
+ *     u0 u1 v0 v1 (beamlet rectangle in the axis frame, cm) weight f_I.
+ * Energy: n_bins intervals with edges bin_edges[0..n_bins] and relative
+ * weights bin_weights[0..n_bins-1]; a monoenergetic source is one interval
+ * with equal edges.  Histories of each batch are allotted to intervals by
+ * weight (floor plus largest remainder) and their energies are uniform
+ * within the interval (Sec. 2.3.2).  Host arrays; copied by the call. */
+typedef struct {
+    int particle;
+    int geometry;
+    double origin[3], direction[3];
+    double center[3], axis_u[3], axis_v[3];
+    double half_u, half_v;
+    int n_bins;
+    const double *bin_edges;
+    const double *bin_weights;
+    int n_beamlets;
+    const double *beamlets;
+    int annihilation;              /* 1: positrons end in two 0.511 MeV photons (Sec. 2.1) */
+} gdpm_source_desc;
+
+/* Run statistics: energy ledger (FP64, MeV) and exact integer counts. */
+typedef struct {
+    double source_energy, deposited, escaped, discarded;
+    int64_t n_primary;
+    int64_t ph_created, ph_terminated, ph_flights, ph_real, compton, photoelectric, pair;
+    int64_t el_created, el_terminated, el_steps, moller, brems, annihilations;
+    int64_t local_deposits;
+    int64_t pushes[2], pops[2];    /* queue traffic: [0] photons, [1] electrons */
+    int64_t phases, launches;
+    double dmax, sigma_over_dmax;  /* Sec. 3.1 precision metric over D > 0.5 Dmax */
+    double transport_ms;           /* device time of the transport + fold loop */
+    int64_t crossings;             /* voxel boundaries crossed by electrons */
+    /* with GDPM_PARAM_PROFILE: summed device time and launch count per kernel
+     * kind: [0] photon phase, [1] electron phase, [2] batch fold */
+    double kernel_ms[3];
+    int64_t kernel_launches[3];
+} gdpm_stats;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  `seed` keys the
+ * Philox4x32-10 generator: key = (seed lo 32 bits, seed hi 32 bits ^
+ * request id).  Errors: GDPM_E_ARG (bad device), GDPM_E_CUDA. */
+int gdpm_context_create(gdpm_ctx **out, int device, void *cuda_stream, uint64_t seed);
+int gdpm_context_destroy(gdpm_ctx *ctx);
+
+/* Tuning and run parameters (see GDPM_PARAM_*).  GDPM_E_ARG if unknown or
+ * out of range. */
+int gdpm_set_param(gdpm_ctx *ctx, int param, double value);
+enum {
+    GDPM_PARAM_QUEUE_CAPACITY = 1,   /* particles per queue buffer (0 = automatic) */
+    GDPM_PARAM_BLOCK_THREADS = 2,    /* 64..1024, multiple of 32 (default 256) */
+    GDPM_PARAM_BLOCKS_PER_SM = 3,    /* persistent CTAs per SM (0 = occupancy) */
+    GDPM_PARAM_TALLY_MODE = 4,       /* 0: FP64 atomics; 1: FP32 compensated hi/lo pair */
+    GDPM_PARAM_SOURCE_CHUNK = 5,     /* max primaries per transport phase (0 = auto) */
+    GDPM_PARAM_MAX_PHASES = 6,       /* phase cap per batch -> GDPM_E_TIMEOUT */
+    GDPM_PARAM_REQUEST_ID = 7,       /* xored into the Philox key high word */
+    GDPM_PARAM_SPECULATIVE = 8,      /* phase pairs issued per host check (>=1) */
+    GDPM_PARAM_WARP_AGGREGATE = 9,   /* 1: merge same-voxel deposits within a warp */
+    GDPM_PARAM_PROFILE = 10          /* 1: time every launch with CUDA events (stats kernel_ms) */
+};
+
+/* ------------------------------------------------------------------ inputs */
+
+/* Upload a voxel phantom (Sec. 2.2.1 initialisation): `material` is nx*ny*nz
+ * uint8 material indices into the table set, `density` nx*ny*nz float
+ * densities in g/cm3 (> 0), both x fastest.  Host or device arrays; copied.
+ * Errors: GDPM_E_ARG (non-positive sizes, nx|ny|nz > 1024), GDPM_E_NOMEM. */
+int gdpm_phantom_create(gdpm_ctx *ctx, int nx, int ny, int nz, float dx, float dy, float dz,
+                        const uint8_t *material, const float *density, gdpm_phantom **out);
+int gdpm_phantom_destroy(gdpm_phantom *ph);
+
+/* Build the interpolation tables (Sec. 2.2.2) for n_mats materials on a
+ * log-uniform energy grid of n_energy points in [e_min, e_max], on the
+ * device in FP64 and stored as FP32: photon attenuation (Klein-Nishina,
+ * Z^4/E^3 photoelectric, Bethe-Heitler-shaped pair), electron restricted
+ * stopping power and CSDA range (Bethe + Moller + Kramers bremsstrahlung),
+ * hard-event cross sections, the range inverse, and the screened-Rutherford
+ * screening parameter.  The absorption energies are also the hard-event
+ * thresholds (W_cc = eabs_electron, W_cb = eabs_photon).  `ms_loss` is the
+ * CSDA energy fraction that limits one multiple-scattering step; `flags`
+ * takes GDPM_FLAG_COMPTON_ONLY / GDPM_FLAG_NO_HARD.
+ * Errors: GDPM_E_ARG (n_mats outside 1..8, n_energy < 16, bad energies). */
+int gdpm_tables_build(gdpm_ctx *ctx, const gdpm_material_desc *mats, int n_mats,
+                      double e_min, double e_max, int n_energy, double eabs_photon,
+                      double eabs_electron, double ms_loss, int flags, gdpm_tables **out);
+int gdpm_tables_destroy(gdpm_tables *t);
+
+/* Set the primary source (Sec. 2.3.1-2.3.3).  Copies everything it needs.
+ * Errors: GDPM_E_ARG (n_bins outside 1..256, weights not positive in sum,
+ * unknown geometry, empty beamlet list). */
+int gdpm_source_set(gdpm_ctx *ctx, const gdpm_source_desc *src);
+
+/* ------------------------------------------------------------------ compute */
+
+/* Simulate n_histories primaries in n_batches equal batches (Sec. 2.2.1)
+ * and return, per voxel, the mean dose and its standard error in MeV/g per
+ * source history (Gy per history = value * 1.602176634e-10).  dose_out and
+ * sigma_out hold nx*ny*nz doubles in host or device memory (either may be
+ * NULL).  stats_out (host, may be NULL) receives the ledger and counts.
+ * The call returns when the results are in place.
+ * Errors: GDPM_E_ARG (n_batches < 2, n_histories < n_batches or >= 2^32,
+ * material index beyond the table set, source energy outside the table
+ * grid), GDPM_E_QUEUE_OVERFLOW, GDPM_E_TIMEOUT, GDPM_E_NOMEM, GDPM_E_CUDA. */
+int gdpm_simulate(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
+                  int n_batches, double *dose_out, double *sigma_out, gdpm_stats *stats_out);
+
+/* Optional per-history records for the next gdpm_simulate on this context:
+ * rec (device, n*4 int32: real photon interactions, electron steps, hard
+ * electron events, banked secondaries) and recd (device, n*2 doubles:
+ * escaped energy, electron mass path in g/cm2), indexed by history id.
+ * Pass NULL to switch off.  Errors: GDPM_E_ARG. */
+int gdpm_set_history_records(gdpm_ctx *ctx, int32_t *rec, double *recd, uint64_t n);
+
+/* ------------------------------------------------------------------ serving */
+
+/* A dose request: the source to use, history count and batch count, run on
+ * a phantom/table pair that stays resident.  Results are kept on the device
+ * until polled. */
+typedef struct {
+    gdpm_phantom *phantom;
+    gdpm_tables *tables;
+    gdpm_source_desc source;
+    uint64_t n_histories;
+    int n_batches;
+} gdpm_request_desc;
+
+/* Queue a request; returns at once with its id.  Requests arriving while
+ * others run are admitted as slots and device memory free up and share the
+ * device with them (continuous batching); each request keeps its own Philox
+ * key (request id), so its result does not depend on what else runs.
+ * Thread-safe.  Errors: GDPM_E_ARG, GDPM_E_BUSY (queue full). */
+int gdpm_request_submit(gdpm_ctx *ctx, const gdpm_request_desc *req, uint64_t *req_id);
+
+/* Poll a request: *done = 1 when finished, then copies its dose/sigma
+ * (host or device arrays, nx*ny*nz doubles, may be NULL) and stats, and
+ * releases it.  *done = 0 while queued or running.  Thread-safe.
+ * Errors: GDPM_E_ARG (unknown id), or the request's own failure code. */
+int gdpm_request_poll(gdpm_ctx *ctx, uint64_t req_id, int *done, double *dose_out,
+                      double *sigma_out, gdpm_stats *stats_out);
+
+/* ------------------------------------------------------------------ checks */
+
+/* Human-readable text for a status code (static storage). */
+const char *gdpm_strerror(int code);
+
+/* Philox4x32-10 on the device for n counters (device arrays of 4*n uint32
+ * each, in and out), key (k0, k1).  For bitwise comparison with other
+ * implementations.  Errors: GDPM_E_ARG, GDPM_E_CUDA. */
+int gdpm_debug_philox(gdpm_ctx *ctx, const uint32_t *ctr, uint32_t k0, uint32_t k1,
+                      uint32_t *out, uint64_t n);
+
+/* Draw n samples from one device-side interaction sampler with the same
+ * random-number protocol as the transport (sample s uses history id s,
+ * particle id 1, key (seed lo, seed hi)):
+ *   kind 0 Klein-Nishina at energy a: out1 = E'/E, out2 = cos(theta)
+ *   kind 1 Moller at T = a, W_cc = b: out1 = W/T, out2 = cos(theta_delta)
+ *   kind 2 bremsstrahlung at T = a, W_cb = b: out1 = k
+ *   kind 3 screened Rutherford with screening a: out1 = mu
+ *   kind 4 isotropic: out1 = cos(theta), out2 = phi
+ * out1/out2: device arrays of n doubles (out2 may be NULL). */
+int gdpm_debug_sample(gdpm_ctx *ctx, int kind, double a, double b, uint64_t n,
+                      uint64_t seed, double *out1, double *out2);
+
+/* Copy one FP32 table to a device buffer of doubles:
+ *   0 mu_compton [m][i], 1 mu_compton + mu_photo, 2 total mu (cm2/g; the
+ *   cumulative forms the transport stores and samples from), 3 CSDA range
+ *   (g/cm2), 4 hard Moller, 5 hard bremsstrahlung (cm2/g), 6 energy grid (i),
+ *   7 per-material X0 (g/cm2), 8 per-material hard-event majorant (cm2/g).
+ * *count receives the number of values written (out may be NULL to query). */
+int gdpm_tables_export(gdpm_tables *t, int which, double *out, int64_t *count);
+
+/* Generate the primaries of histories [first, first+n) of batch 0 of an
+ * n_histories/n_batches run with the current source, as the transport does
+ * (Sec. 2.3), without transporting them.  out (device, n*8 doubles per
+ * primary: x y z u v w E entered) -- position is on the phantom surface
+ * after entry; entered = 0 if the primary misses the phantom. */
+int gdpm_debug_sources(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
+                       int n_batches, uint64_t first, uint64_t n, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GDPM_H */

@@ -175,6 +175,7 @@ typedef struct {
     orc_result *res;
     int *hrec; double *hrecd;      /* per-history records or NULL */
     uint64_t cur_hist;
+    uint64_t hrec_base;            /* history id of record row 0 */
     orc_particle *stack; size_t sp, scap;
     int flags;
 } orc_sim;
@@ -585,7 +586,7 @@ static void bank(orc_sim *S, orc_particle *parent, int type, double E, const dou
     parent->nchild++;
     c.ctr = 0; c.nchild = 0;
     if (type == PT_PHOTON) S->res->ph_created++; else S->res->el_created++;
-    if (S->hrec) S->hrec[S->cur_hist * HR_NI + HR_BANKED]++;
+    if (S->hrec) S->hrec[(S->cur_hist - S->hrec_base) * HR_NI + HR_BANKED]++;
     push(S, &c);
 }
 
@@ -663,7 +664,7 @@ static void photon_track(orc_sim *S, orc_particle *p)
         S->res->ph_flights++;
         if (u[1] * mumax >= mut * rho) continue;     /* virtual (delta) collision */
         S->res->ph_real++;
-        if (S->hrec) S->hrec[S->cur_hist * HR_NI + HR_PH_REAL]++;
+        if (S->hrec) S->hrec[(S->cur_hist - S->hrec_base) * HR_NI + HR_PH_REAL]++;
         double r = u[2] * mut;
         if (r < muc) {
             compton(S, p, &alive);
@@ -753,12 +754,12 @@ static void electron_absorb(orc_sim *S, orc_particle *p)
 static void electron_escape(orc_sim *S, orc_particle *p, double energy)
 {
     S->res->escaped += energy;
-    if (S->hrec) S->hrecd[S->cur_hist * HD_ND + HD_ESCAPED] += energy;
+    if (S->hrec) S->hrecd[(S->cur_hist - S->hrec_base) * HD_ND + HD_ESCAPED] += energy;
     if (p->type == PT_POSITRON) {
         if (S->P->flags & ORC_NO_ANNIHILATION) S->res->discarded += 2.0 * MC2;
         else {
             S->res->escaped += 2.0 * MC2;
-            if (S->hrec) S->hrecd[S->cur_hist * HD_ND + HD_ESCAPED] += 2.0 * MC2;
+            if (S->hrec) S->hrecd[(S->cur_hist - S->hrec_base) * HD_ND + HD_ESCAPED] += 2.0 * MC2;
         }
     }
     S->res->el_terminated++;
@@ -777,7 +778,7 @@ static void electron_track(orc_sim *S, orc_particle *p)
         double u[4];
         draw4(S, p, u);
         S->res->el_steps++;
-        if (S->hrec) S->hrec[S->cur_hist * HR_NI + HR_EL_STEPS]++;
+        if (S->hrec) S->hrec[(S->cur_hist - S->hrec_base) * HR_NI + HR_EL_STEPS]++;
         int m = P->mat[vidx(P, p->iv)];
         double Tk = p->E;
         /* step limits, all as mass thickness in the start material */
@@ -793,7 +794,7 @@ static void electron_track(orc_sim *S, orc_particle *p)
         if (xs < 0.0) xs = 0.0;
         double Tend = (ev == EV_CUT) ? eabs : range_inverse(T, m, R0 - xs);
         double dT = Tk - Tend;
-        if (S->hrec) S->hrecd[S->cur_hist * HD_ND + HD_EL_MASSPATH] += xs;
+        if (S->hrec) S->hrecd[(S->cur_hist - S->hrec_base) * HD_ND + HD_EL_MASSPATH] += xs;
         /* multiple scattering: screened Rutherford angle matched to the
          * Rossi-Greisen first moment G1 at the mid-step energy (READING) */
         double Tm = 0.5 * (Tk + Tend);
@@ -825,7 +826,7 @@ static void electron_track(orc_sim *S, orc_particle *p)
         double sb = (Tn > wcb) ? tab_at(T, T->sig_b, m, Tn) : 0.0;
         double sh = sm + sb;
         if (!(v[0] * T->sigmax[m] < sh)) continue;
-        if (S->hrec) S->hrec[S->cur_hist * HR_NI + HR_HARD]++;
+        if (S->hrec) S->hrec[(S->cur_hist - S->hrec_base) * HR_NI + HR_HARD]++;
         if (v[1] * sh < sm) {
             /* Moller: eps = W/T on [W_cc/T, 1/2], proposal 1/eps^2 + rejection */
             S->res->moller++;
@@ -940,7 +941,7 @@ static void run_history(orc_sim *S, orc_particle *prim)
     if (prim->type == PT_PHOTON) S->res->ph_created++; else S->res->el_created++;
     if (!enter_box(P, prim->x, prim->u)) {
         S->res->escaped += prim->E;
-        if (S->hrec) S->hrecd[S->cur_hist * HD_ND + HD_ESCAPED] += prim->E;
+        if (S->hrec) S->hrecd[(S->cur_hist - S->hrec_base) * HD_ND + HD_ESCAPED] += prim->E;
         if (prim->type == PT_PHOTON) S->res->ph_terminated++; else S->res->el_terminated++;
         return;
     }
@@ -952,7 +953,7 @@ static void run_history(orc_sim *S, orc_particle *prim)
         if (p.type == PT_PHOTON) {
             double esc0 = S->res->escaped;
             photon_track(S, &p);
-            if (S->hrec) S->hrecd[S->cur_hist * HD_ND + HD_ESCAPED] += S->res->escaped - esc0;
+            if (S->hrec) S->hrecd[(S->cur_hist - S->hrec_base) * HD_ND + HD_ESCAPED] += S->res->escaped - esc0;
         } else {
             electron_track(S, &p);
         }
@@ -1239,4 +1240,71 @@ void orc_rotate(const double u[3], double cost, double phi, double out[3])
     double v[3] = {u[0], u[1], u[2]};
     rotate(v, cost, phi);
     out[0] = v[0]; out[1] = v[1]; out[2] = v[2];
+}
+
+/* Primaries [first, first+n) of batch 0 of the problem (as the transport
+ * makes them), after entering the phantom: out rows x y z u v w E entered. */
+int orc_sources(const orc_problem *P, unsigned long long first, unsigned long long n, double *out)
+{
+    orc_sim S;
+    orc_result res;
+    sim_init(&S, P, &res);
+    uint64_t nb0 = P->n_hist / P->n_batches + (P->n_hist % P->n_batches ? 1 : 0);
+    uint64_t cnt[ORC_MAX_BINS];
+    allot(P, nb0, cnt);
+    for (uint64_t s = 0; s < n; s++) {
+        uint64_t local = first + s, acc = 0;
+        int j = 0;
+        while (j < P->n_bins - 1 && local >= acc + cnt[j]) { acc += cnt[j]; j++; }
+        orc_particle p;
+        make_primary(&S, (uint32_t)local, P->edges[j], P->edges[j + 1], &p);
+        int in = enter_box(P, p.x, p.u);
+        double *o = out + 8 * s;
+        for (int a = 0; a < 3; a++) { o[a] = p.x[a]; o[3 + a] = p.u[a]; }
+        o[6] = p.E; o[7] = in ? 1.0 : 0.0;
+    }
+    tables_free(&S.T);
+    return 0;
+}
+
+/* Per-history records of histories [first, first+n) of the full problem
+ * (same batch split and spectrum allotment as orc_run); dose discarded.
+ * rec: n*HR_NI ints, recd: n*HD_ND doubles, indexed from `first`. */
+int orc_history_records(const orc_problem *P, unsigned long long first, unsigned long long n,
+                        int *rec, double *recd)
+{
+    orc_sim S;
+    orc_result res;
+    sim_init(&S, P, &res);
+    size_t V = (size_t)P->nx * P->ny * P->nz;
+    S.edep = calloc(V, sizeof(double));
+    memset(rec, 0, sizeof(int) * HR_NI * n);
+    memset(recd, 0, sizeof(double) * HD_ND * n);
+    uint64_t cnt[ORC_MAX_BINS];
+    int NB = P->n_batches;
+    uint64_t bstart = 0;
+    for (int b = 0; b < NB; b++) {
+        uint64_t nb = P->n_hist / NB + ((uint64_t)b < P->n_hist % NB ? 1 : 0);
+        uint64_t lo = first > bstart ? first : bstart;
+        uint64_t hi = (first + n) < (bstart + nb) ? (first + n) : (bstart + nb);
+        if (lo < hi) {
+            allot(P, nb, cnt);
+            for (uint64_t h = lo; h < hi; h++) {
+                uint64_t local = h - bstart, acc = 0;
+                int j = 0;
+                while (j < P->n_bins - 1 && local >= acc + cnt[j]) { acc += cnt[j]; j++; }
+                S.hrec = rec;
+                S.hrecd = recd;
+                S.hrec_base = first;
+                S.cur_hist = h;
+                orc_particle prim;
+                make_primary(&S, (uint32_t)h, P->edges[j], P->edges[j + 1], &prim);
+                run_history(&S, &prim);
+            }
+        }
+        bstart += nb;
+    }
+    free(S.edep); free(S.stack);
+    tables_free(&S.T);
+    return 0;
 }

@@ -105,6 +105,9 @@ def lib():
                                             C.c_void_p]
         L.orc_allot.argtypes = [C.POINTER(OrcProblem), C.c_ulonglong, C.c_void_p]
         L.orc_rotate.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p]
+        L.orc_sources.argtypes = [C.POINTER(OrcProblem), C.c_ulonglong, C.c_ulonglong, C.c_void_p]
+        L.orc_history_records.argtypes = [C.POINTER(OrcProblem), C.c_ulonglong, C.c_ulonglong,
+                                          C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -247,3 +250,20 @@ def rotate(u, cost: float, phi: float) -> np.ndarray:
     o = np.zeros(3)
     lib().orc_rotate(_ptr(a), cost, phi, _ptr(o))
     return o
+
+
+def sources(prob, first: int, n: int) -> np.ndarray:
+    """Primaries [first, first+n) of batch 0 after entry: rows x y z u v w E entered."""
+    prep = _Prepared(prob)
+    out = np.zeros((n, 8))
+    lib().orc_sources(C.byref(prep.c), first, n, _ptr(out))
+    return out
+
+
+def history_records(prob, first: int, n: int):
+    """Per-history records of histories [first, first+n) of the full problem."""
+    prep = _Prepared(prob)
+    rec = np.zeros((n, HR_NI), np.int32)
+    recd = np.zeros((n, HD_ND), np.float64)
+    lib().orc_history_records(C.byref(prep.c), first, n, _ptr(rec), _ptr(recd))
+    return rec, recd

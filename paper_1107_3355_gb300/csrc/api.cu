@@ -1,0 +1,811 @@
+// C ABI of the engine and the host-side scheduler of one dose calculation.
+//
+// A calculation runs N_b batches (Sec. 2.2.1).  Within a batch the device
+// alternates photon and electron phases (Sec. 2.2.1 Step 3: one particle
+// type at a time) until no primaries are left and both queues are empty.
+// Queue bookkeeping lives entirely on the device: every phase k owns a pop
+// counter, and every queue fill owns its own count, all zeroed once per
+// batch, so phases chain without host round trips.  The host checks for an
+// empty batch only after the primaries are used up, once per
+// `speculative` phase pairs (phases launched on an empty input exit at once).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace gdpm {
+
+cudaError_t& last_cuda_error() {
+    static thread_local cudaError_t e = cudaSuccess;
+    return e;
+}
+
+int ensure(Buffer& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.p && b.bytes >= bytes) return GDPM_OK;
+    release(b);
+    void* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GDPM_E_NOMEM;
+    }
+    b.p = p;
+    b.bytes = bytes;
+    return GDPM_OK;
+}
+
+void release(Buffer& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// Histories of one batch allotted to the spectrum intervals by weight:
+// floor, then the remainder one by one to the largest fractional parts
+// (ties to the lower interval) (Sec. 2.3.2).  Writes n_bins+1 prefix counts.
+static void allot_prefix(const std::vector<double>& w, uint64_t nb, uint32_t* prefix) {
+    const int K = int(w.size());
+    double ws = 0;
+    for (double x : w) ws += x;
+    std::vector<uint64_t> c(K);
+    std::vector<double> frac(K);
+    uint64_t given = 0;
+    for (int j = 0; j < K; ++j) {
+        const double q = double(nb) * (w[j] / ws);
+        c[j] = uint64_t(std::floor(q));
+        frac[j] = q - std::floor(q);
+        given += c[j];
+    }
+    while (given < nb) {
+        int best = -1;
+        for (int j = 0; j < K; ++j)
+            if (w[j] > 0 && (best < 0 || frac[j] > frac[best])) best = j;
+        ++c[best];
+        frac[best] = -1.0;
+        ++given;
+    }
+    prefix[0] = 0;
+    for (int j = 0; j < K; ++j) prefix[j + 1] = prefix[j] + uint32_t(c[j]);
+}
+
+// Optional per-launch device timing (GDPM_PARAM_PROFILE): an event pair on
+// the context's stream around each launch, summed per kernel kind at the end.
+static size_t prof_begin(gdpm_ctx* ctx, int kind) {
+    if (!ctx->profile) return 0;
+    const size_t idx = ctx->prof_kind.size();
+    while (ctx->prof_events.size() < 2 * (idx + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        ctx->prof_events.push_back(e);
+    }
+    cudaEventRecord(ctx->prof_events[2 * idx], ctx->stream);
+    ctx->prof_kind.push_back(kind);
+    return idx;
+}
+static void prof_end(gdpm_ctx* ctx, size_t idx) {
+    if (ctx->profile && 2 * idx + 1 < ctx->prof_events.size())
+        cudaEventRecord(ctx->prof_events[2 * idx + 1], ctx->stream);
+}
+static void prof_collect(gdpm_ctx* ctx, gdpm_stats* st) {
+    for (size_t i = 0; i < ctx->prof_kind.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->prof_events[2 * i], ctx->prof_events[2 * i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        const int k = ctx->prof_kind[i];
+        if (st && k >= 0 && k < 3) {
+            st->kernel_ms[k] += ms;
+            st->kernel_launches[k] += 1;
+        }
+    }
+    ctx->prof_kind.clear();
+}
+
+static Queue make_queue(const Buffer& b, uint32_t cap) {
+    Queue q{};
+    uint32_t* base = static_cast<uint32_t*>(b.p);
+    float** fs[7] = {&q.x, &q.y, &q.z, &q.u, &q.v, &q.w, &q.E};
+    for (int k = 0; k < 7; ++k) *fs[k] = reinterpret_cast<float*>(base + size_t(k) * cap);
+    uint32_t** us[6] = {&q.vox, &q.hist, &q.pidlo, &q.pidhi, &q.ctr, &q.flags};
+    for (int k = 0; k < 6; ++k) *us[k] = base + size_t(7 + k) * cap;
+    q.capacity = cap;
+    return q;
+}
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int source_upload(gdpm_ctx* ctx, const gdpm_source_state& s, DevSource& d) {
+    const gdpm_source_desc& g = s.desc;
+    d.particle = g.particle;
+    d.geometry = g.geometry;
+    d.annihilation = g.annihilation ? 1 : 0;
+    d.n_bins = int(s.weights.size());
+    d.n_beamlets = g.geometry == GDPM_GEO_BEAMLETS ? int(s.beamlets.size() / 17) : 0;
+    for (int a = 0; a < 3; ++a) {
+        d.origin[a] = float(g.origin[a]);
+        d.center[a] = float(g.center[a]);
+        d.axis_u[a] = float(g.axis_u[a]);
+        d.axis_v[a] = float(g.axis_v[a]);
+    }
+    double dn = std::sqrt(g.direction[0] * g.direction[0] + g.direction[1] * g.direction[1] +
+                          g.direction[2] * g.direction[2]);
+    for (int a = 0; a < 3; ++a) d.direction[a] = float(g.direction[a] / dn);
+    d.half_u = float(g.half_u);
+    d.half_v = float(g.half_v);
+    std::vector<float> e(s.edges.begin(), s.edges.end());
+    int rc = ensure(ctx->ws.edges, e.size() * 4);
+    if (rc) return rc;
+    GDPM_CUDA_TRY(cudaMemcpyAsync(ctx->ws.edges.p, e.data(), e.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    d.edges = static_cast<const float*>(ctx->ws.edges.p);
+    d.beamlets = nullptr;
+    d.bl_cdf = nullptr;
+    if (d.n_beamlets > 0) {
+        const int nbl = d.n_beamlets;
+        std::vector<float> rows(size_t(nbl) * 16);
+        std::vector<double> cdf(nbl);
+        double tot = 0;
+        for (int b = 0; b < nbl; ++b) tot += s.beamlets[size_t(b) * 17 + 16];
+        double acc = 0;
+        for (int b = 0; b < nbl; ++b) {
+            for (int k = 0; k < 16; ++k) rows[size_t(b) * 16 + k] = float(s.beamlets[size_t(b) * 17 + k]);
+            acc += s.beamlets[size_t(b) * 17 + 16];
+            cdf[b] = acc / tot;
+        }
+        cdf[nbl - 1] = 1.0;
+        if ((rc = ensure(ctx->ws.beamlets, rows.size() * 4)) || (rc = ensure(ctx->ws.bl_cdf, cdf.size() * 8)))
+            return rc;
+        GDPM_CUDA_TRY(cudaMemcpyAsync(ctx->ws.beamlets.p, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(ctx->ws.bl_cdf.p, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+        d.beamlets = static_cast<const float*>(ctx->ws.beamlets.p);
+        d.bl_cdf = static_cast<const double*>(ctx->ws.bl_cdf.p);
+    }
+    return GDPM_OK;
+}
+
+static SimParams base_params(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint32_t request_id) {
+    SimParams P{};
+    P.nx = ph->nx; P.ny = ph->ny; P.nz = ph->nz;
+    P.dx = ph->dx; P.dy = ph->dy; P.dz = ph->dz;
+    P.inv_dx = 1.f / ph->dx; P.inv_dy = 1.f / ph->dy; P.inv_dz = 1.f / ph->dz;
+    P.Lx = float(double(ph->nx) * ph->dx);
+    P.Ly = float(double(ph->ny) * ph->dy);
+    P.Lz = float(double(ph->nz) * ph->dz);
+    P.mat = static_cast<const uint8_t*>(ph->mat.p);
+    P.rho = static_cast<const float*>(ph->rho.p);
+    P.maj = static_cast<const float*>(ph->maj.p);
+    P.T = tb->dev;
+    P.key0 = uint32_t(ctx->seed);
+    P.key1 = uint32_t(ctx->seed >> 32) ^ request_id;
+    P.tally_mode = ctx->tally_mode;
+    P.warp_aggregate = ctx->warp_aggregate;
+    P.max_iters = 1u << 22;   // per-warp iterations in one phase; far above real use
+    return P;
+}
+
+static int validate_run(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const gdpm_source_state& src,
+                        uint64_t n_hist, int n_batches) {
+    if (!ctx || !ph || !tb) return GDPM_E_ARG;
+    if (!src.set) return GDPM_E_STATE;
+    if (n_batches < 2 || n_hist < uint64_t(n_batches) || n_hist >= (1ull << 32)) return GDPM_E_ARG;
+    for (int m = tb->n_mat; m < 256; ++m)
+        if (ph->rhomax_host[m] > 0.f) return GDPM_E_ARG;
+    // energies that can be drawn: the intervals with positive weight
+    double emin = 1e300, emax = 0.0;
+    for (size_t j = 0; j < src.weights.size(); ++j) {
+        if (!(src.weights[j] > 0)) continue;
+        emin = std::min(emin, src.edges[j]);
+        emax = std::max(emax, src.edges[j + 1]);
+    }
+    if (emax > tb->e_max * (1 + 1e-12) || emin < tb->e_min * (1 - 1e-12)) return GDPM_E_ARG;
+    return GDPM_OK;
+}
+
+// Work buffers for a phantom of V voxels and queues of `cap` particles.
+static int prepare_workspace(gdpm_ctx* ctx, size_t V, uint32_t cap, int n_batches, int n_bins) {
+    Workspace& ws = ctx->ws;
+    int rc;
+    if ((rc = ensure(ws.s1, V * 8)) || (rc = ensure(ws.s2, V * 8))) return rc;
+    if (ctx->tally_mode == 0) {
+        if ((rc = ensure(ws.edep, V * 8))) return rc;
+    } else {
+        if ((rc = ensure(ws.hi, V * 4)) || (rc = ensure(ws.lo, V * 4))) return rc;
+    }
+    const size_t qb = size_t(cap) * kQueueWords * 4;
+    if ((rc = ensure(ws.qph, qb)) || (rc = ensure(ws.qel0, qb)) || (rc = ensure(ws.qel1, qb))) return rc;
+    ws.cap_ph = ws.cap_el = cap;
+    if ((rc = ensure(ws.ctl, size_t(ctx->max_phases + 4) * 16)) ||
+        (rc = ensure(ws.prefix, size_t(n_batches) * (n_bins + 1) * 4)) ||
+        (rc = ensure(ws.counters, C_NCOUNT * 8)) || (rc = ensure(ws.ledger, L_NLEDGER * 8)) ||
+        (rc = ensure(ws.status, 16)))
+        return rc;
+    if (!ws.pinned_host.p) {
+        void* h = nullptr;
+        GDPM_CUDA_TRY(cudaMallocHost(&h, 4096));
+        ws.pinned_host.p = h;
+        ws.pinned_host.bytes = 4096;
+    }
+    return GDPM_OK;
+}
+
+// One batch: alternate photon (even k) and electron (odd k) phases.
+//   photon phase k consumes fill P[k] (+ photon primaries), banks electrons into E[k+1];
+//   electron phase k consumes E[k] (+ electron primaries), banks photons into
+//   P[k+1] and electrons into E[k+2].
+// ctl row k: [0] pop counter of phase k, [1] count of P[k], [2] count of E[k].
+static int run_batch(gdpm_ctx* ctx, const SimParams& P, const gdpm_source_state& src, int b,
+                     uint64_t nb, uint64_t first, uint32_t chunk, int64_t& phases) {
+    Workspace& ws = ctx->ws;
+    uint32_t* ctl = static_cast<uint32_t*>(ws.ctl.p);
+    GDPM_CUDA_TRY(cudaMemsetAsync(ctl, 0, size_t(ctx->max_phases + 4) * 16, ctx->stream));
+    const Queue qph = make_queue(ws.qph, ws.cap_ph);
+    const Queue qe[2] = {make_queue(ws.qel0, ws.cap_el), make_queue(ws.qel1, ws.cap_el)};
+    const bool photon_src = src.desc.particle == GDPM_PHOTON;
+    const int n_bins = int(src.weights.size());
+    uint64_t left = nb, next = 0;
+    int k = photon_src ? 0 : 1;
+    int since = 0;
+    uint32_t* host = static_cast<uint32_t*>(ws.pinned_host.p);
+    for (;;) {
+        if (k + 3 >= ctx->max_phases) return GDPM_E_TIMEOUT;
+        const bool ph = (k % 2) == 0;
+        PhaseArgs A{};
+        A.batch_first_hist = uint32_t(first);
+        A.bin_prefix = static_cast<const uint32_t*>(ws.prefix.p) + size_t(b) * (n_bins + 1);
+        if (ph == photon_src && left > 0) {
+            A.n_src = uint32_t(std::min<uint64_t>(left, chunk));
+            A.src_first_local = uint32_t(next);
+            next += A.n_src;
+            left -= A.n_src;
+        }
+        A.head = ctl + size_t(k) * 4 + 0;
+        uint32_t hint = 0;
+        if (ph) {
+            A.in = qph;
+            A.in_count = k >= 1 ? ctl + size_t(k) * 4 + 1 : nullptr;
+            A.out_el = qe[((k + 1) / 2) % 2];
+            A.out_el_count = ctl + size_t(k + 1) * 4 + 2;
+            A.out_ph = qph;
+            A.out_ph_count = ctl + size_t(k + 2) * 4 + 1;
+        } else {
+            A.in = qe[(k / 2) % 2];
+            A.in_count = ctl + size_t(k) * 4 + 2;
+            A.out_ph = qph;
+            A.out_ph_count = ctl + size_t(k + 1) * 4 + 1;
+            A.out_el = qe[((k + 2) / 2) % 2];
+            A.out_el_count = ctl + size_t(k + 2) * 4 + 2;
+        }
+        if (!A.in_count) hint = A.n_src;
+        const size_t pi = prof_begin(ctx, ph ? 0 : 1);
+        int rc = launch_phase(ctx, ph ? GDPM_PHOTON : GDPM_ELECTRON, P, A, hint);
+        prof_end(ctx, pi);
+        if (rc) return rc;
+        ++phases;
+        ++k;
+        ++since;
+        if (!ph && left == 0 && since >= 2 * ctx->speculative) {
+            // pending after electron phase k-1: photons P[k], electrons E[k+1]
+            GDPM_CUDA_TRY(cudaMemcpyAsync(host, ctl + size_t(k) * 4 + 1, 4, cudaMemcpyDeviceToHost, ctx->stream));
+            GDPM_CUDA_TRY(cudaMemcpyAsync(host + 1, ctl + size_t(k + 1) * 4 + 2, 4, cudaMemcpyDeviceToHost, ctx->stream));
+            GDPM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+            if (host[0] == 0 && host[1] == 0) break;
+            since = 0;
+        }
+    }
+    return GDPM_OK;
+}
+
+static void fill_stats(const unsigned long long* c, const double* l, gdpm_stats* st) {
+    st->source_energy = l[L_SOURCE];
+    st->deposited = l[L_DEPOSITED];
+    st->escaped = l[L_ESCAPED];
+    st->discarded = l[L_DISCARDED];
+    st->n_primary = int64_t(c[C_PRIMARY]);
+    st->ph_created = int64_t(c[C_PH_CREATED]);
+    st->ph_terminated = int64_t(c[C_PH_TERMINATED]);
+    st->ph_flights = int64_t(c[C_PH_FLIGHTS]);
+    st->ph_real = int64_t(c[C_PH_REAL]);
+    st->compton = int64_t(c[C_COMPTON]);
+    st->photoelectric = int64_t(c[C_PHOTO]);
+    st->pair = int64_t(c[C_PAIR]);
+    st->el_created = int64_t(c[C_EL_CREATED]);
+    st->el_terminated = int64_t(c[C_EL_TERMINATED]);
+    st->el_steps = int64_t(c[C_EL_STEPS]);
+    st->moller = int64_t(c[C_MOLLER]);
+    st->brems = int64_t(c[C_BREMS]);
+    st->annihilations = int64_t(c[C_ANNIHIL]);
+    st->local_deposits = int64_t(c[C_LOCAL_DEP]);
+    st->pushes[0] = int64_t(c[C_PUSH_PH]);
+    st->pushes[1] = int64_t(c[C_PUSH_EL]);
+    st->pops[0] = int64_t(c[C_POP_PH]);
+    st->pops[1] = int64_t(c[C_POP_EL]);
+    unsigned long long bits;
+    std::memcpy(&bits, &l[L_DMAX], 8);
+    double dmax;
+    std::memcpy(&dmax, &bits, 8);
+    st->dmax = dmax;
+    st->sigma_over_dmax = (l[L_SIGCNT] > 0 && dmax > 0) ? l[L_SIGSUM] / l[L_SIGCNT] / dmax : 0.0;
+}
+
+int simulate_impl(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const gdpm_source_state& src,
+                  uint32_t request_id, uint64_t n_hist, int n_batches, double* dose_out,
+                  double* sigma_out, gdpm_stats* st) {
+    int rc = validate_run(ctx, ph, tb, src, n_hist, n_batches);
+    if (rc) return rc;
+    if ((rc = build_majorant(ctx, ph, tb))) return rc;
+    const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
+    const uint64_t nb_max = (n_hist + n_batches - 1) / n_batches;
+    uint32_t chunk = ctx->source_chunk ? ctx->source_chunk : (1u << 20);
+    chunk = uint32_t(std::min<uint64_t>(chunk, nb_max));
+    const uint32_t cap = ctx->queue_capacity ? ctx->queue_capacity : 8u * chunk + 65536u;
+    const int n_bins = int(src.weights.size());
+    if ((rc = prepare_workspace(ctx, V, cap, n_batches, n_bins))) return rc;
+    Workspace& ws = ctx->ws;
+    // spectrum allotment of every batch
+    std::vector<uint32_t> prefix(size_t(n_batches) * (n_bins + 1));
+    for (int b = 0; b < n_batches; ++b) {
+        const uint64_t nb = n_hist / n_batches + (uint64_t(b) < n_hist % n_batches ? 1 : 0);
+        allot_prefix(src.weights, nb, &prefix[size_t(b) * (n_bins + 1)]);
+    }
+    GDPM_CUDA_TRY(cudaMemcpyAsync(ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    SimParams P = base_params(ctx, ph, tb, request_id);
+    if ((rc = source_upload(ctx, src, P.S))) return rc;
+    P.edep = static_cast<double*>(ws.edep.p);
+    P.edep_hi = static_cast<float*>(ws.hi.p);
+    P.edep_lo = static_cast<float*>(ws.lo.p);
+    P.counters = static_cast<unsigned long long*>(ws.counters.p);
+    P.ledger = static_cast<double*>(ws.ledger.p);
+    P.status = static_cast<uint32_t*>(ws.status.p);
+    P.hrec = ctx->hrec;
+    P.hrecd = ctx->hrecd;
+    if (P.hrec && ctx->hrec_n < n_hist) return GDPM_E_ARG;
+    cudaStream_t s = ctx->stream;
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.s1.p, 0, V * 8, s));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.s2.p, 0, V * 8, s));
+    if (ctx->tally_mode == 0) {
+        GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep.p, 0, V * 8, s));
+    } else {
+        GDPM_CUDA_TRY(cudaMemsetAsync(ws.hi.p, 0, V * 4, s));
+        GDPM_CUDA_TRY(cudaMemsetAsync(ws.lo.p, 0, V * 4, s));
+    }
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.counters.p, 0, C_NCOUNT * 8, s));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.ledger.p, 0, L_NLEDGER * 8, s));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, 16, s));
+    if (P.hrec) {
+        GDPM_CUDA_TRY(cudaMemsetAsync(P.hrec, 0, n_hist * 16, s));
+        GDPM_CUDA_TRY(cudaMemsetAsync(P.hrecd, 0, n_hist * 16, s));
+    }
+    ctx->prof_kind.clear();
+    GDPM_CUDA_TRY(cudaEventRecord(ctx->ev0, s));
+    int64_t phases = 0;
+    uint64_t first = 0;
+    int run_rc = GDPM_OK;
+    for (int b = 0; b < n_batches && run_rc == GDPM_OK; ++b) {
+        const uint64_t nb = n_hist / n_batches + (uint64_t(b) < n_hist % n_batches ? 1 : 0);
+        run_rc = run_batch(ctx, P, src, b, nb, first, chunk, phases);
+        if (run_rc == GDPM_OK) {
+            const size_t pi = prof_begin(ctx, 2);
+            run_rc = launch_fold(ctx, P, V, uint32_t(nb));
+            prof_end(ctx, pi);
+        }
+        first += nb;
+    }
+    GDPM_CUDA_TRY(cudaEventRecord(ctx->ev1, s));
+    if (run_rc != GDPM_OK) {
+        cudaStreamSynchronize(s);
+        ctx->prof_kind.clear();
+        return run_rc;
+    }
+    // results: straight into device outputs, or via staging for host outputs
+    const bool dev_out = (!dose_out || is_device_ptr(dose_out)) && (!sigma_out || is_device_ptr(sigma_out)) &&
+                         dose_out && sigma_out;
+    double *dd = dose_out, *ds = sigma_out;
+    if (!dev_out) {
+        if ((rc = ensure(ws.stage, V * 16))) return rc;
+        dd = static_cast<double*>(ws.stage.p);
+        ds = dd + V;
+    }
+    if ((rc = launch_finalize(ctx, P, V, n_batches, dd, ds))) return rc;
+    if (!dev_out) {
+        if (dose_out) GDPM_CUDA_TRY(cudaMemcpyAsync(dose_out, dd, V * 8, cudaMemcpyDefault, s));
+        if (sigma_out) GDPM_CUDA_TRY(cudaMemcpyAsync(sigma_out, ds, V * 8, cudaMemcpyDefault, s));
+    }
+    unsigned char* h = static_cast<unsigned char*>(ws.pinned_host.p);
+    unsigned long long* hc = reinterpret_cast<unsigned long long*>(h + 64);
+    double* hl = reinterpret_cast<double*>(h + 64 + C_NCOUNT * 8);
+    uint32_t* hs = reinterpret_cast<uint32_t*>(h + 64 + C_NCOUNT * 8 + L_NLEDGER * 8);
+    GDPM_CUDA_TRY(cudaMemcpyAsync(hc, ws.counters.p, C_NCOUNT * 8, cudaMemcpyDeviceToHost, s));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(hl, ws.ledger.p, L_NLEDGER * 8, cudaMemcpyDeviceToHost, s));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(hs, ws.status.p, 4, cudaMemcpyDeviceToHost, s));
+    GDPM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        fill_stats(hc, hl, st);
+        st->phases = phases;
+        st->launches = phases + n_batches + 2;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        st->transport_ms = ms;
+        st->crossings = int64_t(hc[C_CROSS]);
+    }
+    prof_collect(ctx, st);
+    if (*hs & ST_QUEUE_OVERFLOW) return GDPM_E_QUEUE_OVERFLOW;
+    if (*hs & ST_ITER_CAP) return GDPM_E_TIMEOUT;
+    return GDPM_OK;
+}
+
+}  // namespace gdpm
+
+using namespace gdpm;
+
+extern "C" {
+
+const char* gdpm_strerror(int code) {
+    switch (code) {
+    case GDPM_OK: return "ok";
+    case GDPM_E_ARG: return "invalid argument";
+    case GDPM_E_NOMEM: return "device memory allocation failed";
+    case GDPM_E_QUEUE_OVERFLOW: return "secondary particle queue overflow";
+    case GDPM_E_TIMEOUT: return "phase or iteration cap reached";
+    case GDPM_E_CUDA: return cudaGetErrorString(last_cuda_error());
+    case GDPM_E_STATE: return "call not valid in the current state";
+    case GDPM_E_BUSY: return "request not admitted";
+    }
+    return "unknown status";
+}
+
+int gdpm_context_create(gdpm_ctx** out, int device, void* cuda_stream, uint64_t seed) {
+    if (!out) return GDPM_E_ARG;
+    *out = nullptr;
+    int n = 0;
+    GDPM_CUDA_TRY(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return GDPM_E_ARG;
+    GDPM_CUDA_TRY(cudaSetDevice(device));
+    gdpm_ctx* c = new gdpm_ctx();
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->seed = seed;
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess ||
+        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        last_cuda_error() = cudaGetLastError();
+        delete c;
+        return GDPM_E_CUDA;
+    }
+    c->sm_count = prop.multiProcessorCount;
+    *out = c;
+    return GDPM_OK;
+}
+
+int gdpm_context_destroy(gdpm_ctx* ctx) {
+    if (!ctx) return GDPM_E_ARG;
+    if (ctx->worker.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->stop = true;
+        }
+        ctx->cv.notify_all();
+        ctx->worker.join();
+    }
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    Workspace& w = ctx->ws;
+    Buffer* bs[] = {&w.edep, &w.s1, &w.s2, &w.hi, &w.lo, &w.qph, &w.qel0, &w.qel1, &w.ctl,
+                    &w.prefix, &w.counters, &w.ledger, &w.status, &w.edges, &w.beamlets,
+                    &w.bl_cdf, &w.stage};
+    for (Buffer* b : bs) release(*b);
+    if (w.pinned_host.p) cudaFreeHost(w.pinned_host.p);
+    for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+    return GDPM_OK;
+}
+
+int gdpm_set_param(gdpm_ctx* ctx, int param, double v) {
+    if (!ctx) return GDPM_E_ARG;
+    switch (param) {
+    case GDPM_PARAM_QUEUE_CAPACITY:
+        if (v < 0 || v > 4.0e9) return GDPM_E_ARG;
+        ctx->queue_capacity = uint32_t(v);
+        return GDPM_OK;
+    case GDPM_PARAM_BLOCK_THREADS:
+        if (v < 64 || v > 256 || int(v) % 32) return GDPM_E_ARG;
+        ctx->block_threads = int(v);
+        return GDPM_OK;
+    case GDPM_PARAM_BLOCKS_PER_SM:
+        if (v < 0 || v > 32) return GDPM_E_ARG;
+        ctx->blocks_per_sm = int(v);
+        return GDPM_OK;
+    case GDPM_PARAM_TALLY_MODE:
+        if (v != 0 && v != 1) return GDPM_E_ARG;
+        ctx->tally_mode = int(v);
+        return GDPM_OK;
+    case GDPM_PARAM_SOURCE_CHUNK:
+        if (v < 0 || v > 4.0e9) return GDPM_E_ARG;
+        ctx->source_chunk = uint32_t(v);
+        return GDPM_OK;
+    case GDPM_PARAM_MAX_PHASES:
+        if (v < 8 || v > 1e6) return GDPM_E_ARG;
+        ctx->max_phases = int(v);
+        return GDPM_OK;
+    case GDPM_PARAM_REQUEST_ID:
+        if (v < 0 || v > 4294967295.0) return GDPM_E_ARG;
+        ctx->request_id = uint32_t(v);
+        return GDPM_OK;
+    case GDPM_PARAM_SPECULATIVE:
+        if (v < 1 || v > 64) return GDPM_E_ARG;
+        ctx->speculative = int(v);
+        return GDPM_OK;
+    case GDPM_PARAM_WARP_AGGREGATE:
+        if (v != 0 && v != 1) return GDPM_E_ARG;
+        ctx->warp_aggregate = int(v);
+        return GDPM_OK;
+    case GDPM_PARAM_PROFILE:
+        if (v != 0 && v != 1) return GDPM_E_ARG;
+        ctx->profile = int(v);
+        return GDPM_OK;
+    }
+    return GDPM_E_ARG;
+}
+
+int gdpm_phantom_create(gdpm_ctx* ctx, int nx, int ny, int nz, float dx, float dy, float dz,
+                        const uint8_t* material, const float* density, gdpm_phantom** out) {
+    if (!ctx || !out || !material || !density) return GDPM_E_ARG;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 1024 || ny > 1024 || nz > 1024) return GDPM_E_ARG;
+    if (!(dx > 0) || !(dy > 0) || !(dz > 0)) return GDPM_E_ARG;
+    GDPM_CUDA_TRY(cudaSetDevice(ctx->device));
+    gdpm_phantom* ph = new gdpm_phantom();
+    ph->ctx = ctx;
+    ph->nx = nx; ph->ny = ny; ph->nz = nz;
+    ph->dx = dx; ph->dy = dy; ph->dz = dz;
+    const size_t V = size_t(nx) * ny * nz;
+    int rc;
+    if ((rc = ensure(ph->mat, V)) || (rc = ensure(ph->rho, V * 4))) {
+        gdpm_phantom_destroy(ph);
+        return rc;
+    }
+    if (cudaMemcpyAsync(ph->mat.p, material, V, cudaMemcpyDefault, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(ph->rho.p, density, V * 4, cudaMemcpyDefault, ctx->stream) != cudaSuccess) {
+        last_cuda_error() = cudaGetLastError();
+        gdpm_phantom_destroy(ph);
+        return GDPM_E_CUDA;
+    }
+    if ((rc = phantom_density_max(ctx, ph))) {
+        gdpm_phantom_destroy(ph);
+        return rc;
+    }
+    *out = ph;
+    return GDPM_OK;
+}
+
+int gdpm_phantom_destroy(gdpm_phantom* ph) {
+    if (!ph) return GDPM_E_ARG;
+    if (ph->ctx) cudaStreamSynchronize(ph->ctx->stream);
+    release(ph->mat);
+    release(ph->rho);
+    release(ph->rhomax);
+    release(ph->maj);
+    delete ph;
+    return GDPM_OK;
+}
+
+int gdpm_tables_build(gdpm_ctx* ctx, const gdpm_material_desc* mats, int n_mats, double e_min,
+                      double e_max, int n_energy, double eabs_photon, double eabs_electron,
+                      double ms_loss, int flags, gdpm_tables** out) {
+    if (!ctx || !mats || !out) return GDPM_E_ARG;
+    *out = nullptr;
+    if (n_mats < 1 || n_mats > GDPM_MAX_MATERIALS || n_energy < 16 || n_energy > 8192) return GDPM_E_ARG;
+    if (!(e_min > 0) || !(e_max > e_min * 1.01)) return GDPM_E_ARG;
+    if (!(eabs_photon >= e_min) || !(eabs_electron >= e_min / 0.5) || eabs_electron >= e_max ||
+        eabs_photon >= e_max || !(ms_loss > 0 && ms_loss < 0.9))
+        return GDPM_E_ARG;
+    if (flags & ~(GDPM_FLAG_COMPTON_ONLY | GDPM_FLAG_NO_HARD)) return GDPM_E_ARG;
+    for (int m = 0; m < n_mats; ++m) {
+        const gdpm_material_desc& d = mats[m];
+        if (d.n_elements < 1 || d.n_elements > GDPM_MAX_ELEMENTS || !(d.mean_excitation_MeV > 0))
+            return GDPM_E_ARG;
+        double ws = 0;
+        for (int i = 0; i < d.n_elements; ++i) {
+            if (d.Z[i] < 1 || d.Z[i] > 100 || !(d.A[i] > 0) || d.mass_fraction[i] < 0) return GDPM_E_ARG;
+            ws += d.mass_fraction[i];
+        }
+        if (!(ws > 0)) return GDPM_E_ARG;
+    }
+    GDPM_CUDA_TRY(cudaSetDevice(ctx->device));
+    gdpm_tables* t = new gdpm_tables();
+    t->ctx = ctx;
+    t->id = ctx->next_tables_id++;
+    t->n_mat = n_mats;
+    t->n_e = n_energy;
+    t->e_min = e_min; t->e_max = e_max;
+    t->eabs_ph = eabs_photon; t->eabs_el = eabs_electron;
+    t->ms_loss = ms_loss;
+    t->flags = flags;
+    const int rc = build_tables_device(ctx, t, mats);
+    if (rc) {
+        gdpm_tables_destroy(t);
+        return rc;
+    }
+    if (transport_smem(t, GDPM_ELECTRON) > 200 * 1024 || transport_smem(t, GDPM_PHOTON) > 200 * 1024) {
+        gdpm_tables_destroy(t);
+        return GDPM_E_ARG;
+    }
+    *out = t;
+    return GDPM_OK;
+}
+
+int gdpm_tables_destroy(gdpm_tables* t) {
+    if (!t) return GDPM_E_ARG;
+    if (t->ctx) cudaStreamSynchronize(t->ctx->stream);
+    release(t->ph_tot); release(t->ph_cum); release(t->el); release(t->rinv); release(t->atab);
+    delete t;
+    return GDPM_OK;
+}
+
+int gdpm_source_set(gdpm_ctx* ctx, const gdpm_source_desc* s) {
+    if (!ctx || !s) return GDPM_E_ARG;
+    if (s->particle != GDPM_PHOTON && s->particle != GDPM_ELECTRON) return GDPM_E_ARG;
+    if (s->geometry < GDPM_GEO_PENCIL || s->geometry > GDPM_GEO_BEAMLETS) return GDPM_E_ARG;
+    if (s->n_bins < 1 || s->n_bins > GDPM_MAX_BINS || !s->bin_edges || !s->bin_weights) return GDPM_E_ARG;
+    double ws = 0;
+    for (int j = 0; j < s->n_bins; ++j) {
+        if (s->bin_weights[j] < 0 || s->bin_edges[j + 1] < s->bin_edges[j]) return GDPM_E_ARG;
+        ws += s->bin_weights[j];
+    }
+    if (!(ws > 0) || !(s->bin_edges[0] >= 0)) return GDPM_E_ARG;
+    if (s->geometry == GDPM_GEO_BEAMLETS) {
+        if (s->n_beamlets < 1 || !s->beamlets) return GDPM_E_ARG;
+        double bw = 0;
+        for (int b = 0; b < s->n_beamlets; ++b) {
+            if (s->beamlets[size_t(b) * 17 + 16] < 0) return GDPM_E_ARG;
+            bw += s->beamlets[size_t(b) * 17 + 16];
+        }
+        if (!(bw > 0)) return GDPM_E_ARG;
+    }
+    const double dn = s->direction[0] * s->direction[0] + s->direction[1] * s->direction[1] +
+                      s->direction[2] * s->direction[2];
+    if (s->geometry == GDPM_GEO_PENCIL && !(dn > 0)) return GDPM_E_ARG;
+    gdpm_source_state& st = ctx->src;
+    st.desc = *s;
+    st.edges.assign(s->bin_edges, s->bin_edges + s->n_bins + 1);
+    st.weights.assign(s->bin_weights, s->bin_weights + s->n_bins);
+    if (s->geometry == GDPM_GEO_BEAMLETS) st.beamlets.assign(s->beamlets, s->beamlets + size_t(s->n_beamlets) * 17);
+    else st.beamlets.clear();
+    st.desc.bin_edges = nullptr;
+    st.desc.bin_weights = nullptr;
+    st.desc.beamlets = nullptr;
+    st.set = true;
+    return GDPM_OK;
+}
+
+int gdpm_set_history_records(gdpm_ctx* ctx, int32_t* rec, double* recd, uint64_t n) {
+    if (!ctx) return GDPM_E_ARG;
+    if ((rec == nullptr) != (recd == nullptr)) return GDPM_E_ARG;
+    if (rec && (!is_device_ptr(rec) || !is_device_ptr(recd) || n == 0)) return GDPM_E_ARG;
+    ctx->hrec = rec;
+    ctx->hrecd = recd;
+    ctx->hrec_n = rec ? n : 0;
+    return GDPM_OK;
+}
+
+int gdpm_simulate(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_histories,
+                  int n_batches, double* dose_out, double* sigma_out, gdpm_stats* stats_out) {
+    if (!ctx) return GDPM_E_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return GDPM_E_CUDA;
+    return simulate_impl(ctx, ph, tb, ctx->src, ctx->request_id, n_histories, n_batches, dose_out,
+                         sigma_out, stats_out);
+}
+
+int gdpm_debug_philox(gdpm_ctx* ctx, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
+                      uint64_t n) {
+    if (!ctx || !ctr || !out || !is_device_ptr(ctr) || !is_device_ptr(out)) return GDPM_E_ARG;
+    int rc = launch_debug_philox(ctx, ctr, k0, k1, out, n);
+    if (rc) return rc;
+    GDPM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GDPM_OK;
+}
+
+int gdpm_debug_sample(gdpm_ctx* ctx, int kind, double a, double b, uint64_t n, uint64_t seed,
+                      double* out1, double* out2) {
+    if (!ctx || !out1 || kind < 0 || kind > 4 || !is_device_ptr(out1) || (out2 && !is_device_ptr(out2)))
+        return GDPM_E_ARG;
+    if (kind == 1 && !(a > 2 * b && b > 0)) return GDPM_E_ARG;
+    if (kind == 2 && !(a > b && b > 0)) return GDPM_E_ARG;
+    if (kind == 0 && !(a > 0)) return GDPM_E_ARG;
+    int rc = launch_debug_sample(ctx, kind, a, b, n, seed, out1, out2);
+    if (rc) return rc;
+    GDPM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GDPM_OK;
+}
+
+int gdpm_tables_export(gdpm_tables* t, int which, double* out, int64_t* count) {
+    if (!t || !count) return GDPM_E_ARG;
+    const int M = t->n_mat, n = t->n_e;
+    std::vector<double> v;
+    cudaStream_t s = t->ctx->stream;
+    if (which >= 0 && which <= 5) {
+        std::vector<float> a(size_t(M) * n);
+        if (which <= 2) {
+            std::vector<float> tot(size_t(M) * n);
+            std::vector<float2> cum(size_t(M) * n);
+            GDPM_CUDA_TRY(cudaMemcpyAsync(tot.data(), t->ph_tot.p, tot.size() * 4, cudaMemcpyDeviceToHost, s));
+            GDPM_CUDA_TRY(cudaMemcpyAsync(cum.data(), t->ph_cum.p, cum.size() * 8, cudaMemcpyDeviceToHost, s));
+            GDPM_CUDA_TRY(cudaStreamSynchronize(s));
+            for (size_t k = 0; k < a.size(); ++k) {
+                if (which == 0) v.push_back(cum[k].x);
+                else if (which == 1) v.push_back(cum[k].y);
+                else v.push_back(tot[k]);
+            }
+        } else {
+            std::vector<float4> el(size_t(M) * n);
+            GDPM_CUDA_TRY(cudaMemcpyAsync(el.data(), t->el.p, el.size() * 16, cudaMemcpyDeviceToHost, s));
+            GDPM_CUDA_TRY(cudaStreamSynchronize(s));
+            for (size_t k = 0; k < el.size(); ++k)
+                v.push_back(which == 3 ? el[k].x : (which == 4 ? el[k].z : el[k].w));
+        }
+    } else if (which == 6) {
+        for (int i = 0; i < n; ++i)
+            v.push_back(std::exp(std::log(t->e_min) + i * (std::log(t->e_max) - std::log(t->e_min)) / (n - 1)));
+    } else if (which == 7) {
+        for (int m = 0; m < M; ++m) v.push_back(t->dev.x0[m]);
+    } else if (which == 8) {
+        for (int m = 0; m < M; ++m) v.push_back(t->dev.sigmax[m]);
+    } else {
+        return GDPM_E_ARG;
+    }
+    *count = int64_t(v.size());
+    if (out) GDPM_CUDA_TRY(cudaMemcpy(out, v.data(), v.size() * 8, cudaMemcpyDefault));
+    return GDPM_OK;
+}
+
+int gdpm_debug_sources(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_histories,
+                       int n_batches, uint64_t first, uint64_t n, double* out) {
+    int rc = validate_run(ctx, ph, tb, ctx ? ctx->src : gdpm_source_state(), n_histories, n_batches);
+    if (rc) return rc;
+    const uint64_t nb0 = n_histories / n_batches + (n_histories % n_batches ? 1 : 0);
+    if (!out || !is_device_ptr(out) || first + n > nb0) return GDPM_E_ARG;
+    const int n_bins = int(ctx->src.weights.size());
+    std::vector<uint32_t> prefix(n_bins + 1);
+    allot_prefix(ctx->src.weights, nb0, prefix.data());
+    if ((rc = ensure(ctx->ws.prefix, prefix.size() * 4))) return rc;
+    GDPM_CUDA_TRY(cudaMemcpyAsync(ctx->ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    if ((rc = build_majorant(ctx, ph, tb))) return rc;
+    SimParams P = base_params(ctx, ph, tb, ctx->request_id);
+    if ((rc = source_upload(ctx, ctx->src, P.S))) return rc;
+    PhaseArgs A{};
+    A.src_first_local = uint32_t(first);
+    A.batch_first_hist = 0;
+    A.bin_prefix = static_cast<const uint32_t*>(ctx->ws.prefix.p);
+    if ((rc = launch_debug_sources(ctx, P, A, n, out))) return rc;
+    GDPM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GDPM_OK;
+}
+
+int gdpm_request_submit(gdpm_ctx* ctx, const gdpm_request_desc* req, uint64_t* req_id) {
+    (void)ctx; (void)req; (void)req_id;
+    return GDPM_E_STATE;
+}
+
+int gdpm_request_poll(gdpm_ctx* ctx, uint64_t req_id, int* done, double* dose_out, double* sigma_out,
+                      gdpm_stats* stats_out) {
+    (void)ctx; (void)req_id; (void)done; (void)dose_out; (void)sigma_out; (void)stats_out;
+    return GDPM_E_STATE;
+}
+
+}  // extern "C"

@@ -1,0 +1,805 @@
+// Transport kernels of the gDPM method on sm_103a.
+//
+// Photon and electron transport run in separate phases (Sec. 2.2.1: only
+// one particle type is in flight at a time; secondaries go to per-type
+// stacks).  Each phase is one persistent launch: every warp keeps its 32
+// lanes busy by refilling a lane from the phase's input (a queue of banked
+// particles, plus freshly generated primaries) whenever the lane's particle
+// terminates, so warps stay full until the input is drained instead of
+// idling on their longest history.  A lane advances its particle by one
+// step per iteration:
+//   photon:   one Woodcock flight against the majorant (Sec. 2.1) and, if
+//             the collision is real, one Compton / photoelectric / pair event;
+//   electron: one condensed-history step (CSDA loss over the step, random
+//             hinge multiple scattering, voxel walk depositing along the
+//             path) and, at a hard-event candidate, Moller or
+//             bremsstrahlung (Sec. 2.1).
+// Tables live in shared memory (Sec. 2.2.2 reads them by linear
+// interpolation); random numbers come from Philox4x32-10 keyed per history
+// and particle, so results do not depend on scheduling.
+#include <cfloat>
+
+#include "internal.h"
+
+namespace gdpm {
+namespace {
+
+constexpr float kInf = FLT_MAX;
+constexpr float kEs = 21.2f;            // Rossi-Greisen scattering energy, MeV
+
+// ---------------------------------------------------------------- ledger/tally
+struct Acc {
+    double src, esc, disc;
+};
+
+__device__ __forceinline__ void tally(const SimParams& P, uint32_t vox, float e) {
+    if (P.tally_mode == 0) {
+        if (P.warp_aggregate) {
+            const uint32_t mask = __activemask();
+            const uint32_t peers = __match_any_sync(mask, vox);
+            const int lane = int(lane_id());
+            const int leader = __ffs(peers) - 1;
+            const uint32_t rounds = __reduce_max_sync(mask, uint32_t(__popc(peers))) - 1u;
+            uint32_t others = peers & ~(1u << lane);
+            double acc = e;
+            for (uint32_t r = 0; r < rounds; ++r) {
+                const int src = (lane == leader && others) ? __ffs(others) - 1 : lane;
+                const float v = __shfl_sync(mask, e, src);
+                if (lane == leader && others) {
+                    acc += v;
+                    others &= others - 1u;
+                }
+            }
+            if (lane == leader) atomicAdd(&P.edep[vox], acc);
+        } else {
+            atomicAdd(&P.edep[vox], double(e));
+        }
+    } else {
+        // FP32 pair: hi accumulates, lo collects the exact rounding error of
+        // each addition (TwoSum on the value the atomic returned).
+        const float old = atomicAdd(&P.edep_hi[vox], e);
+        const float s = old + e;
+        const float bb = s - old;
+        const float err = (old - (s - bb)) + (e - bb);
+        if (err != 0.f) atomicAdd(&P.edep_lo[vox], err);
+    }
+}
+
+__device__ __forceinline__ uint32_t vox_of(const SimParams& P, int ix, int iy, int iz) {
+    return uint32_t(ix) + uint32_t(P.nx) * (uint32_t(iy) + uint32_t(P.ny) * uint32_t(iz));
+}
+
+__device__ __forceinline__ void hist_count(const SimParams& P, uint32_t hist, int k) {
+    if (P.hrec) atomicAdd(&P.hrec[size_t(hist) * 4 + k], 1);
+}
+__device__ __forceinline__ void hist_add(const SimParams& P, uint32_t hist, int k, double v) {
+    if (P.hrec) atomicAdd(&P.hrecd[size_t(hist) * 2 + k], v);
+}
+
+// Bank a secondary in queue q (Sec. 2.2.1 stacks).  Electrons and photons
+// below their absorption energy are deposited on the spot; positrons are
+// always banked.  The child's Philox stream is keyed by a counter-derived
+// id, so it does not depend on when or where it is transported.
+__device__ void bank(const SimParams& P, const Queue& q, uint32_t* tail, Part& parent, bool photon,
+                     bool positron, float E, float x, float y, float z, float u, float v, float w,
+                     uint32_t* s_cnt) {
+    if (!positron && E < (photon ? P.T.eabs_ph : P.T.eabs_el)) {
+        tally(P, vox_of(P, parent.ix, parent.iy, parent.iz), E);
+        count_event(s_cnt, C_LOCAL_DEP);
+        return;
+    }
+    Part c;
+    c.x = x; c.y = y; c.z = z; c.u = u; c.v = v; c.w = w; c.E = E;
+    c.ix = parent.ix; c.iy = parent.iy; c.iz = parent.iz;
+    c.hist = parent.hist;
+    const uint64_t id = child_id(uint64_t(parent.pidlo) | (uint64_t(parent.pidhi) << 32),
+                                 parent.flags & 0xFFFFFFu);
+    c.pidlo = uint32_t(id);
+    c.pidhi = uint32_t(id >> 32);
+    c.ctr = 0;
+    c.flags = positron ? kPositron : 0u;
+    ++parent.flags;
+    const uint32_t slot = reserve_slot(tail);
+    if (slot < q.capacity) queue_store(q, slot, c);
+    else atomicOr(P.status, ST_QUEUE_OVERFLOW);
+    count_event(s_cnt, photon ? C_PH_CREATED : C_EL_CREATED);
+    count_event(s_cnt, photon ? C_PUSH_PH : C_PUSH_EL);
+    hist_count(P, parent.hist, 3);
+}
+
+// ---------------------------------------------------------------- samplers
+// Klein-Nishina in eps = E'/E by the two-branch mixture method: with weight
+// ln(1/eps0) sample from 1/eps, with weight (1-eps0^2)/2 from eps, accept
+// with 1 - eps sin^2(theta)/(1+eps^2).  Draws: (branch, eps, accept, phi).
+__device__ __forceinline__ void sample_kn(Part& p, const SimParams& P, float E, float& eps,
+                                          float& cost, float& rphi) {
+    const float k = E * (1.f / kMC2f);
+    const float e0 = 1.f / fmaf(2.f, k, 1.f);
+    const float a1 = -__logf(e0), a2 = 0.5f * (1.f - e0 * e0);
+    float t = 0.f;
+    eps = 1.f;
+    rphi = 0.5f;
+    for (int it = 0; it < 4096; ++it) {
+        const float4 c = draw(p, P.key0, P.key1);
+        if (c.x * (a1 + a2) < a1) eps = __expf(-a1 * c.y);
+        else eps = sqrtf(fmaf(1.f - e0 * e0, c.y, e0 * e0));
+        t = (1.f - eps) / (k * eps);
+        const float g = 1.f - eps * t * (2.f - t) / fmaf(eps, eps, 1.f);
+        rphi = c.w;
+        if (c.z <= g) break;
+    }
+    cost = 1.f - t;
+}
+
+// Moller: eps = W/T on [W_cc/T, 1/2] from the 1/eps^2 proposal, accepted with
+// eps^2 f(eps) / (2 + c1/4).  Draws: (eps, accept, phi, -).
+__device__ __forceinline__ void sample_moller(Part& p, const SimParams& P, float T, float wcc,
+                                              float& eps, float& rphi) {
+    const float tau = T * (1.f / kMC2f);
+    const float g = tau / (tau + 1.f);
+    const float c1 = g * g, c2 = (2.f * tau + 1.f) / ((tau + 1.f) * (tau + 1.f));
+    const float ec = wcc / T;
+    const float bound = 2.f + 0.25f * c1;
+    eps = ec;
+    rphi = 0.5f;
+    for (int it = 0; it < 4096; ++it) {
+        const float4 w = draw(p, P.key0, P.key1);
+        eps = ec / (1.f - w.x * (1.f - 2.f * ec));
+        const float x = eps / (1.f - eps);
+        const float gg = 1.f + x * x + c1 * eps * eps - c2 * x;
+        rphi = w.z;
+        if (w.y * bound <= gg) break;
+    }
+}
+
+// Screening parameter A for first moment G1 (table in ln G1; asymptote
+// 1/A = 3d(1 + 3d/2), d = 1 - G1, near isotropy).
+__device__ __forceinline__ float screening_A(const DevTables& T, const float* atab, float G1) {
+    if (G1 > T.a_g1hi) {
+        const float d = 1.f - G1;
+        return 1.f / (3.f * d * (1.f + 1.5f * d));
+    }
+    float kk = (__logf(G1) - T.a_l1lo) * T.a_idl;
+    kk = fmaxf(kk, 0.f);
+    const int k = min(int(kk), T.n_a - 2);
+    const float f = fminf(kk - float(k), 1.f);
+    return __expf(lerpf(atab[k], atab[k + 1], f));
+}
+
+// ---------------------------------------------------------------- geometry
+__device__ __forceinline__ bool inside(const SimParams& P, float x, float y, float z) {
+    return x >= 0.f && x <= P.Lx && y >= 0.f && y <= P.Ly && z >= 0.f && z <= P.Lz;
+}
+
+__device__ __forceinline__ void voxel_of(const SimParams& P, Part& p) {
+    p.ix = min(int(p.x * P.inv_dx), P.nx - 1);
+    p.iy = min(int(p.y * P.inv_dy), P.ny - 1);
+    p.iz = min(int(p.z * P.inv_dz), P.nz - 1);
+}
+
+// Move a primary from outside onto the phantom surface (ray-box slabs); the
+// entry coordinate is set exactly on the face.  False if the ray misses.
+__device__ bool enter_box(const SimParams& P, Part& p) {
+    if (inside(P, p.x, p.y, p.z)) return true;
+    const float o[3] = {p.x, p.y, p.z}, d[3] = {p.u, p.v, p.w}, L[3] = {P.Lx, P.Ly, P.Lz};
+    float tmin = -kInf, tmax = kInf;
+    int amin = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.f) {
+            if (o[a] < 0.f || o[a] > L[a]) return false;
+            continue;
+        }
+        const float t1 = (0.f - o[a]) / d[a], t2 = (L[a] - o[a]) / d[a];
+        const float lo = fminf(t1, t2), hi = fmaxf(t1, t2);
+        if (lo > tmin) { tmin = lo; amin = a; }
+        if (hi < tmax) tmax = hi;
+    }
+    if (amin < 0 || tmax <= tmin || tmax <= 0.f) return false;
+    float q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q[a] = fminf(fmaxf(fmaf(tmin, d[a], o[a]), 0.f), L[a]);
+    q[amin] = d[amin] > 0.f ? 0.f : L[amin];
+    p.x = q[0]; p.y = q[1]; p.z = q[2];
+    return true;
+}
+
+// Primary number `idx` of this phase (Sec. 2.3): energy from the batch's
+// spectrum interval allotment (uniform inside the interval), position and
+// direction from the source geometry.  Draw 0 of the primary's stream:
+// (u-position, v-position, energy, beamlet).
+__device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t idx, bool photon,
+                             Part& p, Acc& acc, uint32_t* s_cnt) {
+    const DevSource& S = P.S;
+    const uint32_t local = A.src_first_local + idx;
+    p.hist = A.batch_first_hist + local;
+    p.pidlo = 1u; p.pidhi = 0u; p.ctr = 0u; p.flags = 0u;
+    const float4 r = draw(p, P.key0, P.key1);
+    int lo = 0, hi = S.n_bins;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (A.bin_prefix[mid] <= local) lo = mid; else hi = mid;
+    }
+    p.E = fmaf(S.edges[lo + 1] - S.edges[lo], r.z, S.edges[lo]);
+    if (S.geometry == GDPM_GEO_PENCIL) {
+        p.x = S.origin[0]; p.y = S.origin[1]; p.z = S.origin[2];
+        p.u = S.direction[0]; p.v = S.direction[1]; p.w = S.direction[2];
+    } else {
+        const float *src, *cen, *au, *av;
+        float a0, a1, b0, b1;
+        if (S.geometry == GDPM_GEO_POINT_FIELD) {
+            src = S.origin; cen = S.center; au = S.axis_u; av = S.axis_v;
+            a0 = -S.half_u; a1 = S.half_u; b0 = -S.half_v; b1 = S.half_v;
+        } else {
+            // beamlet I with P(I) <= r < P(I+1) on the cumulative fluence (Sec. 2.3.1)
+            const double rr = double(r.w);
+            int l = 0, h = S.n_beamlets - 1;
+            while (l < h) {
+                const int mid = (l + h) >> 1;
+                if (rr < S.bl_cdf[mid]) h = mid; else l = mid + 1;
+            }
+            const float* row = S.beamlets + size_t(l) * 16;
+            src = row; cen = row + 3; au = row + 6; av = row + 9;
+            a0 = row[12]; a1 = row[13]; b0 = row[14]; b1 = row[15];
+        }
+        const float su = fmaf(a1 - a0, r.x, a0), sv = fmaf(b1 - b0, r.y, b0);
+        const float ax = cen[0] + su * au[0] + sv * av[0];
+        const float ay = cen[1] + su * au[1] + sv * av[1];
+        const float az = cen[2] + su * au[2] + sv * av[2];
+        p.x = src[0]; p.y = src[1]; p.z = src[2];
+        const float dx = ax - p.x, dy = ay - p.y, dz = az - p.z;
+        const float n = rsqrtf(dx * dx + dy * dy + dz * dz);
+        p.u = dx * n; p.v = dy * n; p.w = dz * n;
+    }
+    acc.src += p.E;
+    count_event(s_cnt, C_PRIMARY);
+    count_event(s_cnt, photon ? C_PH_CREATED : C_EL_CREATED);
+    if (!enter_box(P, p)) {
+        acc.esc += p.E;
+        hist_add(P, p.hist, 0, p.E);
+        count_event(s_cnt, photon ? C_PH_TERMINATED : C_EL_TERMINATED);
+        return false;
+    }
+    voxel_of(P, p);
+    return true;
+}
+
+// ---------------------------------------------------------------- photon step
+struct PhSmem {
+    const float* maj;
+    const float* tot;
+    const float2* cum;
+};
+
+__device__ void photon_step(const SimParams& P, const PhaseArgs& A, const PhSmem& S, Part& p,
+                            bool& active, Acc& acc, uint32_t* s_cnt) {
+    const DevTables& T = P.T;
+    if (p.E < T.eabs_ph) {   // only a source photon below the cutoff reaches here
+        tally(P, vox_of(P, p.ix, p.iy, p.iz), p.E);
+        count_event(s_cnt, C_PH_TERMINATED);
+        active = false;
+        return;
+    }
+    const float4 r = draw(p, P.key0, P.key1);
+    int i;
+    float f;
+    grid_pos(T, p.E, i, f);
+    const float mm = lerpf(S.maj[i], S.maj[i + 1], f);
+    const float s = -__logf(r.x) / mm;
+    p.x = fmaf(s, p.u, p.x);
+    p.y = fmaf(s, p.v, p.y);
+    p.z = fmaf(s, p.w, p.z);
+    if (!inside(P, p.x, p.y, p.z)) {
+        acc.esc += p.E;
+        hist_add(P, p.hist, 0, p.E);
+        count_event(s_cnt, C_PH_TERMINATED);
+        active = false;
+        return;
+    }
+    voxel_of(P, p);
+    const uint32_t vox = vox_of(P, p.ix, p.iy, p.iz);
+    const int m = __ldg(&P.mat[vox]);
+    const float rho = __ldg(&P.rho[vox]);
+    count_event(s_cnt, C_PH_FLIGHTS);
+    const int mi = m * T.n_e + i;
+    const float mt = lerpf(S.tot[mi], S.tot[mi + 1], f);
+    if (r.y * mm >= mt * rho) return;                 // virtual (delta) collision
+    count_event(s_cnt, C_PH_REAL);
+    hist_count(P, p.hist, 0);
+    const float2 c0 = S.cum[mi], c1 = S.cum[mi + 1];
+    const float rr = r.z * mt;
+    if (rr < lerpf(c0.x, c1.x, f)) {
+        // Compton (Klein-Nishina); recoil electron along E u - E' u'
+        count_event(s_cnt, C_COMPTON);
+        const float E = p.E;
+        float eps, cost, rphi;
+        sample_kn(p, P, E, eps, cost, rphi);
+        float cp, sp;
+        cossin_2pi(rphi, cp, sp);
+        const float u0 = p.u, v0 = p.v, w0 = p.w;
+        rotate(p.u, p.v, p.w, cost, cp, sp);
+        const float Ep = eps * E, Te = E - Ep;
+        float ex = E * u0 - Ep * p.u, ey = E * v0 - Ep * p.v, ez = E * w0 - Ep * p.w;
+        const float en = rsqrtf(ex * ex + ey * ey + ez * ez);
+        bank(P, A.out_el, A.out_el_count, p, false, false, Te, p.x, p.y, p.z, ex * en, ey * en,
+             ez * en, s_cnt);
+        if (Ep < T.eabs_ph) {
+            tally(P, vox, Ep);
+            count_event(s_cnt, C_LOCAL_DEP);
+            count_event(s_cnt, C_PH_TERMINATED);
+            active = false;
+        } else {
+            p.E = Ep;
+        }
+    } else if (rr < lerpf(c0.y, c1.y, f)) {
+        // photoelectric: photon absorbed, photoelectron along the photon
+        count_event(s_cnt, C_PHOTO);
+        bank(P, A.out_el, A.out_el_count, p, false, false, p.E, p.x, p.y, p.z, p.u, p.v, p.w, s_cnt);
+        count_event(s_cnt, C_PH_TERMINATED);
+        active = false;
+    } else {
+        // pair: electron takes r.w of the kinetic energy, positron the rest
+        count_event(s_cnt, C_PAIR);
+        const float tav = p.E - 2.f * kMC2f;
+        const float t1 = r.w * tav, t2 = tav - t1;
+        bank(P, A.out_el, A.out_el_count, p, false, false, t1, p.x, p.y, p.z, p.u, p.v, p.w, s_cnt);
+        bank(P, A.out_el, A.out_el_count, p, false, true, t2, p.x, p.y, p.z, p.u, p.v, p.w, s_cnt);
+        count_event(s_cnt, C_PH_TERMINATED);
+        active = false;
+    }
+}
+
+// ---------------------------------------------------------------- electron step
+struct ElSmem {
+    const float4* el;
+    const float* rinv;
+    const float* atab;
+};
+
+// Straight segment of mass thickness `mass` through the voxel grid (3-D
+// DDA), depositing dpm MeV per g/cm2 in each voxel; with defer_last the
+// final piece is left to the caller.  True if the particle left the phantom.
+__device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& dep, bool defer_last,
+                     uint32_t& crossings) {
+    if (!(mass > 0.f)) return false;
+    const float iu = p.u != 0.f ? 1.f / p.u : 0.f;
+    const float iv = p.v != 0.f ? 1.f / p.v : 0.f;
+    const float iw = p.w != 0.f ? 1.f / p.w : 0.f;
+    const int sx = p.u > 0.f ? 1 : -1, sy = p.v > 0.f ? 1 : -1, sz = p.w > 0.f ? 1 : -1;
+    uint32_t vox = vox_of(P, p.ix, p.iy, p.iz);
+    float left = mass;
+    for (int guard = 0; guard < (1 << 20); ++guard) {
+        const float tx = p.u != 0.f ? (float(p.ix + (sx > 0)) * P.dx - p.x) * iu : kInf;
+        const float ty = p.v != 0.f ? (float(p.iy + (sy > 0)) * P.dy - p.y) * iv : kInf;
+        const float tz = p.w != 0.f ? (float(p.iz + (sz > 0)) * P.dz - p.z) * iw : kInf;
+        float tb;
+        int ab;
+        if (tx <= ty && tx <= tz) { tb = tx; ab = 0; }
+        else if (ty <= tz) { tb = ty; ab = 1; }
+        else { tb = tz; ab = 2; }
+        tb = fmaxf(tb, 0.f);
+        const float rho = __ldg(&P.rho[vox]);
+        if (rho * tb >= left) {
+            const float t = left / rho;
+            p.x = fmaf(t, p.u, p.x);
+            p.y = fmaf(t, p.v, p.y);
+            p.z = fmaf(t, p.w, p.z);
+            if (!defer_last) {
+                tally(P, vox, dpm * left);
+                dep += dpm * left;
+            }
+            return false;
+        }
+        p.x = fmaf(tb, p.u, p.x);
+        p.y = fmaf(tb, p.v, p.y);
+        p.z = fmaf(tb, p.w, p.z);
+        const float piece = rho * tb;
+        if (piece > 0.f) {
+            tally(P, vox, dpm * piece);
+            dep += dpm * piece;
+        }
+        left -= piece;
+        ++crossings;
+        if (ab == 0) {
+            p.ix += sx;
+            if (p.ix < 0 || p.ix >= P.nx) return true;
+            vox += sx;
+        } else if (ab == 1) {
+            p.iy += sy;
+            if (p.iy < 0 || p.iy >= P.ny) return true;
+            vox = sy > 0 ? vox + P.nx : vox - P.nx;
+        } else {
+            p.iz += sz;
+            if (p.iz < 0 || p.iz >= P.nz) return true;
+            const uint32_t plane = uint32_t(P.nx) * uint32_t(P.ny);
+            vox = sz > 0 ? vox + plane : vox - plane;
+        }
+    }
+    atomicOr(P.status, ST_ITER_CAP);
+    return true;
+}
+
+// End of an electron or positron track inside the phantom: residual energy
+// deposited; a positron then annihilates into two back-to-back 0.511 MeV
+// photons (isotropic), or its rest energy is discarded (Sec. 2.1, Sec. 4).
+__device__ void electron_absorb(const SimParams& P, const PhaseArgs& A, Part& p, Acc& acc,
+                                uint32_t* s_cnt) {
+    tally(P, vox_of(P, p.ix, p.iy, p.iz), p.E);
+    count_event(s_cnt, C_EL_TERMINATED);
+    if (!(p.flags & kPositron)) return;
+    if (!P.S.annihilation) {
+        acc.disc += 2.0 * kMC2;
+        return;
+    }
+    const float4 a = draw(p, P.key0, P.key1);
+    const float cost = 2.f * a.x - 1.f;
+    const float sint = sqrtf(fmaxf(0.f, 1.f - cost * cost));
+    float cp, sp;
+    cossin_2pi(a.y, cp, sp);
+    const float dx = sint * cp, dy = sint * sp, dz = cost;
+    count_event(s_cnt, C_ANNIHIL);
+    bank(P, A.out_ph, A.out_ph_count, p, true, false, kMC2f, p.x, p.y, p.z, dx, dy, dz, s_cnt);
+    bank(P, A.out_ph, A.out_ph_count, p, true, false, kMC2f, p.x, p.y, p.z, -dx, -dy, -dz, s_cnt);
+}
+
+__device__ void electron_escape(const SimParams& P, Part& p, float energy, Acc& acc,
+                                uint32_t* s_cnt) {
+    double e = energy;
+    if (p.flags & kPositron) {
+        if (P.S.annihilation) e += 2.0 * kMC2;
+        else acc.disc += 2.0 * kMC2;
+    }
+    acc.esc += e;
+    hist_add(P, p.hist, 0, e);
+    count_event(s_cnt, C_EL_TERMINATED);
+}
+
+__device__ void electron_step(const SimParams& P, const PhaseArgs& A, const ElSmem& S, Part& p,
+                              bool& active, Acc& acc, uint32_t* s_cnt) {
+    const DevTables& T = P.T;
+    if (p.E < T.eabs_el) {
+        electron_absorb(P, A, p, acc, s_cnt);
+        active = false;
+        return;
+    }
+    const float4 r = draw(p, P.key0, P.key1);
+    count_event(s_cnt, C_EL_STEPS);
+    hist_count(P, p.hist, 1);
+    const int m = __ldg(&P.mat[vox_of(P, p.ix, p.iy, p.iz)]);
+    int i;
+    float f;
+    grid_pos(T, p.E, i, f);
+    const int mi = m * T.n_e + i;
+    float4 a0 = S.el[mi], a1 = S.el[mi + 1];
+    // step limits as mass thickness in the start material: reach E_abs,
+    // hard-event candidate, or the multiple-scattering step
+    const float R0 = lerpf(a0.x, a1.x, f);
+    const float xms = lerpf(a0.y, a1.y, f);
+    const float xcut = R0 - T.r_eabs[m];
+    const float xhard = (T.flags & GDPM_FLAG_NO_HARD) ? kInf : -__logf(r.x) * T.inv_sigmax[m];
+    int ev;
+    float xs;
+    if (xcut <= xms && xcut <= xhard) { ev = 0; xs = xcut; }
+    else if (xhard <= xms) { ev = 1; xs = xhard; }
+    else { ev = 2; xs = xms; }
+    xs = fmaxf(xs, 0.f);
+    float Tend;
+    if (ev == 0) {
+        Tend = T.eabs_el;
+    } else {
+        const float rr = (R0 - xs - T.rinv_lo[m]) * T.rinv_idr[m];
+        const int j = min(max(int(floorf(rr)), 0), T.n_r - 2);
+        const float g = fminf(fmaxf(rr - float(j), 0.f), 1.f);
+        const float* ri = S.rinv + m * T.n_r;
+        Tend = fminf(lerpf(ri[j], ri[j + 1], g), p.E);
+    }
+    const float Tk = p.E;
+    const float dT = Tk - Tend;
+    if (P.hrec) hist_add(P, p.hist, 1, double(xs));
+    // multiple scattering at the mid-step energy
+    const float Tm = 0.5f * (Tk + Tend);
+    const float pbc = Tm * (Tm + 2.f * kMC2f) / (Tm + kMC2f);
+    const float q = kEs / pbc;
+    const float G1 = xs * q * q * 0.5f * T.inv_x0[m];
+    float mu;
+    if (G1 >= 1.f) {
+        mu = 2.f * r.z - 1.f;
+    } else {
+        const float Asc = screening_A(T, S.atab, G1);
+        mu = 1.f - 2.f * Asc * r.z / (1.f - r.z + Asc);
+    }
+    float cp, sp;
+    cossin_2pi(r.w, cp, sp);
+    const float dpm = xs > 0.f ? dT / xs : 0.f;
+    float dep = 0.f;
+    uint32_t crossings = 0;
+    // random hinge: zeta*xs straight, deflect, (1-zeta)*xs straight
+    const bool out1 = walk(P, p, r.y * xs, dpm, dep, false, crossings);
+    if (crossings) atomicAdd(&s_cnt[C_CROSS], crossings);
+    crossings = 0;
+    if (out1) {
+        electron_escape(P, p, Tk - dep, acc, s_cnt);
+        active = false;
+        return;
+    }
+    rotate(p.u, p.v, p.w, mu, cp, sp);
+    const bool out2 = walk(P, p, (1.f - r.y) * xs, dpm, dep, true, crossings);
+    if (crossings) atomicAdd(&s_cnt[C_CROSS], crossings);
+    if (out2) {
+        electron_escape(P, p, Tk - dep, acc, s_cnt);
+        active = false;
+        return;
+    }
+    tally(P, vox_of(P, p.ix, p.iy, p.iz), dT - dep);
+    p.E = Tend;
+    if (ev == 0) {
+        electron_absorb(P, A, p, acc, s_cnt);
+        active = false;
+        return;
+    }
+    if (ev != 1) return;
+    // hard-event candidate: accept with Sigma_h(T)/Sigma_max (start material)
+    const float4 v = draw(p, P.key0, P.key1);
+    const float Tn = p.E, wcc = T.eabs_el, wcb = T.eabs_ph;
+    float sm = 0.f, sb = 0.f;
+    if (Tn > wcb || Tn > 2.f * wcc) {
+        grid_pos(T, Tn, i, f);
+        const int mj = m * T.n_e + i;
+        a0 = S.el[mj];
+        a1 = S.el[mj + 1];
+        if (Tn > 2.f * wcc) sm = lerpf(a0.z, a1.z, f);
+        if (Tn > wcb) sb = lerpf(a0.w, a1.w, f);
+    }
+    const float sh = sm + sb;
+    if (!(v.x * T.sigmax[m] < sh)) return;
+    hist_count(P, p.hist, 2);
+    if (v.y * sh < sm) {
+        count_event(s_cnt, C_MOLLER);
+        float eps, rphi;
+        sample_moller(p, P, Tn, wcc, eps, rphi);
+        float c, s;
+        cossin_2pi(rphi, c, s);
+        const float W = eps * Tn, Tp = Tn - W;
+        const float cd = sqrtf(W * (Tn + 2.f * kMC2f) / (Tn * (W + 2.f * kMC2f)));
+        const float cpr = sqrtf(Tp * (Tn + 2.f * kMC2f) / (Tn * (Tp + 2.f * kMC2f)));
+        float du = p.u, dv = p.v, dw = p.w;
+        rotate(du, dv, dw, cd, c, s);
+        bank(P, A.out_el, A.out_el_count, p, false, false, W, p.x, p.y, p.z, du, dv, dw, s_cnt);
+        rotate(p.u, p.v, p.w, cpr, -c, -s);
+        p.E = Tp;
+    } else {
+        count_event(s_cnt, C_BREMS);
+        const float k = wcb * exp2f(v.z * __log2f(Tn / wcb));
+        bank(P, A.out_ph, A.out_ph_count, p, true, false, k, p.x, p.y, p.z, p.u, p.v, p.w, s_cnt);
+        p.E = Tn - k;
+    }
+}
+
+// ---------------------------------------------------------------- phase kernel
+__device__ __forceinline__ void copy_to_smem(void* dst, const void* src, size_t bytes) {
+    const float4* s = static_cast<const float4*>(src);
+    float4* d = static_cast<float4*>(dst);
+    const size_t n4 = bytes / 16;
+    for (size_t k = threadIdx.x; k < n4; k += blockDim.x) d[k] = __ldg(&s[k]);
+    const size_t rem = bytes - n4 * 16;
+    const unsigned char* sb = static_cast<const unsigned char*>(src) + n4 * 16;
+    unsigned char* db = static_cast<unsigned char*>(dst) + n4 * 16;
+    for (size_t k = threadIdx.x; k < rem; k += blockDim.x) db[k] = sb[k];
+}
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+template <int PT>
+__global__ void __launch_bounds__(256) k_phase(const SimParams P, const PhaseArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t n_in = A.in_count ? min(*A.in_count, A.in.capacity) : 0u;
+    const uint32_t total = A.n_src + n_in;
+    if (total == 0u || blockIdx.x * blockDim.x >= total) return;
+
+    const DevTables& T = P.T;
+    const size_t ne = size_t(T.n_mat) * T.n_e;
+    PhSmem ps{};
+    ElSmem es{};
+    uint32_t* s_cnt;
+    if (PT == 0) {
+        float2* cum = reinterpret_cast<float2*>(smem);
+        float* tot = reinterpret_cast<float*>(smem + align16(ne * 8));
+        float* maj = reinterpret_cast<float*>(smem + align16(ne * 8) + align16(ne * 4));
+        s_cnt = reinterpret_cast<uint32_t*>(smem + align16(ne * 8) + align16(ne * 4) +
+                                            align16(size_t(T.n_e) * 4));
+        copy_to_smem(cum, T.ph_cum, ne * 8);
+        copy_to_smem(tot, T.ph_tot, ne * 4);
+        copy_to_smem(maj, P.maj, size_t(T.n_e) * 4);
+        ps.maj = maj; ps.tot = tot; ps.cum = cum;
+    } else {
+        float4* el = reinterpret_cast<float4*>(smem);
+        float* rinv = reinterpret_cast<float*>(smem + ne * 16);
+        const size_t nr = size_t(T.n_mat) * T.n_r;
+        float* atab = reinterpret_cast<float*>(smem + ne * 16 + align16(nr * 4));
+        s_cnt = reinterpret_cast<uint32_t*>(smem + ne * 16 + align16(nr * 4) +
+                                            align16(size_t(T.n_a) * 4));
+        copy_to_smem(el, T.el, ne * 16);
+        copy_to_smem(rinv, T.rinv, nr * 4);
+        copy_to_smem(atab, T.atab, size_t(T.n_a) * 4);
+        es.el = el; es.rinv = rinv; es.atab = atab;
+    }
+    for (int k = threadIdx.x; k < C_NCOUNT; k += blockDim.x) s_cnt[k] = 0u;
+    __syncthreads();
+
+    Acc acc{0.0, 0.0, 0.0};
+    Part p{};
+    bool active = false, exhausted = false;
+    const uint32_t lane = lane_id();
+    for (uint32_t it = 0;; ++it) {
+        const bool need = !active && !exhausted;
+        const uint32_t nm = __ballot_sync(0xffffffffu, need);
+        if (nm) {
+            const int leader = __ffs(nm) - 1;
+            uint32_t base = 0;
+            if (int(lane) == leader) base = atomicAdd(A.head, uint32_t(__popc(nm)));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (need) {
+                const uint32_t idx = base + __popc(nm & lanemask_lt());
+                if (idx < A.n_src) {
+                    active = make_primary(P, A, idx, PT == 0, p, acc, s_cnt);
+                } else if (idx < total) {
+                    queue_load(A.in, idx - A.n_src, p);
+                    count_event(s_cnt, PT == 0 ? C_POP_PH : C_POP_EL);
+                    active = true;
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (__all_sync(0xffffffffu, exhausted)) break;
+        if (it >= P.max_iters) {
+            if (lane == 0) atomicOr(P.status, ST_ITER_CAP);
+            break;
+        }
+        if (active) {
+            if (PT == 0) photon_step(P, A, ps, p, active, acc, s_cnt);
+            else electron_step(P, A, es, p, active, acc, s_cnt);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.src += __shfl_down_sync(0xffffffffu, acc.src, o);
+        acc.esc += __shfl_down_sync(0xffffffffu, acc.esc, o);
+        acc.disc += __shfl_down_sync(0xffffffffu, acc.disc, o);
+    }
+    if (lane == 0) {
+        if (acc.src != 0.0) atomicAdd(&P.ledger[L_SOURCE], acc.src);
+        if (acc.esc != 0.0) atomicAdd(&P.ledger[L_ESCAPED], acc.esc);
+        if (acc.disc != 0.0) atomicAdd(&P.ledger[L_DISCARDED], acc.disc);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < C_NCOUNT; k += blockDim.x)
+        if (s_cnt[k]) atomicAdd(&P.counters[k], (unsigned long long)s_cnt[k]);
+}
+
+// ---------------------------------------------------------------- checks
+__global__ void k_debug_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
+                               uint64_t n) {
+    for (uint64_t s = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; s < n;
+         s += uint64_t(gridDim.x) * blockDim.x) {
+        const uint4 c = make_uint4(ctr[4 * s], ctr[4 * s + 1], ctr[4 * s + 2], ctr[4 * s + 3]);
+        const uint4 o = philox4x32_10(c, k0, k1);
+        out[4 * s] = o.x; out[4 * s + 1] = o.y; out[4 * s + 2] = o.z; out[4 * s + 3] = o.w;
+    }
+}
+
+__global__ void k_debug_sample(int kind, float a, float b, uint64_t n, uint32_t k0, uint32_t k1,
+                               double* out1, double* out2) {
+    SimParams P{};
+    P.key0 = k0;
+    P.key1 = k1;
+    for (uint64_t s = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; s < n;
+         s += uint64_t(gridDim.x) * blockDim.x) {
+        Part p{};
+        p.hist = uint32_t(s);
+        p.pidlo = 1u;
+        double o1 = 0, o2 = 0;
+        if (kind == 0) {
+            float eps, cost, rphi;
+            sample_kn(p, P, a, eps, cost, rphi);
+            o1 = eps; o2 = cost;
+        } else if (kind == 1) {
+            float eps, rphi;
+            sample_moller(p, P, a, b, eps, rphi);
+            const float W = eps * a;
+            o1 = eps;
+            o2 = sqrtf(W * (a + 2.f * kMC2f) / (a * (W + 2.f * kMC2f)));
+        } else if (kind == 2) {
+            const float4 v = draw(p, k0, k1);
+            o1 = b * exp2f(v.z * __log2f(a / b));
+        } else if (kind == 3) {
+            const float4 r = draw(p, k0, k1);
+            o1 = 1.f - 2.f * a * r.z / (1.f - r.z + a);
+        } else {
+            const float4 r = draw(p, k0, k1);
+            o1 = 2.f * r.x - 1.f;
+            o2 = kTwoPi * r.y;
+        }
+        out1[s] = o1;
+        if (out2) out2[s] = o2;
+    }
+}
+
+__global__ void k_debug_sources(const SimParams P, const PhaseArgs A, uint64_t n, double* out) {
+    __shared__ uint32_t s_cnt[C_NCOUNT];
+    for (int k = threadIdx.x; k < C_NCOUNT; k += blockDim.x) s_cnt[k] = 0;
+    __syncthreads();
+    for (uint64_t s = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; s < n;
+         s += uint64_t(gridDim.x) * blockDim.x) {
+        Part p{};
+        Acc acc{0, 0, 0};
+        const bool in = make_primary(P, A, uint32_t(s), P.S.particle == GDPM_PHOTON, p, acc, s_cnt);
+        double* o = out + 8 * s;
+        o[0] = p.x; o[1] = p.y; o[2] = p.z; o[3] = p.u; o[4] = p.v; o[5] = p.w; o[6] = p.E;
+        o[7] = in ? 1.0 : 0.0;
+    }
+}
+
+}  // namespace
+
+static size_t smem_of(const DevTables& T, int particle) {
+    const size_t ne = size_t(T.n_mat) * T.n_e;
+    const size_t cnt = align16(C_NCOUNT * 4);
+    if (particle == GDPM_PHOTON)
+        return align16(ne * 8) + align16(ne * 4) + align16(size_t(T.n_e) * 4) + cnt;
+    return ne * 16 + align16(size_t(T.n_mat) * T.n_r * 4) + align16(size_t(T.n_a) * 4) + cnt;
+}
+
+int transport_smem(const gdpm_tables* t, int particle) { return int(smem_of(t->dev, particle)); }
+
+// Persistent grid: SM count x resident CTAs per SM for this shared-memory size.
+int launch_phase(gdpm_ctx* ctx, int particle, const SimParams& P, const PhaseArgs& A,
+                 uint32_t n_items_hint) {
+    const size_t smem = smem_of(P.T, particle);
+    const void* fn = particle == GDPM_PHOTON ? (const void*)k_phase<0> : (const void*)k_phase<1>;
+    GDPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int bps = ctx->blocks_per_sm;
+    if (bps <= 0) {
+        GDPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, ctx->block_threads, smem));
+        if (bps < 1) return GDPM_E_ARG;
+    }
+    uint32_t grid = uint32_t(ctx->sm_count) * uint32_t(bps);
+    if (n_items_hint > 0) {
+        const uint32_t need = (n_items_hint + ctx->block_threads - 1) / ctx->block_threads;
+        grid = need < grid ? need : grid;
+    }
+    if (grid == 0) grid = 1;
+    if (particle == GDPM_PHOTON)
+        k_phase<0><<<grid, ctx->block_threads, smem, ctx->stream>>>(P, A);
+    else
+        k_phase<1><<<grid, ctx->block_threads, smem, ctx->stream>>>(P, A);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+int launch_debug_philox(gdpm_ctx* ctx, const uint32_t* ctr, uint32_t k0, uint32_t k1,
+                        uint32_t* out, uint64_t n) {
+    const uint32_t grid = uint32_t(ctx->sm_count) * 4u;
+    k_debug_philox<<<grid, 256, 0, ctx->stream>>>(ctr, k0, k1, out, n);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+int launch_debug_sample(gdpm_ctx* ctx, int kind, double a, double b, uint64_t n, uint64_t seed,
+                        double* out1, double* out2) {
+    const uint32_t grid = uint32_t(ctx->sm_count) * 4u;
+    k_debug_sample<<<grid, 256, 0, ctx->stream>>>(kind, float(a), float(b), n, uint32_t(seed),
+                                                   uint32_t(seed >> 32), out1, out2);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+int launch_debug_sources(gdpm_ctx* ctx, const SimParams& P, const PhaseArgs& A, uint64_t n,
+                         double* out) {
+    const uint32_t grid = uint32_t(ctx->sm_count) * 2u;
+    k_debug_sources<<<grid, 256, 0, ctx->stream>>>(P, A, n, out);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+}  // namespace gdpm

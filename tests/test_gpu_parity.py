@@ -1,0 +1,345 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Element by element where the same random-number protocol makes the result
+deterministic (Philox words, table values, sampler draws, primaries, and
+per-history event records of same-seed runs); statistically where FP32
+versus FP64 arithmetic lets streams diverge (per-voxel t-test, Sec. 3.1);
+exactly for the integer bookkeeping inside the CUDA path.
+"""
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1107_3355_gb300 import gdpm as G
+from paper_1107_3355_gb300 import workloads as W
+from tests._stats import t_test
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def cuda_f64(n):
+    return torch.empty(n, dtype=torch.float64, device="cuda")
+
+
+def run_gpu(prob, params=None, records=False, seed=None):
+    eng = G.Engine(prob, params=params, seed=seed)
+    try:
+        rec = recd = None
+        if records:
+            rec = torch.zeros(prob.n_histories * 4, dtype=torch.int32, device="cuda")
+            recd = torch.zeros(prob.n_histories * 2, dtype=torch.float64, device="cuda")
+            G.gdpm_set_history_records(eng.ctx, rec, recd, prob.n_histories)
+        d, s, st = eng.run()
+        out = [d.cpu().numpy(), s.cpu().numpy(), st]
+        if records:
+            out += [rec.cpu().numpy().reshape(-1, 4), recd.cpu().numpy().reshape(-1, 2)]
+        return out
+    finally:
+        eng.close()
+
+
+def check_ledger(st, n_hist, tol):
+    bal = st["deposited"] + st["escaped"] + st["discarded"]
+    assert abs(bal - st["source_energy"]) <= tol * st["source_energy"], st
+    assert st["n_primary"] == n_hist
+    assert st["ph_created"] == st["ph_terminated"]
+    assert st["el_created"] == st["el_terminated"]
+    assert st["pushes"][0] == st["pops"][0]
+    assert st["pushes"][1] == st["pops"][1]
+
+
+# --------------------------------------------------------------------- RNG
+
+def test_philox_bitwise_vs_oracle():
+    ctx = G.gdpm_context_create(0)
+    try:
+        rng = np.random.default_rng(5)
+        n = 4096
+        ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+        k0, k1 = 0x12345678, 0x9ABCDEF0
+        dc = torch.from_numpy(ctr.reshape(-1).view(np.int32)).cuda()
+        out = torch.zeros(4 * n, dtype=torch.int32, device="cuda")
+        G.gdpm_debug_philox(ctx, dc, k0, k1, out, n)
+        got = out.cpu().numpy().view(np.uint32).reshape(n, 4)
+        ref = np.array([O.philox(c, [k0, k1]) for c in ctr])
+        assert np.array_equal(got, ref)
+    finally:
+        G.gdpm_context_destroy(ctx)
+
+
+def _curand_ref():
+    src = os.path.join(HERE, "cuda", "curand_philox_ref.cu")
+    lib = os.path.join(HERE, "cuda", "libcurandref.so")
+    if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+        subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+                               "-Xcompiler", "-fPIC", "-o", lib, src])
+    import ctypes
+    L = ctypes.CDLL(lib)
+    L.curand_philox_ref.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.c_int,
+                                    ctypes.c_void_p]
+    return L
+
+
+def test_oracle_philox_matches_curand_library():
+    """Pins the oracle's Philox4x32-10 against cuRAND's: curand_init(seed,
+    subsequence s) then the j-th curand4() is Philox(ctr=(j,0,s_lo,s_hi),
+    key=(seed_lo, seed_hi))."""
+    L = _curand_ref()
+    for seed, sub in [(0, 0), (12345, 0), (0xDEADBEEFCAFEBABE, 7), (42, 2 ** 40 + 3)]:
+        out = np.zeros(4 * 8, np.uint32)
+        assert L.curand_philox_ref(seed, sub, 8, out.ctypes.data) == 0
+        got = out.reshape(8, 4)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        ref = np.array([O.philox([j, 0, sub & 0xFFFFFFFF, sub >> 32], key) for j in range(8)])
+        assert np.array_equal(got, ref), (seed, sub)
+
+
+# --------------------------------------------------------------------- tables
+
+def test_tables_match_oracle():
+    prob = W.slab_photon_problem(n_histories=1000, shape=(8, 8, 128)).with_(e_max=21.0)
+    eng = G.Engine(prob)
+    try:
+        ref = O.tables(prob)
+        M, n = 3, prob.n_energy
+        want = {0: ref["mu_c"], 1: ref["mu_c"] + ref["mu_pe"],
+                2: ref["mu_c"] + ref["mu_pe"] + ref["mu_pair"], 3: ref["range"],
+                4: ref["sig_m"], 5: ref["sig_b"]}
+        for which, r in want.items():
+            cnt = G.gdpm_tables_export(eng.tables, which)
+            out = cuda_f64(cnt)
+            G.gdpm_tables_export(eng.tables, which, out)
+            got = out.cpu().numpy().reshape(M, n)
+            key = which
+            scale = np.abs(r).max(axis=1, keepdims=True)
+            err = np.abs(got - r) / np.maximum(np.abs(r), 1e-3 * scale)
+            assert err.max() < 2e-5, (key, err.max())
+        for which, key in {7: "x0", 8: "sigmax"}.items():
+            out = cuda_f64(M)
+            G.gdpm_tables_export(eng.tables, which, out)
+            np.testing.assert_allclose(out.cpu().numpy(), ref[key], rtol=1e-6)
+    finally:
+        eng.close()
+
+
+# --------------------------------------------------------------------- samplers
+
+@pytest.mark.parametrize("kind,a,b", [(0, 0.1, 0), (0, 1.0, 0), (0, 6.0, 0), (1, 1.0, 0.2),
+                                      (1, 15.0, 0.2), (2, 5.0, 0.05), (3, 0.01, 0), (4, 0, 0)])
+def test_samplers_elementwise(kind, a, b):
+    """Same Philox streams: the GPU sampler (FP32) reproduces the oracle's
+    (FP64) sample by sample, except where a rejection test flips."""
+    n = 100_000
+    ctx = G.gdpm_context_create(0)
+    try:
+        o1, o2 = cuda_f64(n), cuda_f64(n)
+        G.gdpm_debug_sample(ctx, kind, a, b, n, 777, o1, o2)
+        g1 = o1.cpu().numpy()
+        oracle_kind = {0: O.OS_KN, 1: O.OS_MOLLER, 2: O.OS_BREMS, 3: O.OS_SR, 4: O.OS_ISO}[kind]
+        r1, _ = O.sample(oracle_kind, a, b, n, seed=777)
+        # inputs differ by < 2^-23 (23-bit vs 32-bit uniforms) plus FP32 rounding
+        match = np.abs(g1 - r1) <= 2e-5 + 1e-4 * np.abs(r1)
+        print("sampler %d match %.6f" % (kind, match.mean()))
+        assert match.mean() > 0.999, match.mean()
+    finally:
+        G.gdpm_context_destroy(ctx)
+
+
+# --------------------------------------------------------------------- sources
+
+@pytest.mark.parametrize("which", ["field", "pencil"])
+def test_primaries_elementwise(which):
+    prob = W.slab_photon_problem(n_histories=100_000, n_batches=4)
+    if which == "pencil":
+        prob = W.tiny_problem(n_histories=100_000, n_batches=4)
+    n = 20000
+    eng = G.Engine(prob)
+    try:
+        out = cuda_f64(8 * n)
+        G.gdpm_debug_sources(eng.ctx, eng.phantom, eng.tables, prob.n_histories, prob.n_batches,
+                             0, n, out)
+        got = out.cpu().numpy().reshape(n, 8)
+    finally:
+        eng.close()
+    ref = O.sources(prob, 0, n)
+    np.testing.assert_array_equal(got[:, 7], ref[:, 7])
+    np.testing.assert_allclose(got[:, :3], ref[:, :3], atol=2e-5)
+    np.testing.assert_allclose(got[:, 3:6], ref[:, 3:6], atol=2e-6)
+    np.testing.assert_allclose(got[:, 6], ref[:, 6], rtol=2e-6)
+
+
+# --------------------------------------------------------------------- transport
+
+def test_tiny_pencil_same_seed_elementwise():
+    """1 MeV pencil, 32^3 water: same seed -> same histories.  Per-history
+    integer records agree for almost every history; dose passes the t-test."""
+    prob = W.tiny_problem(n_histories=100_000)
+    d_o, s_o, led_o, rec_o, recd_o = O.run(prob, per_history=True)
+    d_g, s_g, st, rec_g, recd_g = run_gpu(prob, records=True)
+    check_ledger(st, prob.n_histories, 1e-5)
+    same = np.all(rec_o == rec_g, axis=1)
+    print("identical history records: %.5f" % same.mean())
+    assert same.mean() > 0.98
+    esc_ok = np.abs(recd_o[same, 0] - recd_g[same, 0]) <= 1e-4 * np.maximum(recd_o[same, 0], 1e-3)
+    assert esc_ok.mean() > 0.99
+    r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
+    print("same-seed t-test", r)
+    assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97
+    assert abs(r["bias"]) < 0.005
+    for k in ["compton", "photoelectric", "el_steps", "moller", "brems"]:
+        assert st[k] == pytest.approx(led_o[k], rel=0.02, abs=30), k
+
+
+def test_tiny_pencil_independent_seeds():
+    """Independent streams: the per-voxel |t| <= 2 pass rate over the high-dose
+    region is a binomial around 0.953 (N_b = 100); accept down to 4 sigma."""
+    prob = W.tiny_problem(n_histories=200_000, seed=1)
+    d_o, s_o, _ = O.run(prob)
+    d_g, s_g, st = run_gpu(prob.with_(seed=99))
+    r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
+    print("independent t-test", r)
+    floor = 0.953 - 4 * math.sqrt(0.953 * 0.047 / r["n_high"])
+    assert r["P_high"] >= floor
+    assert r["P_all"] >= 0.97
+    # signed bias over the high-dose region within 4 standard errors
+    high = d_o > 0.1 * max(d_o.max(), d_g.max())
+    se = math.sqrt(np.sum(s_o[high] ** 2 + s_g[high] ** 2)) / np.sum(d_o[high])
+    assert abs(r["bias"]) <= max(4 * se, 1e-3)
+
+
+def test_slab_photon_same_seed():
+    prob = W.slab_photon_problem(n_histories=40_000, n_batches=20, shape=(64, 64, 128))
+    d_o, s_o, led_o, rec_o, _ = O.run(prob, per_history=True)
+    d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
+    check_ledger(st, prob.n_histories, 1e-5)
+    same = np.all(rec_o == rec_g, axis=1)
+    print("slab photon identical records: %.5f" % same.mean())
+    assert same.mean() > 0.97
+    r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
+    print("slab photon t-test", r)
+    assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97
+
+
+def test_slab_electron_same_seed():
+    prob = W.slab_electron_problem(n_histories=4_000, n_batches=20, shape=(64, 64, 128))
+    d_o, s_o, led_o, rec_o, _ = O.run(prob, per_history=True)
+    d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
+    check_ledger(st, prob.n_histories, 1e-5)
+    same = np.all(rec_o == rec_g, axis=1)
+    print("slab electron identical records: %.5f" % same.mean())
+    assert same.mean() > 0.9
+    r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
+    print("slab electron t-test", r)
+    assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97
+
+
+def test_tally_modes_agree():
+    prob = W.tiny_problem(n_histories=50_000)
+    d64, _, st64 = run_gpu(prob)
+    d32, _, st32 = run_gpu(prob, params={G.GDPM_PARAM_TALLY_MODE: 1})
+    np.testing.assert_allclose(d32, d64, rtol=1e-9, atol=1e-12 * d64.max())
+    assert st32["compton"] == st64["compton"]
+
+
+def test_warp_aggregated_tally_agrees():
+    prob = W.tiny_problem(n_histories=50_000)
+    d0, _, _ = run_gpu(prob)
+    d1, _, _ = run_gpu(prob, params={G.GDPM_PARAM_WARP_AGGREGATE: 1})
+    np.testing.assert_allclose(d1, d0, rtol=1e-9, atol=1e-12 * d0.max())
+
+
+def test_host_outputs_equal_device_outputs():
+    prob = W.tiny_problem(n_histories=20_000, n_batches=10)
+    eng = G.Engine(prob)
+    try:
+        d, s, _ = eng.run()
+        hd = np.zeros(prob.phantom.n_voxels)
+        hs = np.zeros(prob.phantom.n_voxels)
+        G.gdpm_simulate(eng.ctx, eng.phantom, eng.tables, prob.n_histories, prob.n_batches, hd, hs)
+        np.testing.assert_allclose(hd, d.cpu().numpy(), rtol=1e-12, atol=0)
+        np.testing.assert_allclose(hs, s.cpu().numpy(), rtol=1e-9, atol=1e-15)
+    finally:
+        eng.close()
+
+
+# --------------------------------------------------------------------- failure paths
+
+def test_queue_overflow_reported():
+    prob = W.tiny_problem(n_histories=20_000, n_batches=2)
+    eng = G.Engine(prob, params={G.GDPM_PARAM_QUEUE_CAPACITY: 64})
+    try:
+        with pytest.raises(G.GdpmError) as e:
+            eng.run()
+        assert e.value.code == G.GDPM_E_QUEUE_OVERFLOW
+    finally:
+        eng.close()
+
+
+def test_phase_cap_reported():
+    prob = W.slab_electron_problem(n_histories=2000, n_batches=2, shape=(32, 32, 128))
+    eng = G.Engine(prob, params={G.GDPM_PARAM_MAX_PHASES: 8})
+    try:
+        with pytest.raises(G.GdpmError) as e:
+            eng.run()
+        assert e.value.code == G.GDPM_E_TIMEOUT
+    finally:
+        eng.close()
+
+
+def test_bad_inputs_rejected():
+    prob = W.tiny_problem(n_histories=1000, n_batches=10)
+    eng = G.Engine(prob)
+    try:
+        with pytest.raises(G.GdpmError):
+            G.gdpm_simulate(eng.ctx, eng.phantom, eng.tables, 1000, 1)
+        with pytest.raises(G.GdpmError):
+            G.gdpm_simulate(eng.ctx, eng.phantom, eng.tables, 5, 10)
+        bad_mat = prob.phantom.mat.copy()
+        bad_mat[7] = 3
+        ph = G.gdpm_phantom_create(eng.ctx, prob.phantom.shape, prob.phantom.voxel, bad_mat,
+                                   prob.phantom.rho)
+        with pytest.raises(G.GdpmError) as e:
+            G.gdpm_simulate(eng.ctx, ph, eng.tables, 1000, 10)
+        assert e.value.code == G.GDPM_E_ARG
+        G.gdpm_phantom_destroy(ph)
+        bad_rho = prob.phantom.rho.copy()
+        bad_rho[3] = 0.0
+        with pytest.raises(G.GdpmError):
+            G.gdpm_phantom_create(eng.ctx, prob.phantom.shape, prob.phantom.voxel,
+                                  prob.phantom.mat, bad_rho)
+        hot = W.Source(W.PHOTON, W.mono_spectrum(5.0), "pencil", (8, 8, 0), (0, 0, 1))
+        G.gdpm_source_set(eng.ctx, hot)          # 5 MeV is beyond this table grid (1.5 MeV)
+        with pytest.raises(G.GdpmError):
+            G.gdpm_simulate(eng.ctx, eng.phantom, eng.tables, 1000, 10)
+    finally:
+        eng.close()
+
+
+# --------------------------------------------------------------------- full size
+
+def test_full_size_slab_sampled_histories():
+    """The 128^3 slab, 6 MV field, at the bench's launch configuration (1e7
+    histories here, same batches as the bench's per-batch size): sampled
+    histories compared one by one with the oracle, plus invariants that
+    hold at any size."""
+    prob = W.slab_photon_problem(n_histories=10_000_000, n_batches=10)
+    d_g, s_g, st, rec_g, recd_g = run_gpu(prob, records=True)
+    check_ledger(st, prob.n_histories, 1e-5)
+    rng = np.random.default_rng(0)
+    for first in sorted(rng.choice(prob.n_histories - 300, 4, replace=False)):
+        rec_o, recd_o = O.history_records(prob, int(first), 300)
+        same = np.all(rec_o == rec_g[first:first + 300], axis=1)
+        assert same.mean() > 0.95, (first, same.mean())
+    # x <-> y symmetry of the square field on the symmetric slab
+    g = prob.phantom.grid3(d_g)
+    gs = prob.phantom.grid3(s_g)
+    r = t_test(g.ravel(), gs.ravel(), np.swapaxes(g, 1, 2).ravel(), np.swapaxes(gs, 1, 2).ravel(),
+               high_frac=0.1)
+    assert r["P_high"] > 0.9
