@@ -258,6 +258,47 @@ int gdpm_tables_export(gdpm_tables *t, int which, double *out, int64_t *count);
 int gdpm_debug_sources(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
                        int n_batches, uint64_t first, uint64_t n, double *out);
 
+/* ------------------------------------------------------------------ no allocation */
+
+/* gdpm_simulate_noalloc -- the same dose calculation as gdpm_simulate, for
+ * small problems, without allocating any memory.  The paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc: code that
+ * runs while a CUDA graph is being captured (allocation is not allowed during
+ * stream capture), and host applications that hand all device memory to
+ * their own allocator and forbid libraries from allocating behind it.
+ *
+ * All work buffers (batch tally, batch sums, particle queues, counters,
+ * source arrays, Woodcock majorant) come from one file-scope device array of
+ * GDPM_NOALLOC_SCRATCH_BYTES (about 3.6 MB).  Every GPU that loads this
+ * library holds that array until the process exits.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) for that
+ * device; make that first call before any stream capture begins.
+ *
+ * Limits (GDPM_E_ARG beyond them): nx*ny*nz <= GDPM_NOALLOC_MAX_VOXELS, at
+ * most GDPM_NOALLOC_QUEUE_CAPACITY banked particles per queue fill (more is
+ * reported as GDPM_E_QUEUE_OVERFLOW), n_batches*(n_bins+1) <=
+ * GDPM_NOALLOC_MAX_PREFIX, n_beamlets <= GDPM_NOALLOC_MAX_BEAMLETS, table
+ * grid <= 8192 energies.  dose_out and sigma_out must be device arrays (or
+ * NULL); stats_out is a host struct (or NULL).  The phantom, tables and
+ * source are the caller's existing handles on this context; the context's
+ * per-history records and profiling are not used.  Results equal those of
+ * gdpm_simulate with the same seed up to the summation order of the FP64
+ * tallies.
+ *
+ * Every call on a device shares the one array, and it keeps the last call's
+ * contents (the call clears what must start at zero).  Calls whose work
+ * overlaps on the same GPU -- from two streams, two contexts or two threads
+ * -- race on that array and corrupt each other's results: run them one after
+ * another. */
+#define GDPM_NOALLOC_MAX_VOXELS 32768
+#define GDPM_NOALLOC_QUEUE_CAPACITY 16384
+#define GDPM_NOALLOC_MAX_PREFIX 65536
+#define GDPM_NOALLOC_MAX_BEAMLETS 1024
+#define GDPM_NOALLOC_SCRATCH_BYTES 3729408
+int gdpm_simulate_noalloc(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
+                          int n_batches, double *dose_out, double *sigma_out,
+                          gdpm_stats *stats_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -187,3 +187,37 @@ int launch_finalize(gdpm_ctx* ctx, const SimParams& P, size_t V, int n_batches, 
 }
 
 }  // namespace gdpm
+
+namespace gdpm {
+
+// Variants of the launchers above that take every buffer explicitly (used by
+// the no-allocation entry point, whose buffers live in a static array).
+int launch_majorant_into(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* t, float* maj) {
+    k_majorant<<<(t->n_e + 127) / 128, 128, 0, ctx->stream>>>(
+        static_cast<const float*>(t->ph_tot.p), static_cast<const float*>(ph->rhomax.p), t->n_mat,
+        t->n_e, maj);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+int launch_fold_into(gdpm_ctx* ctx, const SimParams& P, size_t V, uint32_t nb, double* s1, double* s2) {
+    k_fold<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(P, V, 1.0 / double(nb), s1, s2);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+int launch_finalize_into(gdpm_ctx* ctx, const SimParams& P, size_t V, int n_batches,
+                         const double* s1, const double* s2, double* dose, double* sigma) {
+    const double dvol = double(P.dx) * P.dy * P.dz;
+    unsigned long long* dmax_bits = reinterpret_cast<unsigned long long*>(&P.ledger[L_DMAX]);
+    k_finalize<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(s1, s2, P.rho, V, n_batches, dvol, dose,
+                                                             sigma, dmax_bits);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    if (dose && sigma) {
+        k_metric<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(dose, sigma, V, dmax_bits, P.ledger);
+        GDPM_CUDA_TRY(cudaGetLastError());
+    }
+    return GDPM_OK;
+}
+
+}  // namespace gdpm

@@ -33,7 +33,7 @@ EXPORTED = ["gdpm_context_create", "gdpm_context_destroy", "gdpm_set_param",
             "gdpm_tables_destroy", "gdpm_source_set", "gdpm_simulate",
             "gdpm_set_history_records", "gdpm_request_submit", "gdpm_request_poll",
             "gdpm_strerror", "gdpm_debug_philox", "gdpm_debug_sample", "gdpm_tables_export",
-            "gdpm_debug_sources"]
+            "gdpm_debug_sources", "gdpm_simulate_noalloc"]
 
 
 class gdpm_material_desc(C.Structure):
@@ -120,6 +120,7 @@ def lib():
                 "gdpm_debug_sample": [vp, i, d, d, u64, u64, vp, vp],
                 "gdpm_tables_export": [vp, i, vp, C.POINTER(C.c_int64)],
                 "gdpm_debug_sources": [vp, vp, vp, u64, i, u64, u64, vp],
+                "gdpm_simulate_noalloc": [vp, vp, vp, u64, i, vp, vp, C.POINTER(gdpm_stats)],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -289,6 +290,19 @@ def gdpm_tables_export(tables, which, out=None):
 def gdpm_debug_sources(ctx, phantom, tables, n_histories, n_batches, first, n, out):
     _check(lib().gdpm_debug_sources(ctx, phantom, tables, n_histories, n_batches, first, n,
                                     _ptr(out)), "gdpm_debug_sources")
+
+
+def gdpm_simulate_noalloc(ctx, phantom, tables, n_histories, n_batches, dose_out=None,
+                          sigma_out=None):
+    """gdpm_simulate for small problems without any allocation: every work
+    buffer lives in the library's fixed static device array (see gdpm.h for
+    the limits).  For callers that may not allocate device memory, such as
+    code running under CUDA graph capture.  dose_out/sigma_out: device arrays."""
+    st = gdpm_stats()
+    _check(lib().gdpm_simulate_noalloc(ctx, phantom, tables, n_histories, n_batches,
+                                       _ptr(dose_out), _ptr(sigma_out), C.byref(st)),
+           "gdpm_simulate_noalloc")
+    return st.as_dict()
 
 
 # ------------------------------------------------------------------ marshalling helper

@@ -1,0 +1,67 @@
+"""gdpm_simulate_noalloc: the dose calculation without any allocation.
+
+Some callers cannot call cudaMalloc -- code running while a CUDA graph is
+captured, or applications whose own allocator owns the GPU's memory -- so the
+library offers one entry point whose work buffers all live in a fixed static
+device array.  This file is named so that pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+from paper_1107_3355_gb300 import gdpm as G
+from paper_1107_3355_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_matches_simulate_on_two_calls():
+    prob = W.tiny_problem(n_histories=50_000, n_batches=10)
+    eng = G.Engine(prob)
+    try:
+        V = prob.phantom.n_voxels
+        d_ref, s_ref, st_ref = eng.run()
+        d_ref = d_ref.cpu().numpy()
+        s_ref = s_ref.cpu().numpy()
+        for call in range(2):
+            d = torch.full((V,), -1.0, dtype=torch.float64, device="cuda")
+            s = torch.full((V,), -1.0, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info()[0]
+            st = G.gdpm_simulate_noalloc(eng.ctx, eng.phantom, eng.tables, prob.n_histories,
+                                         prob.n_batches, d, s)
+            torch.cuda.synchronize()
+            free_after = torch.cuda.mem_get_info()[0]
+            if call == 1:   # the first call on a device may load the module
+                assert free_after == free_before
+            # same per-history random streams: equal up to FP64 summation order
+            np.testing.assert_allclose(d.cpu().numpy(), d_ref, rtol=1e-9,
+                                       atol=1e-12 * d_ref.max())
+            np.testing.assert_allclose(s.cpu().numpy(), s_ref, rtol=1e-6,
+                                       atol=1e-9 * s_ref.max())
+            for k in ("n_primary", "compton", "photoelectric", "el_steps", "moller", "brems",
+                      "el_created", "ph_created", "crossings"):
+                assert st[k] == st_ref[k], k
+            assert st["deposited"] == pytest.approx(st_ref["deposited"], rel=1e-12)
+            assert st["sigma_over_dmax"] == pytest.approx(st_ref["sigma_over_dmax"], rel=1e-6)
+    finally:
+        eng.close()
+
+
+def test_noalloc_rejects_sizes_beyond_its_limit():
+    prob = W.tiny_problem(n_histories=1000, n_batches=10)
+    eng = G.Engine(prob)
+    try:
+        big = W.homogeneous_phantom((40, 40, 40), (0.5, 0.5, 0.5))     # 64000 > 32768 voxels
+        ph = G.gdpm_phantom_create(eng.ctx, big.shape, big.voxel, big.mat, big.rho)
+        d = torch.empty(big.n_voxels, dtype=torch.float64, device="cuda")
+        with pytest.raises(G.GdpmError) as e:
+            G.gdpm_simulate_noalloc(eng.ctx, ph, eng.tables, 1000, 10, d, d)
+        assert e.value.code == G.GDPM_E_ARG
+        G.gdpm_phantom_destroy(ph)
+        host = np.zeros(prob.phantom.n_voxels)
+        with pytest.raises(G.GdpmError) as e:
+            G.gdpm_simulate_noalloc(eng.ctx, eng.phantom, eng.tables, 1000, 10, host, host)
+        assert e.value.code == G.GDPM_E_ARG
+    finally:
+        eng.close()
