@@ -137,7 +137,8 @@ enum {
     GDPM_PARAM_REQUEST_ID = 7,       /* xored into the Philox key high word */
     GDPM_PARAM_SPECULATIVE = 8,      /* phase pairs issued per host check (>=1) */
     GDPM_PARAM_WARP_AGGREGATE = 9,   /* 1: merge same-voxel deposits within a warp */
-    GDPM_PARAM_PROFILE = 10          /* 1: time every launch with CUDA events (stats kernel_ms) */
+    GDPM_PARAM_PROFILE = 10,         /* 1: time every launch with CUDA events (stats kernel_ms) */
+    GDPM_PARAM_OVERLAP_FOLD = 11     /* 1 (default): fold batch b while batch b+1 runs */
 };
 
 /* ------------------------------------------------------------------ inputs */

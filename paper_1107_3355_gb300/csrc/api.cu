@@ -221,9 +221,11 @@ static int prepare_workspace(gdpm_ctx* ctx, size_t V, uint32_t cap, int n_batche
     int rc;
     if ((rc = ensure(ws.s1, V * 8)) || (rc = ensure(ws.s2, V * 8))) return rc;
     if (ctx->tally_mode == 0) {
-        if ((rc = ensure(ws.edep, V * 8))) return rc;
+        if ((rc = ensure(ws.edep, V * 8)) || (rc = ensure(ws.edep2, V * 8))) return rc;
     } else {
-        if ((rc = ensure(ws.hi, V * 4)) || (rc = ensure(ws.lo, V * 4))) return rc;
+        if ((rc = ensure(ws.hi, V * 4)) || (rc = ensure(ws.lo, V * 4)) || (rc = ensure(ws.hi2, V * 4)) ||
+            (rc = ensure(ws.lo2, V * 4)))
+            return rc;
     }
     const size_t qb = size_t(cap) * kQueueWords * 4;
     if ((rc = ensure(ws.qph, qb)) || (rc = ensure(ws.qel0, qb)) || (rc = ensure(ws.qel1, qb))) return rc;
@@ -309,6 +311,14 @@ static int run_batch(gdpm_ctx* ctx, const SimParams& P, const gdpm_source_state&
     return GDPM_OK;
 }
 
+// Point P's batch tally at buffer `which` (0 or 1).
+static void select_tally(gdpm_ctx* ctx, SimParams& P, int which) {
+    Workspace& ws = ctx->ws;
+    P.edep = static_cast<double*>(which ? ws.edep2.p : ws.edep.p);
+    P.edep_hi = static_cast<float*>(which ? ws.hi2.p : ws.hi.p);
+    P.edep_lo = static_cast<float*>(which ? ws.lo2.p : ws.lo.p);
+}
+
 static void fill_stats(const unsigned long long* c, const double* l, gdpm_stats* st) {
     st->source_energy = l[L_SOURCE];
     st->deposited = l[L_DEPOSITED];
@@ -364,9 +374,7 @@ int simulate_impl(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const gdpm_s
     GDPM_CUDA_TRY(cudaMemcpyAsync(ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     SimParams P = base_params(ctx, ph, tb, request_id);
     if ((rc = source_upload(ctx, src, P.S))) return rc;
-    P.edep = static_cast<double*>(ws.edep.p);
-    P.edep_hi = static_cast<float*>(ws.hi.p);
-    P.edep_lo = static_cast<float*>(ws.lo.p);
+    select_tally(ctx, P, 0);
     P.counters = static_cast<unsigned long long*>(ws.counters.p);
     P.ledger = static_cast<double*>(ws.ledger.p);
     P.status = static_cast<uint32_t*>(ws.status.p);
@@ -378,9 +386,12 @@ int simulate_impl(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const gdpm_s
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.s2.p, 0, V * 8, s));
     if (ctx->tally_mode == 0) {
         GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep.p, 0, V * 8, s));
+        GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep2.p, 0, V * 8, s));
     } else {
         GDPM_CUDA_TRY(cudaMemsetAsync(ws.hi.p, 0, V * 4, s));
         GDPM_CUDA_TRY(cudaMemsetAsync(ws.lo.p, 0, V * 4, s));
+        GDPM_CUDA_TRY(cudaMemsetAsync(ws.hi2.p, 0, V * 4, s));
+        GDPM_CUDA_TRY(cudaMemsetAsync(ws.lo2.p, 0, V * 4, s));
     }
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.counters.p, 0, C_NCOUNT * 8, s));
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.ledger.p, 0, L_NLEDGER * 8, s));
@@ -394,19 +405,37 @@ int simulate_impl(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const gdpm_s
     int64_t phases = 0;
     uint64_t first = 0;
     int run_rc = GDPM_OK;
+    // Batch b tallies into buffer b%2.  Its fold runs on the side stream
+    // while batch b+1 transports into the other buffer; batch b+2 waits for
+    // that fold before reusing the buffer.
+    cudaStream_t side = ctx->overlap_fold ? ctx->side : s;
+    GDPM_CUDA_TRY(cudaEventRecord(ctx->fold_done[0], s));
+    GDPM_CUDA_TRY(cudaEventRecord(ctx->fold_done[1], s));
     for (int b = 0; b < n_batches && run_rc == GDPM_OK; ++b) {
         const uint64_t nb = n_hist / n_batches + (uint64_t(b) < n_hist % n_batches ? 1 : 0);
+        const int buf = ctx->overlap_fold ? (b & 1) : 0;
+        select_tally(ctx, P, buf);
+        GDPM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fold_done[buf], 0));
         run_rc = run_batch(ctx, P, src, b, nb, first, chunk, phases);
         if (run_rc == GDPM_OK) {
+            GDPM_CUDA_TRY(cudaEventRecord(ctx->batch_done[buf], s));
+            GDPM_CUDA_TRY(cudaStreamWaitEvent(side, ctx->batch_done[buf], 0));
+            cudaStream_t keep = ctx->stream;
+            ctx->stream = side;
             const size_t pi = prof_begin(ctx, 2);
             run_rc = launch_fold(ctx, P, V, uint32_t(nb));
             prof_end(ctx, pi);
+            ctx->stream = keep;
+            GDPM_CUDA_TRY(cudaEventRecord(ctx->fold_done[buf], side));
         }
         first += nb;
     }
+    GDPM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fold_done[0], 0));
+    GDPM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fold_done[1], 0));
     GDPM_CUDA_TRY(cudaEventRecord(ctx->ev1, s));
     if (run_rc != GDPM_OK) {
         cudaStreamSynchronize(s);
+        cudaStreamSynchronize(ctx->side);
         ctx->prof_kind.clear();
         return run_rc;
     }
@@ -487,6 +516,15 @@ int gdpm_context_create(gdpm_ctx** out, int device, void* cuda_stream, uint64_t 
         return GDPM_E_CUDA;
     }
     c->sm_count = prop.multiProcessorCount;
+    bool ok = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k)
+        ok = cudaEventCreateWithFlags(&c->batch_done[k], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->fold_done[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        last_cuda_error() = cudaGetLastError();
+        gdpm_context_destroy(c);
+        return GDPM_E_CUDA;
+    }
     *out = c;
     return GDPM_OK;
 }
@@ -503,13 +541,19 @@ int gdpm_context_destroy(gdpm_ctx* ctx) {
     }
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
     Workspace& w = ctx->ws;
-    Buffer* bs[] = {&w.edep, &w.s1, &w.s2, &w.hi, &w.lo, &w.qph, &w.qel0, &w.qel1, &w.ctl,
+    Buffer* bs[] = {&w.edep, &w.edep2, &w.hi2, &w.lo2, &w.s1, &w.s2, &w.hi, &w.lo, &w.qph, &w.qel0, &w.qel1, &w.ctl,
                     &w.prefix, &w.counters, &w.ledger, &w.status, &w.edges, &w.beamlets,
                     &w.bl_cdf, &w.stage};
     for (Buffer* b : bs) release(*b);
     if (w.pinned_host.p) cudaFreeHost(w.pinned_host.p);
     for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->batch_done[k]) cudaEventDestroy(ctx->batch_done[k]);
+        if (ctx->fold_done[k]) cudaEventDestroy(ctx->fold_done[k]);
+    }
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -554,6 +598,10 @@ int gdpm_set_param(gdpm_ctx* ctx, int param, double v) {
     case GDPM_PARAM_WARP_AGGREGATE:
         if (v != 0 && v != 1) return GDPM_E_ARG;
         ctx->warp_aggregate = int(v);
+        return GDPM_OK;
+    case GDPM_PARAM_OVERLAP_FOLD:
+        if (v != 0 && v != 1) return GDPM_E_ARG;
+        ctx->overlap_fold = int(v);
         return GDPM_OK;
     case GDPM_PARAM_PROFILE:
         if (v != 0 && v != 1) return GDPM_E_ARG;

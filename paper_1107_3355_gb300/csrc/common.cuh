@@ -189,6 +189,13 @@ __device__ __forceinline__ uint32_t reserve_slot(uint32_t* tail) {
     return base + g.thread_rank();
 }
 
+// Add a per-thread count n, one shared atomic per group of converged threads.
+__device__ __forceinline__ void count_n(uint32_t* s_counts, int slot, uint32_t n) {
+    const uint32_t mask = __activemask();
+    const uint32_t tot = __reduce_add_sync(mask, n);
+    if (int(lane_id()) == __ffs(mask) - 1 && tot) atomicAdd(&s_counts[slot], tot);
+}
+
 // Count an event once per calling thread, one shared atomic per group.
 __device__ __forceinline__ void count_event(uint32_t* s_counts, int slot) {
     cg::coalesced_group g = cg::coalesced_threads();

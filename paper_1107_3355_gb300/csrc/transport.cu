@@ -25,6 +25,11 @@ namespace gdpm {
 namespace {
 
 constexpr float kInf = FLT_MAX;
+
+#ifndef GDPM_MIN_CTAS
+#define GDPM_MIN_CTAS 4
+#endif
+
 constexpr float kEs = 21.2f;            // Rossi-Greisen scattering energy, MeV
 
 // ---------------------------------------------------------------- ledger/tally
@@ -77,34 +82,48 @@ __device__ __forceinline__ void hist_add(const SimParams& P, uint32_t hist, int 
 }
 
 // Bank a secondary in queue q (Sec. 2.2.1 stacks).  Electrons and photons
-// below their absorption energy are deposited on the spot; positrons are
-// always banked.  The child's Philox stream is keyed by a counter-derived
-// id, so it does not depend on when or where it is transported.
-__device__ void bank(const SimParams& P, const Queue& q, uint32_t* tail, Part& parent, bool photon,
-                     bool positron, float E, float x, float y, float z, float u, float v, float w,
-                     uint32_t* s_cnt) {
+// below their absorption energy are deposited on the spot (returns false);
+// positrons are always banked.  The child's Philox stream is keyed by a
+// counter-derived id (parent id, child index), so it does not depend on when
+// or where the child is transported.  Kept inline: its warp-synchronous slot
+// reservation needs the caller's converged lane set, which an out-of-line call
+// does not preserve (measured: an out-of-line version lost and duplicated
+// queue slots).
+__device__ __forceinline__ bool bank(const SimParams& P, const Queue& q, uint32_t* tail,
+                                  uint32_t hist, uint32_t pidlo, uint32_t pidhi, uint32_t child,
+                                  int ix, int iy, int iz, bool photon, bool positron, float E,
+                                  float x, float y, float z, float u, float v, float w,
+                                  uint32_t* s_cnt) {
     if (!positron && E < (photon ? P.T.eabs_ph : P.T.eabs_el)) {
-        tally(P, vox_of(P, parent.ix, parent.iy, parent.iz), E);
+        tally(P, vox_of(P, ix, iy, iz), E);
         count_event(s_cnt, C_LOCAL_DEP);
-        return;
+        return false;
     }
     Part c;
     c.x = x; c.y = y; c.z = z; c.u = u; c.v = v; c.w = w; c.E = E;
-    c.ix = parent.ix; c.iy = parent.iy; c.iz = parent.iz;
-    c.hist = parent.hist;
-    const uint64_t id = child_id(uint64_t(parent.pidlo) | (uint64_t(parent.pidhi) << 32),
-                                 parent.flags & 0xFFFFFFu);
+    c.ix = ix; c.iy = iy; c.iz = iz;
+    c.hist = hist;
+    const uint64_t id = child_id(uint64_t(pidlo) | (uint64_t(pidhi) << 32), child);
     c.pidlo = uint32_t(id);
     c.pidhi = uint32_t(id >> 32);
     c.ctr = 0;
     c.flags = positron ? kPositron : 0u;
-    ++parent.flags;
     const uint32_t slot = reserve_slot(tail);
     if (slot < q.capacity) queue_store(q, slot, c);
     else atomicOr(P.status, ST_QUEUE_OVERFLOW);
     count_event(s_cnt, photon ? C_PH_CREATED : C_EL_CREATED);
     count_event(s_cnt, photon ? C_PUSH_PH : C_PUSH_EL);
-    hist_count(P, parent.hist, 3);
+    hist_count(P, hist, 3);
+    return true;
+}
+
+// Bank a secondary of particle p at p's position and voxel.
+__device__ __forceinline__ void bank_from(const SimParams& P, const Queue& q, uint32_t* tail, Part& p,
+                                          bool photon, bool positron, float E, float u, float v,
+                                          float w, uint32_t* s_cnt) {
+    if (bank(P, q, tail, p.hist, p.pidlo, p.pidhi, p.flags & 0xFFFFFFu, p.ix, p.iy, p.iz, photon,
+             positron, E, p.x, p.y, p.z, u, v, w, s_cnt))
+        ++p.flags;
 }
 
 // ---------------------------------------------------------------- samplers
@@ -280,30 +299,42 @@ __device__ void photon_step(const SimParams& P, const PhaseArgs& A, const PhSmem
         active = false;
         return;
     }
-    const float4 r = draw(p, P.key0, P.key1);
+    // Woodcock flights at fixed energy until a real collision (or escape), so
+    // that the interaction below runs with the warp's lanes together.
     int i;
     float f;
     grid_pos(T, p.E, i, f);
     const float mm = lerpf(S.maj[i], S.maj[i + 1], f);
-    const float s = -__logf(r.x) / mm;
-    p.x = fmaf(s, p.u, p.x);
-    p.y = fmaf(s, p.v, p.y);
-    p.z = fmaf(s, p.w, p.z);
-    if (!inside(P, p.x, p.y, p.z)) {
-        acc.esc += p.E;
-        hist_add(P, p.hist, 0, p.E);
-        count_event(s_cnt, C_PH_TERMINATED);
-        active = false;
-        return;
+    const float inv_mm = 1.f / mm;
+    float4 r;
+    uint32_t vox;
+    float mt;
+    int mi;
+    uint32_t flights = 0;
+    for (;;) {
+        r = draw(p, P.key0, P.key1);
+        const float s = -__logf(r.x) * inv_mm;
+        p.x = fmaf(s, p.u, p.x);
+        p.y = fmaf(s, p.v, p.y);
+        p.z = fmaf(s, p.w, p.z);
+        if (!inside(P, p.x, p.y, p.z)) {
+            count_n(s_cnt, C_PH_FLIGHTS, flights);
+            acc.esc += p.E;
+            hist_add(P, p.hist, 0, p.E);
+            count_event(s_cnt, C_PH_TERMINATED);
+            active = false;
+            return;
+        }
+        ++flights;
+        voxel_of(P, p);
+        vox = vox_of(P, p.ix, p.iy, p.iz);
+        const int m = __ldg(&P.mat[vox]);
+        const float rho = __ldg(&P.rho[vox]);
+        mi = m * T.n_e + i;
+        mt = lerpf(S.tot[mi], S.tot[mi + 1], f);
+        if (r.y * mm < mt * rho) break;             // real; otherwise a virtual (delta) collision
     }
-    voxel_of(P, p);
-    const uint32_t vox = vox_of(P, p.ix, p.iy, p.iz);
-    const int m = __ldg(&P.mat[vox]);
-    const float rho = __ldg(&P.rho[vox]);
-    count_event(s_cnt, C_PH_FLIGHTS);
-    const int mi = m * T.n_e + i;
-    const float mt = lerpf(S.tot[mi], S.tot[mi + 1], f);
-    if (r.y * mm >= mt * rho) return;                 // virtual (delta) collision
+    count_n(s_cnt, C_PH_FLIGHTS, flights);
     count_event(s_cnt, C_PH_REAL);
     hist_count(P, p.hist, 0);
     const float2 c0 = S.cum[mi], c1 = S.cum[mi + 1];
@@ -321,7 +352,7 @@ __device__ void photon_step(const SimParams& P, const PhaseArgs& A, const PhSmem
         const float Ep = eps * E, Te = E - Ep;
         float ex = E * u0 - Ep * p.u, ey = E * v0 - Ep * p.v, ez = E * w0 - Ep * p.w;
         const float en = rsqrtf(ex * ex + ey * ey + ez * ez);
-        bank(P, A.out_el, A.out_el_count, p, false, false, Te, p.x, p.y, p.z, ex * en, ey * en,
+        bank_from(P, A.out_el, A.out_el_count, p, false, false, Te, ex * en, ey * en,
              ez * en, s_cnt);
         if (Ep < T.eabs_ph) {
             tally(P, vox, Ep);
@@ -334,7 +365,7 @@ __device__ void photon_step(const SimParams& P, const PhaseArgs& A, const PhSmem
     } else if (rr < lerpf(c0.y, c1.y, f)) {
         // photoelectric: photon absorbed, photoelectron along the photon
         count_event(s_cnt, C_PHOTO);
-        bank(P, A.out_el, A.out_el_count, p, false, false, p.E, p.x, p.y, p.z, p.u, p.v, p.w, s_cnt);
+        bank_from(P, A.out_el, A.out_el_count, p, false, false, p.E, p.u, p.v, p.w, s_cnt);
         count_event(s_cnt, C_PH_TERMINATED);
         active = false;
     } else {
@@ -342,8 +373,8 @@ __device__ void photon_step(const SimParams& P, const PhaseArgs& A, const PhSmem
         count_event(s_cnt, C_PAIR);
         const float tav = p.E - 2.f * kMC2f;
         const float t1 = r.w * tav, t2 = tav - t1;
-        bank(P, A.out_el, A.out_el_count, p, false, false, t1, p.x, p.y, p.z, p.u, p.v, p.w, s_cnt);
-        bank(P, A.out_el, A.out_el_count, p, false, true, t2, p.x, p.y, p.z, p.u, p.v, p.w, s_cnt);
+        bank_from(P, A.out_el, A.out_el_count, p, false, false, t1, p.u, p.v, p.w, s_cnt);
+        bank_from(P, A.out_el, A.out_el_count, p, false, true, t2, p.u, p.v, p.w, s_cnt);
         count_event(s_cnt, C_PH_TERMINATED);
         active = false;
     }
@@ -438,8 +469,8 @@ __device__ void electron_absorb(const SimParams& P, const PhaseArgs& A, Part& p,
     cossin_2pi(a.y, cp, sp);
     const float dx = sint * cp, dy = sint * sp, dz = cost;
     count_event(s_cnt, C_ANNIHIL);
-    bank(P, A.out_ph, A.out_ph_count, p, true, false, kMC2f, p.x, p.y, p.z, dx, dy, dz, s_cnt);
-    bank(P, A.out_ph, A.out_ph_count, p, true, false, kMC2f, p.x, p.y, p.z, -dx, -dy, -dz, s_cnt);
+    bank_from(P, A.out_ph, A.out_ph_count, p, true, false, kMC2f, dx, dy, dz, s_cnt);
+    bank_from(P, A.out_ph, A.out_ph_count, p, true, false, kMC2f, -dx, -dy, -dz, s_cnt);
 }
 
 __device__ void electron_escape(const SimParams& P, Part& p, float energy, Acc& acc,
@@ -515,7 +546,7 @@ __device__ void electron_step(const SimParams& P, const PhaseArgs& A, const ElSm
     uint32_t crossings = 0;
     // random hinge: zeta*xs straight, deflect, (1-zeta)*xs straight
     const bool out1 = walk(P, p, r.y * xs, dpm, dep, false, crossings);
-    if (crossings) atomicAdd(&s_cnt[C_CROSS], crossings);
+    count_n(s_cnt, C_CROSS, crossings);
     crossings = 0;
     if (out1) {
         electron_escape(P, p, Tk - dep, acc, s_cnt);
@@ -524,7 +555,7 @@ __device__ void electron_step(const SimParams& P, const PhaseArgs& A, const ElSm
     }
     rotate(p.u, p.v, p.w, mu, cp, sp);
     const bool out2 = walk(P, p, (1.f - r.y) * xs, dpm, dep, true, crossings);
-    if (crossings) atomicAdd(&s_cnt[C_CROSS], crossings);
+    count_n(s_cnt, C_CROSS, crossings);
     if (out2) {
         electron_escape(P, p, Tk - dep, acc, s_cnt);
         active = false;
@@ -564,13 +595,13 @@ __device__ void electron_step(const SimParams& P, const PhaseArgs& A, const ElSm
         const float cpr = sqrtf(Tp * (Tn + 2.f * kMC2f) / (Tn * (Tp + 2.f * kMC2f)));
         float du = p.u, dv = p.v, dw = p.w;
         rotate(du, dv, dw, cd, c, s);
-        bank(P, A.out_el, A.out_el_count, p, false, false, W, p.x, p.y, p.z, du, dv, dw, s_cnt);
+        bank_from(P, A.out_el, A.out_el_count, p, false, false, W, du, dv, dw, s_cnt);
         rotate(p.u, p.v, p.w, cpr, -c, -s);
         p.E = Tp;
     } else {
         count_event(s_cnt, C_BREMS);
         const float k = wcb * exp2f(v.z * __log2f(Tn / wcb));
-        bank(P, A.out_ph, A.out_ph_count, p, true, false, k, p.x, p.y, p.z, p.u, p.v, p.w, s_cnt);
+        bank_from(P, A.out_ph, A.out_ph_count, p, true, false, k, p.u, p.v, p.w, s_cnt);
         p.E = Tn - k;
     }
 }
@@ -590,7 +621,7 @@ __device__ __forceinline__ void copy_to_smem(void* dst, const void* src, size_t 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
 template <int PT>
-__global__ void __launch_bounds__(256) k_phase(const SimParams P, const PhaseArgs A) {
+__global__ void __launch_bounds__(256, GDPM_MIN_CTAS) k_phase(const SimParams P, const PhaseArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t n_in = A.in_count ? min(*A.in_count, A.in.capacity) : 0u;
     const uint32_t total = A.n_src + n_in;

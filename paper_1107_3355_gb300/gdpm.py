@@ -25,7 +25,8 @@ GDPM_GEO_PENCIL, GDPM_GEO_POINT_FIELD, GDPM_GEO_BEAMLETS = 0, 1, 2
 GDPM_FLAG_COMPTON_ONLY, GDPM_FLAG_NO_HARD = 2, 4
 (GDPM_PARAM_QUEUE_CAPACITY, GDPM_PARAM_BLOCK_THREADS, GDPM_PARAM_BLOCKS_PER_SM,
  GDPM_PARAM_TALLY_MODE, GDPM_PARAM_SOURCE_CHUNK, GDPM_PARAM_MAX_PHASES, GDPM_PARAM_REQUEST_ID,
- GDPM_PARAM_SPECULATIVE, GDPM_PARAM_WARP_AGGREGATE, GDPM_PARAM_PROFILE) = range(1, 11)
+ GDPM_PARAM_SPECULATIVE, GDPM_PARAM_WARP_AGGREGATE, GDPM_PARAM_PROFILE,
+ GDPM_PARAM_OVERLAP_FOLD) = range(1, 12)
 MAX_EL, MAX_MAT, MAX_BINS = 16, 8, 256
 
 EXPORTED = ["gdpm_context_create", "gdpm_context_destroy", "gdpm_set_param",
