@@ -1023,11 +1023,13 @@ int orc_run(const orc_problem *P, double *dose, double *sigma, orc_result *res,
         double mass = P->rho[v] * dV;
         dose[v] = mean / mass;
         sigma[v] = sqrt(var) / mass;
-        if (dose[v] > dmax) dmax = dose[v];
+        /* READING: the Sec. 3.1 precision metric over tissue-like voxels only
+         * (rho >= 0.05 g/cm3); air voxels of tiny mass have meaningless noise */
+        if (P->rho[v] >= 0.05f && dose[v] > dmax) dmax = dose[v];
     }
     double acc = 0; long long na = 0;
     for (size_t v = 0; v < V; v++)
-        if (dose[v] > 0.5 * dmax) { acc += sigma[v]; na++; }
+        if (P->rho[v] >= 0.05f && dose[v] > 0.5 * dmax) { acc += sigma[v]; na++; }
     res->dmax = dmax;
     res->sigma_over_dmax = (na > 0 && dmax > 0) ? acc / na / dmax : 0.0;
     free(s1); free(s2); free(S.edep); free(S.stack);
