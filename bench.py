@@ -30,6 +30,7 @@ from paper_1107_3355_gb300 import workloads as W  # noqa: E402
 
 WORKLOADS = {
     "slab128_6MV": lambda n, nb: W.slab_photon_problem(n_histories=n, n_batches=nb),
+    "ct256_imrt7": lambda n, nb: W.ct_imrt_problem(n_histories=n, n_batches=nb),
     "slab128_e20MeV": lambda n, nb: W.slab_electron_problem(n_histories=n, n_batches=nb),
     "water32_1MeV_pencil": lambda n, nb: W.tiny_problem(n_histories=n, n_batches=nb),
 }
@@ -62,6 +63,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--serve-arc-histories", type=float, default=5e8)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-seed", type=int, default=3)
     return ap.parse_args()
 
 
@@ -134,15 +141,135 @@ def oracle_rate(prob_fn, seconds, first_n=2000):
         n = int(max(n * 2, n * seconds / max(dt, 1e-3) * 1.1))
 
 
+def serve_bench(args):
+    """Request stream on the patient-like phantom (Poisson arrivals, seeded):
+    60 % single beamlets (1e5 histories), 30 % full fluence-map beams (1e7),
+    10 % VMAT arcs (180 control points, MLC apertures).  Served with
+    continuous batching (gdpm_request_submit/poll, several slots) and one at a
+    time with plain gdpm_simulate calls; same requests, same histories."""
+    import numpy as np
+    import torch
+    from paper_1107_3355_gb300 import gdpm as G
+
+    rng = np.random.default_rng(args.serve_seed)
+    ph = W.ct_phantom()
+    base = W.Problem(ph, W.single_beamlet(ph, 0.0, 0.0, 0.0, 1.0), 100, 10, eabs_photon=0.05,
+                     eabs_electron=0.2, e_min=0.005, e_max=6.5)
+    iso = tuple(e / 2 for e in ph.extent)
+    reqs = []
+    for k in range(args.serve_requests):
+        r = rng.uniform()
+        ang = float(rng.uniform(0, 360))
+        if r < 0.6:
+            u, v = rng.uniform(-8, 7, 2)
+            reqs.append(("beamlet", W.single_beamlet(ph, ang, float(u), float(v), 1.0), 100_000))
+        elif r < 0.9:
+            fr = W.beam_frame(ang, iso)
+            rows = W.fluence_map_rows(fr, rng.uniform(0, 1, (20, 20)), 1.0)
+            reqs.append(("beam", W.beamlet_source(rows, W.kramers_spectrum()), 10_000_000))
+        else:
+            reqs.append(("arc", W.vmat_arc(ph, seed=int(rng.integers(1 << 30))),
+                         int(args.serve_arc_histories)))
+    eng = G.Engine(base)
+    ctx = eng.ctx
+    V = ph.n_voxels
+    dose = torch.empty(V, dtype=torch.float64, device="cuda")
+    sig = torch.empty(V, dtype=torch.float64, device="cuda")
+    # calibrate service rate for the arrival process
+    G.gdpm_source_set(ctx, reqs[0][1])
+    G.gdpm_simulate(ctx, eng.phantom, eng.tables, 1_000_000, 10, dose, sig)
+    t0 = time.perf_counter()
+    G.gdpm_simulate(ctx, eng.phantom, eng.tables, 5_000_000, 10, dose, sig)
+    rate = 5_000_000 / (time.perf_counter() - t0)
+    mean_hist = np.mean([n for _, _, n in reqs])
+    lam = args.serve_load * rate / mean_hist
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
+    total_hist = sum(n for _, _, n in reqs)
+
+    # (a) one at a time, plain gdpm_simulate calls in arrival order
+    lat_a = []
+    start = time.perf_counter()
+    for k, (kind, src, n) in enumerate(reqs):
+        now = time.perf_counter() - start
+        if now < arrivals[k]:
+            time.sleep(arrivals[k] - now)
+        G.gdpm_source_set(ctx, src)
+        G.gdpm_simulate(ctx, eng.phantom, eng.tables, n, 10, dose, sig)
+        lat_a.append(time.perf_counter() - start - arrivals[k])
+    span_a = time.perf_counter() - start
+
+    # (b) continuous batching through the request loop
+    G.gdpm_set_param(ctx, G.GDPM_PARAM_SERVE_SLOTS, args.serve_slots)
+    import threading
+    ids = [None] * len(reqs)
+    done_at = [None] * len(reqs)
+    start = time.perf_counter()
+
+    def submitter():
+        for k, (kind, src, n) in enumerate(reqs):
+            now = time.perf_counter() - start
+            if now < arrivals[k]:
+                time.sleep(arrivals[k] - now)
+            ids[k] = G.gdpm_request_submit(ctx, eng.phantom, eng.tables, src, n, 10)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    outstanding = set(range(len(reqs)))
+    while outstanding:
+        for k in list(outstanding):
+            if ids[k] is None:
+                continue
+            fin, _ = G.gdpm_request_poll(ctx, ids[k], dose, sig)
+            if fin:
+                done_at[k] = time.perf_counter() - start
+                outstanding.discard(k)
+        time.sleep(0.0005)
+    th.join()
+    span_b = time.perf_counter() - start
+    lat_b = [done_at[k] - arrivals[k] for k in range(len(reqs))]
+    eng.close()
+
+    def pct(x, q):
+        return float(np.percentile(np.asarray(x) * 1e3, q))
+
+    def by_kind(lat):
+        out = {}
+        for kind in ("beamlet", "beam", "arc"):
+            xs = [l for (k, _, _), l in zip(reqs, lat) if k == kind]
+            if xs:
+                out[kind] = {"n": len(xs), "p50_ms": pct(xs, 50), "p99_ms": pct(xs, 99)}
+        return out
+
+    line = {"metric": "p50/p99 request latency", "unit": "ms", "mode": "serve",
+            "value": pct(lat_b, 99), "higher_is_better": False, "n_gpus": 1,
+            "data": "synthetic",
+            "config": {"workload": "ct256_serving_mix", "requests": len(reqs),
+                       "mix": "60%% beamlet 1e5, 30%% beam 1e7, 10%% VMAT arc %.0e" % args.serve_arc_histories,
+                       "load": args.serve_load, "slots": args.serve_slots, "batches": 10},
+            "continuous": {"p50_ms": pct(lat_b, 50), "p99_ms": pct(lat_b, 99),
+                           "histories_per_s": total_hist / span_b, "makespan_s": span_b,
+                           "by_kind": by_kind(lat_b)},
+            "one_at_a_time": {"p50_ms": pct(lat_a, 50), "p99_ms": pct(lat_a, 99),
+                              "histories_per_s": total_hist / span_a, "makespan_s": span_a,
+                              "by_kind": by_kind(lat_a)},
+            "calibrated_histories_per_s": rate, "total_histories": int(total_hist)}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
+    if args.mode == "serve":
+        serve_bench(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     n_hist = int(args.histories)
     make = WORKLOADS[args.workload]
     config = {"workload": args.workload, "histories_per_step": n_hist, "batches": args.batches,
-              "phantom": "128x128x128 @0.25cm" if "slab" in args.workload else "32^3 @0.5cm",
+              "phantom": {"slab128_6MV": "128^3 slab @0.25cm", "slab128_e20MeV": "128^3 slab @0.25cm",
+                          "ct256_imrt7": "256x256x128 ellipsoid CT @0.25cm",
+                          "water32_1MeV_pencil": "32^3 water @0.5cm"}[args.workload],
               "l2": "flushed between steps (256 MB write)",
               "parallelism": "replicas" if world > 1 else "single GPU"}
 

@@ -106,7 +106,8 @@ typedef struct {
     int64_t local_deposits;
     int64_t pushes[2], pops[2];    /* queue traffic: [0] photons, [1] electrons */
     int64_t phases, launches;
-    double dmax, sigma_over_dmax;  /* Sec. 3.1 precision metric over D > 0.5 Dmax */
+    double dmax, sigma_over_dmax;  /* Sec. 3.1 precision metric over D > 0.5 Dmax, among
+                                      voxels denser than GDPM_PARAM_METRIC_MIN_DENSITY */
     double transport_ms;           /* device time of the transport + fold loop */
     int64_t crossings;             /* voxel boundaries crossed by electrons */
     /* with GDPM_PARAM_PROFILE: summed device time and launch count per kernel
@@ -136,9 +137,17 @@ enum {
     GDPM_PARAM_MAX_PHASES = 6,       /* phase cap per batch -> GDPM_E_TIMEOUT */
     GDPM_PARAM_REQUEST_ID = 7,       /* xored into the Philox key high word */
     GDPM_PARAM_SPECULATIVE = 8,      /* phase pairs issued per host check (>=1) */
-    GDPM_PARAM_WARP_AGGREGATE = 9,   /* 1: merge same-voxel deposits within a warp */
     GDPM_PARAM_PROFILE = 10,         /* 1: time every launch with CUDA events (stats kernel_ms) */
-    GDPM_PARAM_OVERLAP_FOLD = 11     /* 1 (default): fold batch b while batch b+1 runs */
+    GDPM_PARAM_OVERLAP_FOLD = 11,    /* 1 (default): fold batch b while batch b+1 runs */
+    GDPM_PARAM_SERVE_SLOTS = 12,     /* requests run side by side by the serving loop (1..16) */
+    GDPM_PARAM_SERVE_RESERVE_MB = 13,/* device memory left free when admitting a request */
+    GDPM_PARAM_METRIC_MIN_DENSITY = 14,/* sigma/Dmax only over voxels at least this dense
+                                          (g/cm3, default 0.05: excludes air) */
+    GDPM_PARAM_BATCH_MODE = 15,      /* 0 auto, 1 batches one after another, 2 all batches side
+                                        by side (one tally grid per batch, n_batches <= 128) */
+    GDPM_PARAM_CONCURRENT_MAX_HIST = 16, /* auto: side by side when histories per batch <= this
+                                            (default 131072) ... */
+    GDPM_PARAM_CONCURRENT_MAX_MB = 17    /* ... and the per-batch grids fit in this (default 4096) */
 };
 
 /* ------------------------------------------------------------------ inputs */
@@ -204,6 +213,8 @@ typedef struct {
     gdpm_source_desc source;
     uint64_t n_histories;
     int n_batches;
+    uint32_t stream_id;            /* Philox stream (xored into the key high word);
+                                      0 = use the request id */
 } gdpm_request_desc;
 
 /* Queue a request; returns at once with its id.  Requests arriving while

@@ -9,6 +9,7 @@
 // empty batch only after the primaries are used up, once per
 // `speculative` phase pairs (phases launched on an empty input exit at once).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -71,41 +72,84 @@ static void allot_prefix(const std::vector<double>& w, uint64_t nb, uint32_t* pr
     for (int j = 0; j < K; ++j) prefix[j + 1] = prefix[j] + uint32_t(c[j]);
 }
 
+int runner_init(Runner& r, cudaStream_t stream, bool own_stream) {
+    r.owns_stream = own_stream;
+    if (own_stream) {
+        int least = 0, greatest = 0;
+        GDPM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        GDPM_CUDA_TRY(cudaStreamCreateWithPriority(&r.prio_hi, cudaStreamNonBlocking, greatest));
+        GDPM_CUDA_TRY(cudaStreamCreateWithPriority(&r.prio_lo, cudaStreamNonBlocking, least));
+        r.stream = r.prio_lo;
+    } else {
+        r.stream = stream;
+    }
+    GDPM_CUDA_TRY(cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking));
+    GDPM_CUDA_TRY(cudaEventCreate(&r.ev0));
+    GDPM_CUDA_TRY(cudaEventCreate(&r.ev1));
+    for (int k = 0; k < 2; ++k) {
+        GDPM_CUDA_TRY(cudaEventCreateWithFlags(&r.batch_done[k], cudaEventDisableTiming));
+        GDPM_CUDA_TRY(cudaEventCreateWithFlags(&r.fold_done[k], cudaEventDisableTiming));
+    }
+    return GDPM_OK;
+}
+
+void runner_free(Runner& r) {
+    if (r.stream) cudaStreamSynchronize(r.stream);
+    if (r.side) cudaStreamSynchronize(r.side);
+    Workspace& w = r.ws;
+    Buffer* bs[] = {&w.edep, &w.edep2, &w.hi2, &w.lo2, &w.s1, &w.s2, &w.hi, &w.lo, &w.qph,
+                    &w.qel0, &w.qel1, &w.ctl, &w.prefix, &w.counters, &w.ledger, &w.status,
+                    &w.edges, &w.beamlets, &w.bl_cdf, &w.stage};
+    for (Buffer* b : bs) release(*b);
+    if (w.pinned_host.p) cudaFreeHost(w.pinned_host.p);
+    w.pinned_host.p = nullptr;
+    for (cudaEvent_t e : r.prof_events) cudaEventDestroy(e);
+    r.prof_events.clear();
+    cudaEvent_t evs[] = {r.ev0, r.ev1, r.batch_done[0], r.batch_done[1], r.fold_done[0], r.fold_done[1]};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    if (r.side) cudaStreamDestroy(r.side);
+    if (r.owns_stream) {
+        if (r.prio_hi) cudaStreamSynchronize(r.prio_hi), cudaStreamDestroy(r.prio_hi);
+        if (r.prio_lo) cudaStreamSynchronize(r.prio_lo), cudaStreamDestroy(r.prio_lo);
+    }
+    r.side = r.stream = r.prio_hi = r.prio_lo = nullptr;
+}
+
 // Optional per-launch device timing (GDPM_PARAM_PROFILE): an event pair on
-// the context's stream around each launch, summed per kernel kind at the end.
-static size_t prof_begin(gdpm_ctx* ctx, int kind) {
+// the launching stream around each launch, summed per kernel kind at the end.
+static size_t prof_begin(gdpm_ctx* ctx, Runner& r, cudaStream_t st, int kind) {
     if (!ctx->profile) return 0;
-    const size_t idx = ctx->prof_kind.size();
-    while (ctx->prof_events.size() < 2 * (idx + 1)) {
+    const size_t idx = r.prof_kind.size();
+    while (r.prof_events.size() < 2 * (idx + 1)) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
-        ctx->prof_events.push_back(e);
+        r.prof_events.push_back(e);
     }
-    cudaEventRecord(ctx->prof_events[2 * idx], ctx->stream);
-    ctx->prof_kind.push_back(kind);
+    cudaEventRecord(r.prof_events[2 * idx], st);
+    r.prof_kind.push_back(kind);
     return idx;
 }
-static void prof_end(gdpm_ctx* ctx, size_t idx) {
-    if (ctx->profile && 2 * idx + 1 < ctx->prof_events.size())
-        cudaEventRecord(ctx->prof_events[2 * idx + 1], ctx->stream);
+static void prof_end(gdpm_ctx* ctx, Runner& r, cudaStream_t st, size_t idx) {
+    if (ctx->profile && 2 * idx + 1 < r.prof_events.size()) cudaEventRecord(r.prof_events[2 * idx + 1], st);
 }
-static void prof_collect(gdpm_ctx* ctx, gdpm_stats* st) {
-    for (size_t i = 0; i < ctx->prof_kind.size(); ++i) {
+static void prof_collect(Runner& r, gdpm_stats* st) {
+    for (size_t i = 0; i < r.prof_kind.size(); ++i) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ctx->prof_events[2 * i], ctx->prof_events[2 * i + 1]) != cudaSuccess) {
+        if (cudaEventElapsedTime(&ms, r.prof_events[2 * i], r.prof_events[2 * i + 1]) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
-        const int k = ctx->prof_kind[i];
+        const int k = r.prof_kind[i];
         if (st && k >= 0 && k < 3) {
             st->kernel_ms[k] += ms;
             st->kernel_launches[k] += 1;
         }
     }
-    ctx->prof_kind.clear();
+    r.prof_kind.clear();
 }
 
 static Queue make_queue(const Buffer& b, uint32_t cap) {
@@ -129,7 +173,45 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static int source_upload(gdpm_ctx* ctx, const gdpm_source_state& s, DevSource& d) {
+// Validate a source description and copy what it points to.
+static int source_copy(const gdpm_source_desc* s, gdpm_source_state& st) {
+    if (!s) return GDPM_E_ARG;
+    if (s->particle != GDPM_PHOTON && s->particle != GDPM_ELECTRON) return GDPM_E_ARG;
+    if (s->geometry < GDPM_GEO_PENCIL || s->geometry > GDPM_GEO_BEAMLETS) return GDPM_E_ARG;
+    if (s->n_bins < 1 || s->n_bins > GDPM_MAX_BINS || !s->bin_edges || !s->bin_weights) return GDPM_E_ARG;
+    double ws = 0;
+    for (int j = 0; j < s->n_bins; ++j) {
+        if (s->bin_weights[j] < 0 || s->bin_edges[j + 1] < s->bin_edges[j]) return GDPM_E_ARG;
+        ws += s->bin_weights[j];
+    }
+    if (!(ws > 0) || !(s->bin_edges[0] >= 0)) return GDPM_E_ARG;
+    if (s->geometry == GDPM_GEO_BEAMLETS) {
+        if (s->n_beamlets < 1 || !s->beamlets) return GDPM_E_ARG;
+        double bw = 0;
+        for (int b = 0; b < s->n_beamlets; ++b) {
+            if (s->beamlets[size_t(b) * 17 + 16] < 0) return GDPM_E_ARG;
+            bw += s->beamlets[size_t(b) * 17 + 16];
+        }
+        if (!(bw > 0)) return GDPM_E_ARG;
+    }
+    const double dn = s->direction[0] * s->direction[0] + s->direction[1] * s->direction[1] +
+                      s->direction[2] * s->direction[2];
+    if (s->geometry == GDPM_GEO_PENCIL && !(dn > 0)) return GDPM_E_ARG;
+    st.desc = *s;
+    st.edges.assign(s->bin_edges, s->bin_edges + s->n_bins + 1);
+    st.weights.assign(s->bin_weights, s->bin_weights + s->n_bins);
+    if (s->geometry == GDPM_GEO_BEAMLETS)
+        st.beamlets.assign(s->beamlets, s->beamlets + size_t(s->n_beamlets) * 17);
+    else
+        st.beamlets.clear();
+    st.desc.bin_edges = nullptr;
+    st.desc.bin_weights = nullptr;
+    st.desc.beamlets = nullptr;
+    st.set = true;
+    return GDPM_OK;
+}
+
+static int source_upload(Runner& r, const gdpm_source_state& s, DevSource& d) {
     const gdpm_source_desc& g = s.desc;
     d.particle = g.particle;
     d.geometry = g.geometry;
@@ -142,16 +224,16 @@ static int source_upload(gdpm_ctx* ctx, const gdpm_source_state& s, DevSource& d
         d.axis_u[a] = float(g.axis_u[a]);
         d.axis_v[a] = float(g.axis_v[a]);
     }
-    double dn = std::sqrt(g.direction[0] * g.direction[0] + g.direction[1] * g.direction[1] +
-                          g.direction[2] * g.direction[2]);
-    for (int a = 0; a < 3; ++a) d.direction[a] = float(g.direction[a] / dn);
+    const double dn = std::sqrt(g.direction[0] * g.direction[0] + g.direction[1] * g.direction[1] +
+                                g.direction[2] * g.direction[2]);
+    for (int a = 0; a < 3; ++a) d.direction[a] = dn > 0 ? float(g.direction[a] / dn) : 0.f;
     d.half_u = float(g.half_u);
     d.half_v = float(g.half_v);
     std::vector<float> e(s.edges.begin(), s.edges.end());
-    int rc = ensure(ctx->ws.edges, e.size() * 4);
+    int rc = ensure(r.ws.edges, e.size() * 4);
     if (rc) return rc;
-    GDPM_CUDA_TRY(cudaMemcpyAsync(ctx->ws.edges.p, e.data(), e.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
-    d.edges = static_cast<const float*>(ctx->ws.edges.p);
+    GDPM_CUDA_TRY(cudaMemcpyAsync(r.ws.edges.p, e.data(), e.size() * 4, cudaMemcpyHostToDevice, r.stream));
+    d.edges = static_cast<const float*>(r.ws.edges.p);
     d.beamlets = nullptr;
     d.bl_cdf = nullptr;
     if (d.n_beamlets > 0) {
@@ -167,13 +249,31 @@ static int source_upload(gdpm_ctx* ctx, const gdpm_source_state& s, DevSource& d
             cdf[b] = acc / tot;
         }
         cdf[nbl - 1] = 1.0;
-        if ((rc = ensure(ctx->ws.beamlets, rows.size() * 4)) || (rc = ensure(ctx->ws.bl_cdf, cdf.size() * 8)))
+        if ((rc = ensure(r.ws.beamlets, rows.size() * 4)) || (rc = ensure(r.ws.bl_cdf, cdf.size() * 8)))
             return rc;
-        GDPM_CUDA_TRY(cudaMemcpyAsync(ctx->ws.beamlets.p, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
-        GDPM_CUDA_TRY(cudaMemcpyAsync(ctx->ws.bl_cdf.p, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
-        d.beamlets = static_cast<const float*>(ctx->ws.beamlets.p);
-        d.bl_cdf = static_cast<const double*>(ctx->ws.bl_cdf.p);
+        GDPM_CUDA_TRY(cudaMemcpyAsync(r.ws.beamlets.p, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, r.stream));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(r.ws.bl_cdf.p, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, r.stream));
+        d.beamlets = static_cast<const float*>(r.ws.beamlets.p);
+        d.bl_cdf = static_cast<const double*>(r.ws.bl_cdf.p);
     }
+    // the host vectors above are staged by the copies; make the copies
+    // complete before they go out of scope
+    GDPM_CUDA_TRY(cudaStreamSynchronize(r.stream));
+    return GDPM_OK;
+}
+
+// Woodcock majorant of a (phantom, tables) pair, built once and shared by
+// every calculation on that pair.
+static int get_majorant(gdpm_ctx* ctx, cudaStream_t st, gdpm_phantom* ph, gdpm_tables* tb, const float** out) {
+    std::lock_guard<std::mutex> lk(ctx->maj_mu);
+    Buffer& b = ph->maj[tb->id];
+    if (!b.p) {
+        int rc = ensure(b, sizeof(float) * tb->n_e);
+        if (rc) return rc;
+        if ((rc = launch_majorant_into(st, ph, tb, static_cast<float*>(b.p)))) return rc;
+        GDPM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    *out = static_cast<const float*>(b.p);
     return GDPM_OK;
 }
 
@@ -187,12 +287,10 @@ static SimParams base_params(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, u
     P.Lz = float(double(ph->nz) * ph->dz);
     P.mat = static_cast<const uint8_t*>(ph->mat.p);
     P.rho = static_cast<const float*>(ph->rho.p);
-    P.maj = static_cast<const float*>(ph->maj.p);
     P.T = tb->dev;
     P.key0 = uint32_t(ctx->seed);
     P.key1 = uint32_t(ctx->seed >> 32) ^ request_id;
     P.tally_mode = ctx->tally_mode;
-    P.warp_aggregate = ctx->warp_aggregate;
     P.max_iters = 1u << 22;   // per-warp iterations in one phase; far above real use
     return P;
 }
@@ -215,12 +313,34 @@ static int validate_run(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const 
     return GDPM_OK;
 }
 
+// Primaries per phase: up to 2^20, and no more than one batch (or run) holds.
+static uint32_t chunk_of(gdpm_ctx* ctx, uint64_t n_per_run, int parts) {
+    const uint64_t per = (n_per_run + parts - 1) / parts;
+    const uint32_t chunk = ctx->source_chunk ? ctx->source_chunk : (1u << 20);
+    return uint32_t(std::min<uint64_t>(chunk, per));
+}
+static uint32_t capacity_of(gdpm_ctx* ctx, uint32_t chunk) {
+    return ctx->queue_capacity ? ctx->queue_capacity : 8u * chunk + 65536u;
+}
+
+// Run all batches side by side (one tally grid each) or one after another?
+static bool side_by_side(gdpm_ctx* ctx, size_t V, uint64_t n_hist, int n_batches) {
+    if (ctx->batch_mode == 1 || n_batches > kMaxConcurrentBatches) return false;
+    const size_t bytes = V * size_t(n_batches) * 8;
+    if (ctx->batch_mode == 2) return true;
+    return n_hist / uint64_t(n_batches) <= ctx->concurrent_max_hist && bytes <= ctx->concurrent_max_bytes;
+}
+
 // Work buffers for a phantom of V voxels and queues of `cap` particles.
-static int prepare_workspace(gdpm_ctx* ctx, size_t V, uint32_t cap, int n_batches, int n_bins) {
-    Workspace& ws = ctx->ws;
+static int prepare_workspace(gdpm_ctx* ctx, Runner& r, size_t V, uint32_t cap, int n_batches, int n_bins,
+                             bool concurrent) {
+    Workspace& ws = r.ws;
     int rc;
     if ((rc = ensure(ws.s1, V * 8)) || (rc = ensure(ws.s2, V * 8))) return rc;
-    if (ctx->tally_mode == 0) {
+    if (concurrent) {
+        // one grid per batch: V*n_batches doubles, or hi and lo halves of floats
+        if ((rc = ensure(ws.edep, V * size_t(n_batches) * 8))) return rc;
+    } else if (ctx->tally_mode == 0) {
         if ((rc = ensure(ws.edep, V * 8)) || (rc = ensure(ws.edep2, V * 8))) return rc;
     } else {
         if ((rc = ensure(ws.hi, V * 4)) || (rc = ensure(ws.lo, V * 4)) || (rc = ensure(ws.hi2, V * 4)) ||
@@ -244,21 +364,38 @@ static int prepare_workspace(gdpm_ctx* ctx, size_t V, uint32_t cap, int n_batche
     return GDPM_OK;
 }
 
-// One batch: alternate photon (even k) and electron (odd k) phases.
+// Device bytes a calculation still has to allocate in runner r.
+static size_t bytes_needed(gdpm_ctx* ctx, const Runner& r, size_t V, uint64_t n_hist, int n_batches,
+                           bool with_result) {
+    const bool conc = side_by_side(ctx, V, n_hist, n_batches);
+    const uint32_t cap = capacity_of(ctx, chunk_of(ctx, conc ? n_hist : n_hist / n_batches + 1, 1));
+    auto grow = [](const Buffer& b, size_t want) { return b.bytes >= want ? size_t(0) : want; };
+    const Workspace& w = r.ws;
+    size_t n = grow(w.s1, V * 8) + grow(w.s2, V * 8);
+    n += conc ? grow(w.edep, V * size_t(n_batches) * 8) : grow(w.edep, V * 8) + grow(w.edep2, V * 8);
+    const size_t qb = size_t(cap) * kQueueWords * 4;
+    n += grow(w.qph, qb) + grow(w.qel0, qb) + grow(w.qel1, qb);
+    if (with_result) n += V * 16;
+    return n;
+}
+
+// The histories [first, first+n) (one batch, or all batches side by side):
+// alternate photon (even k) and electron (odd k) phases.
 //   photon phase k consumes fill P[k] (+ photon primaries), banks electrons into E[k+1];
 //   electron phase k consumes E[k] (+ electron primaries), banks photons into
 //   P[k+1] and electrons into E[k+2].
 // ctl row k: [0] pop counter of phase k, [1] count of P[k], [2] count of E[k].
-static int run_batch(gdpm_ctx* ctx, const SimParams& P, const gdpm_source_state& src, int b,
-                     uint64_t nb, uint64_t first, uint32_t chunk, int64_t& phases) {
-    Workspace& ws = ctx->ws;
+static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_source_state& src,
+                      uint64_t first, uint64_t n, uint32_t nb_small, uint32_t nb_rem, uint32_t chunk,
+                      int64_t& phases) {
+    Workspace& ws = r.ws;
+    cudaStream_t s = r.stream;
     uint32_t* ctl = static_cast<uint32_t*>(ws.ctl.p);
-    GDPM_CUDA_TRY(cudaMemsetAsync(ctl, 0, size_t(ctx->max_phases + 4) * 16, ctx->stream));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ctl, 0, size_t(ctx->max_phases + 4) * 16, s));
     const Queue qph = make_queue(ws.qph, ws.cap_ph);
     const Queue qe[2] = {make_queue(ws.qel0, ws.cap_el), make_queue(ws.qel1, ws.cap_el)};
     const bool photon_src = src.desc.particle == GDPM_PHOTON;
-    const int n_bins = int(src.weights.size());
-    uint64_t left = nb, next = 0;
+    uint64_t left = n, next = first;
     int k = photon_src ? 0 : 1;
     int since = 0;
     uint32_t* host = static_cast<uint32_t*>(ws.pinned_host.p);
@@ -266,16 +403,16 @@ static int run_batch(gdpm_ctx* ctx, const SimParams& P, const gdpm_source_state&
         if (k + 3 >= ctx->max_phases) return GDPM_E_TIMEOUT;
         const bool ph = (k % 2) == 0;
         PhaseArgs A{};
-        A.batch_first_hist = uint32_t(first);
-        A.bin_prefix = static_cast<const uint32_t*>(ws.prefix.p) + size_t(b) * (n_bins + 1);
+        A.nb_small = nb_small;
+        A.nb_rem = nb_rem;
+        A.bin_prefix = static_cast<const uint32_t*>(ws.prefix.p);
         if (ph == photon_src && left > 0) {
             A.n_src = uint32_t(std::min<uint64_t>(left, chunk));
-            A.src_first_local = uint32_t(next);
+            A.src_first = uint32_t(next);
             next += A.n_src;
             left -= A.n_src;
         }
         A.head = ctl + size_t(k) * 4 + 0;
-        uint32_t hint = 0;
         if (ph) {
             A.in = qph;
             A.in_count = k >= 1 ? ctl + size_t(k) * 4 + 1 : nullptr;
@@ -291,19 +428,20 @@ static int run_batch(gdpm_ctx* ctx, const SimParams& P, const gdpm_source_state&
             A.out_el = qe[((k + 2) / 2) % 2];
             A.out_el_count = ctl + size_t(k + 2) * 4 + 2;
         }
-        if (!A.in_count) hint = A.n_src;
-        const size_t pi = prof_begin(ctx, ph ? 0 : 1);
-        int rc = launch_phase(ctx, ph ? GDPM_PHOTON : GDPM_ELECTRON, P, A, hint);
-        prof_end(ctx, pi);
+        const uint32_t hint = A.in_count ? 0u : A.n_src;
+        const size_t pi = prof_begin(ctx, r, s, ph ? 0 : 1);
+        const uint32_t share = (r.serving && !r.small && ctx->small_running.load() > 0) ? 4u : 1u;
+        int rc = launch_phase(ctx, s, ph ? GDPM_PHOTON : GDPM_ELECTRON, P, A, hint, share);
+        prof_end(ctx, r, s, pi);
         if (rc) return rc;
         ++phases;
         ++k;
         ++since;
         if (!ph && left == 0 && since >= 2 * ctx->speculative) {
             // pending after electron phase k-1: photons P[k], electrons E[k+1]
-            GDPM_CUDA_TRY(cudaMemcpyAsync(host, ctl + size_t(k) * 4 + 1, 4, cudaMemcpyDeviceToHost, ctx->stream));
-            GDPM_CUDA_TRY(cudaMemcpyAsync(host + 1, ctl + size_t(k + 1) * 4 + 2, 4, cudaMemcpyDeviceToHost, ctx->stream));
-            GDPM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+            GDPM_CUDA_TRY(cudaMemcpyAsync(host, ctl + size_t(k) * 4 + 1, 4, cudaMemcpyDeviceToHost, s));
+            GDPM_CUDA_TRY(cudaMemcpyAsync(host + 1, ctl + size_t(k + 1) * 4 + 2, 4, cudaMemcpyDeviceToHost, s));
+            GDPM_CUDA_TRY(cudaStreamSynchronize(s));
             if (host[0] == 0 && host[1] == 0) break;
             since = 0;
         }
@@ -311,9 +449,10 @@ static int run_batch(gdpm_ctx* ctx, const SimParams& P, const gdpm_source_state&
     return GDPM_OK;
 }
 
+
 // Point P's batch tally at buffer `which` (0 or 1).
-static void select_tally(gdpm_ctx* ctx, SimParams& P, int which) {
-    Workspace& ws = ctx->ws;
+static void select_tally(Runner& r, SimParams& P, int which) {
+    Workspace& ws = r.ws;
     P.edep = static_cast<double*>(which ? ws.edep2.p : ws.edep.p);
     P.edep_hi = static_cast<float*>(which ? ws.hi2.p : ws.hi.p);
     P.edep_lo = static_cast<float*>(which ? ws.lo2.p : ws.lo.p);
@@ -343,48 +482,48 @@ static void fill_stats(const unsigned long long* c, const double* l, gdpm_stats*
     st->pushes[1] = int64_t(c[C_PUSH_EL]);
     st->pops[0] = int64_t(c[C_POP_PH]);
     st->pops[1] = int64_t(c[C_POP_EL]);
-    unsigned long long bits;
-    std::memcpy(&bits, &l[L_DMAX], 8);
+    st->crossings = int64_t(c[C_CROSS]);
     double dmax;
-    std::memcpy(&dmax, &bits, 8);
+    std::memcpy(&dmax, &l[L_DMAX], 8);
     st->dmax = dmax;
     st->sigma_over_dmax = (l[L_SIGCNT] > 0 && dmax > 0) ? l[L_SIGSUM] / l[L_SIGCNT] / dmax : 0.0;
 }
 
-int simulate_impl(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const gdpm_source_state& src,
-                  uint32_t request_id, uint64_t n_hist, int n_batches, double* dose_out,
-                  double* sigma_out, gdpm_stats* st) {
+// One dose calculation on runner r.
+int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
+                  const gdpm_source_state& src, uint32_t request_id, uint64_t n_hist, int n_batches,
+                  double* dose_out, double* sigma_out, gdpm_stats* st, int32_t* hrec, double* hrecd) {
     int rc = validate_run(ctx, ph, tb, src, n_hist, n_batches);
     if (rc) return rc;
-    if ((rc = build_majorant(ctx, ph, tb))) return rc;
+    cudaStream_t s = r.stream;
     const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
-    const uint64_t nb_max = (n_hist + n_batches - 1) / n_batches;
-    uint32_t chunk = ctx->source_chunk ? ctx->source_chunk : (1u << 20);
-    chunk = uint32_t(std::min<uint64_t>(chunk, nb_max));
-    const uint32_t cap = ctx->queue_capacity ? ctx->queue_capacity : 8u * chunk + 65536u;
+    const bool conc = side_by_side(ctx, V, n_hist, n_batches);
+    const uint32_t nb_small = uint32_t(n_hist / n_batches), nb_rem = uint32_t(n_hist % n_batches);
+    uint32_t chunk = conc ? chunk_of(ctx, n_hist, 1) : chunk_of(ctx, n_hist, n_batches);
+    const uint32_t cap = capacity_of(ctx, chunk);
     const int n_bins = int(src.weights.size());
-    if ((rc = prepare_workspace(ctx, V, cap, n_batches, n_bins))) return rc;
-    Workspace& ws = ctx->ws;
+    if ((rc = prepare_workspace(ctx, r, V, cap, n_batches, n_bins, conc))) return rc;
+    Workspace& ws = r.ws;
+    SimParams P = base_params(ctx, ph, tb, request_id);
+    if ((rc = get_majorant(ctx, s, ph, tb, &P.maj))) return rc;
     // spectrum allotment of every batch
     std::vector<uint32_t> prefix(size_t(n_batches) * (n_bins + 1));
     for (int b = 0; b < n_batches; ++b) {
         const uint64_t nb = n_hist / n_batches + (uint64_t(b) < n_hist % n_batches ? 1 : 0);
         allot_prefix(src.weights, nb, &prefix[size_t(b) * (n_bins + 1)]);
     }
-    GDPM_CUDA_TRY(cudaMemcpyAsync(ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
-    SimParams P = base_params(ctx, ph, tb, request_id);
-    if ((rc = source_upload(ctx, src, P.S))) return rc;
-    select_tally(ctx, P, 0);
+    GDPM_CUDA_TRY(cudaMemcpyAsync(ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, s));
+    if ((rc = source_upload(r, src, P.S))) return rc;
     P.counters = static_cast<unsigned long long*>(ws.counters.p);
     P.ledger = static_cast<double*>(ws.ledger.p);
     P.status = static_cast<uint32_t*>(ws.status.p);
-    P.hrec = ctx->hrec;
-    P.hrecd = ctx->hrecd;
-    if (P.hrec && ctx->hrec_n < n_hist) return GDPM_E_ARG;
-    cudaStream_t s = ctx->stream;
+    P.hrec = hrec;
+    P.hrecd = hrecd;
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.s1.p, 0, V * 8, s));
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.s2.p, 0, V * 8, s));
-    if (ctx->tally_mode == 0) {
+    if (conc) {
+        GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep.p, 0, V * size_t(n_batches) * 8, s));
+    } else if (ctx->tally_mode == 0) {
         GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep.p, 0, V * 8, s));
         GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep2.p, 0, V * 8, s));
     } else {
@@ -396,59 +535,74 @@ int simulate_impl(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const gdpm_s
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.counters.p, 0, C_NCOUNT * 8, s));
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.ledger.p, 0, L_NLEDGER * 8, s));
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, 16, s));
-    if (P.hrec) {
-        GDPM_CUDA_TRY(cudaMemsetAsync(P.hrec, 0, n_hist * 16, s));
-        GDPM_CUDA_TRY(cudaMemsetAsync(P.hrecd, 0, n_hist * 16, s));
+    if (hrec) {
+        GDPM_CUDA_TRY(cudaMemsetAsync(hrec, 0, n_hist * 16, s));
+        GDPM_CUDA_TRY(cudaMemsetAsync(hrecd, 0, n_hist * 16, s));
     }
-    ctx->prof_kind.clear();
-    GDPM_CUDA_TRY(cudaEventRecord(ctx->ev0, s));
+    r.prof_kind.clear();
+    GDPM_CUDA_TRY(cudaEventRecord(r.ev0, s));
     int64_t phases = 0;
-    uint64_t first = 0;
     int run_rc = GDPM_OK;
-    // Batch b tallies into buffer b%2.  Its fold runs on the side stream
-    // while batch b+1 transports into the other buffer; batch b+2 waits for
-    // that fold before reusing the buffer.
-    cudaStream_t side = ctx->overlap_fold ? ctx->side : s;
-    GDPM_CUDA_TRY(cudaEventRecord(ctx->fold_done[0], s));
-    GDPM_CUDA_TRY(cudaEventRecord(ctx->fold_done[1], s));
-    for (int b = 0; b < n_batches && run_rc == GDPM_OK; ++b) {
-        const uint64_t nb = n_hist / n_batches + (uint64_t(b) < n_hist % n_batches ? 1 : 0);
-        const int buf = ctx->overlap_fold ? (b & 1) : 0;
-        select_tally(ctx, P, buf);
-        GDPM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fold_done[buf], 0));
-        run_rc = run_batch(ctx, P, src, b, nb, first, chunk, phases);
+    if (conc) {
+        // all batches side by side: particles carry their batch, each batch
+        // has its own grid; one fold at the end
+        P.batch_stride = V;
+        P.edep = static_cast<double*>(ws.edep.p);
+        P.edep_hi = static_cast<float*>(ws.edep.p);
+        P.edep_lo = static_cast<float*>(ws.edep.p) + V * size_t(n_batches);
+        run_rc = run_phases(ctx, r, P, src, 0, n_hist, nb_small, nb_rem, chunk, phases);
         if (run_rc == GDPM_OK) {
-            GDPM_CUDA_TRY(cudaEventRecord(ctx->batch_done[buf], s));
-            GDPM_CUDA_TRY(cudaStreamWaitEvent(side, ctx->batch_done[buf], 0));
-            cudaStream_t keep = ctx->stream;
-            ctx->stream = side;
-            const size_t pi = prof_begin(ctx, 2);
-            run_rc = launch_fold(ctx, P, V, uint32_t(nb));
-            prof_end(ctx, pi);
-            ctx->stream = keep;
-            GDPM_CUDA_TRY(cudaEventRecord(ctx->fold_done[buf], side));
+            const size_t pi = prof_begin(ctx, r, s, 2);
+            run_rc = launch_fold_batches(ctx, s, P, V, n_batches, nb_small, nb_rem,
+                                         static_cast<double*>(ws.s1.p), static_cast<double*>(ws.s2.p));
+            prof_end(ctx, r, s, pi);
         }
-        first += nb;
+    } else {
+        // Batch b tallies into buffer b%2.  Its fold runs on the side stream
+        // while batch b+1 transports into the other buffer; batch b+2 waits
+        // for that fold before reusing the buffer.
+        cudaStream_t side = ctx->overlap_fold ? r.side : s;
+        GDPM_CUDA_TRY(cudaEventRecord(r.fold_done[0], s));
+        GDPM_CUDA_TRY(cudaEventRecord(r.fold_done[1], s));
+        uint64_t first = 0;
+        for (int b = 0; b < n_batches && run_rc == GDPM_OK; ++b) {
+            const uint64_t nb = n_hist / n_batches + (uint64_t(b) < n_hist % n_batches ? 1 : 0);
+            const int buf = ctx->overlap_fold ? (b & 1) : 0;
+            select_tally(r, P, buf);
+            GDPM_CUDA_TRY(cudaStreamWaitEvent(s, r.fold_done[buf], 0));
+            run_rc = run_phases(ctx, r, P, src, first, nb, nb_small, nb_rem, chunk, phases);
+            if (run_rc == GDPM_OK) {
+                GDPM_CUDA_TRY(cudaEventRecord(r.batch_done[buf], s));
+                GDPM_CUDA_TRY(cudaStreamWaitEvent(side, r.batch_done[buf], 0));
+                const size_t pi = prof_begin(ctx, r, side, 2);
+                run_rc = launch_fold_into(ctx, side, P, V, uint32_t(nb), static_cast<double*>(ws.s1.p),
+                                          static_cast<double*>(ws.s2.p));
+                prof_end(ctx, r, side, pi);
+                GDPM_CUDA_TRY(cudaEventRecord(r.fold_done[buf], side));
+            }
+            first += nb;
+        }
+        GDPM_CUDA_TRY(cudaStreamWaitEvent(s, r.fold_done[0], 0));
+        GDPM_CUDA_TRY(cudaStreamWaitEvent(s, r.fold_done[1], 0));
     }
-    GDPM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fold_done[0], 0));
-    GDPM_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fold_done[1], 0));
-    GDPM_CUDA_TRY(cudaEventRecord(ctx->ev1, s));
+    GDPM_CUDA_TRY(cudaEventRecord(r.ev1, s));
     if (run_rc != GDPM_OK) {
         cudaStreamSynchronize(s);
-        cudaStreamSynchronize(ctx->side);
-        ctx->prof_kind.clear();
+        cudaStreamSynchronize(r.side);
+        r.prof_kind.clear();
         return run_rc;
     }
     // results: straight into device outputs, or via staging for host outputs
-    const bool dev_out = (!dose_out || is_device_ptr(dose_out)) && (!sigma_out || is_device_ptr(sigma_out)) &&
-                         dose_out && sigma_out;
+    const bool dev_out = dose_out && sigma_out && is_device_ptr(dose_out) && is_device_ptr(sigma_out);
     double *dd = dose_out, *ds = sigma_out;
     if (!dev_out) {
         if ((rc = ensure(ws.stage, V * 16))) return rc;
         dd = static_cast<double*>(ws.stage.p);
         ds = dd + V;
     }
-    if ((rc = launch_finalize(ctx, P, V, n_batches, dd, ds))) return rc;
+    if ((rc = launch_finalize_into(ctx, s, P, V, n_batches, static_cast<const double*>(ws.s1.p),
+                                   static_cast<const double*>(ws.s2.p), dd, ds)))
+        return rc;
     if (!dev_out) {
         if (dose_out) GDPM_CUDA_TRY(cudaMemcpyAsync(dose_out, dd, V * 8, cudaMemcpyDefault, s));
         if (sigma_out) GDPM_CUDA_TRY(cudaMemcpyAsync(sigma_out, ds, V * 8, cudaMemcpyDefault, s));
@@ -467,14 +621,116 @@ int simulate_impl(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const gdpm_s
         st->phases = phases;
         st->launches = phases + n_batches + 2;
         float ms = 0;
-        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        cudaEventElapsedTime(&ms, r.ev0, r.ev1);
         st->transport_ms = ms;
-        st->crossings = int64_t(hc[C_CROSS]);
     }
-    prof_collect(ctx, st);
+    prof_collect(r, st);
     if (*hs & ST_QUEUE_OVERFLOW) return GDPM_E_QUEUE_OVERFLOW;
     if (*hs & ST_ITER_CAP) return GDPM_E_TIMEOUT;
     return GDPM_OK;
+}
+
+// ------------------------------------------------------------------ serving
+// Each slot is a host thread with its own runner (streams, buffers).  Slots
+// have a class: the first serve_big_slots take large requests (more than
+// serve_small_hist histories) in arrival order and run them on the whole
+// GPU, one at a time per slot; the other slots take small requests, which
+// therefore never wait behind a large one.  While a small request runs,
+// large requests launch on three quarters of the SMs and the small one runs
+// on a high-priority stream, so it gets the SMs left free.  A request is
+// admitted when its slot is free and device memory allows (continuous
+// batching: requests join as they arrive, their work overlaps on the GPU).
+// Result buffers of served requests come from a pool: cudaFree synchronizes
+// the whole device, which would make every poll wait for the other requests.
+static int result_acquire(gdpm_ctx* ctx, size_t bytes, Buffer& out) {
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (size_t k = 0; k < ctx->result_pool.size(); ++k) {
+            if (ctx->result_pool[k].bytes >= bytes) {
+                out = ctx->result_pool[k];
+                ctx->result_pool.erase(ctx->result_pool.begin() + k);
+                return GDPM_OK;
+            }
+        }
+    }
+    return ensure(out, bytes);
+}
+static void result_release(gdpm_ctx* ctx, Buffer& b) {
+    if (!b.p) return;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->result_pool.push_back(b);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// slot_class: 0 any request, 1 large requests, 2 small requests
+static void serve_worker(gdpm_ctx* ctx, int slot_class) {
+    cudaSetDevice(ctx->device);
+    Runner r;
+    const int init_rc = runner_init(r, nullptr, true);
+    r.serving = true;
+    for (;;) {
+        gdpm_request* q = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(ctx->mu);
+            for (;;) {
+                // the oldest pending request of this slot's class
+                auto mine = [&]() {
+                    for (auto it = ctx->pending.begin(); it != ctx->pending.end(); ++it)
+                        if (slot_class == 0 ||
+                            ((*it)->desc.n_histories > ctx->serve_small_hist) == (slot_class == 1))
+                            return it;
+                    return ctx->pending.end();
+                };
+                ctx->cv.wait(lk, [&] { return ctx->stop || mine() != ctx->pending.end(); });
+                if (ctx->stop) break;
+                auto it = mine();
+                gdpm_request* front = *it;
+                const gdpm_phantom* ph = front->desc.phantom;
+                const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
+                const size_t need = bytes_needed(ctx, r, V, front->desc.n_histories, front->desc.n_batches, true);
+                size_t free_b = 0, total_b = 0;
+                if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) cudaGetLastError();
+                if (ctx->running > 0 && free_b < need + ctx->serve_reserve) {
+                    // not admitted yet: wait for a running request to finish
+                    ctx->cv.wait_for(lk, std::chrono::milliseconds(2));
+                    continue;
+                }
+                ctx->pending.erase(it);
+                q = front;
+                ++ctx->running;
+                break;
+            }
+            if (ctx->stop) break;
+        }
+        int rc = init_rc;
+        if (rc == GDPM_OK) {
+            const gdpm_phantom* ph = q->desc.phantom;
+            const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
+            rc = result_acquire(ctx, V * 16, q->result);
+            if (rc == GDPM_OK) {
+                double* d = static_cast<double*>(q->result.p);
+                const uint32_t sid = q->desc.stream_id ? q->desc.stream_id : uint32_t(q->id);
+                // small requests on the high-priority stream: their CTAs get
+                // SMs first whenever a large request's CTAs finish
+                r.small = q->desc.n_histories <= ctx->serve_small_hist;
+                r.stream = r.small ? r.prio_hi : r.prio_lo;
+                if (r.small) ++ctx->small_running;
+                rc = simulate_impl(ctx, r, q->desc.phantom, q->desc.tables, q->src, sid,
+                                   q->desc.n_histories, q->desc.n_batches, d, d + V, &q->stats,
+                                   nullptr, nullptr);
+                if (r.small) --ctx->small_running;
+                r.small = false;
+            }
+        }
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            q->status = rc;
+            --ctx->running;
+        }
+        ctx->cv.notify_all();
+    }
+    runner_free(r);
 }
 
 }  // namespace gdpm
@@ -506,56 +762,40 @@ int gdpm_context_create(gdpm_ctx** out, int device, void* cuda_stream, uint64_t 
     GDPM_CUDA_TRY(cudaSetDevice(device));
     gdpm_ctx* c = new gdpm_ctx();
     c->device = device;
-    c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->seed = seed;
     cudaDeviceProp prop{};
-    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess ||
-        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
         last_cuda_error() = cudaGetLastError();
         delete c;
         return GDPM_E_CUDA;
     }
     c->sm_count = prop.multiProcessorCount;
-    bool ok = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
-    for (int k = 0; k < 2 && ok; ++k)
-        ok = cudaEventCreateWithFlags(&c->batch_done[k], cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&c->fold_done[k], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) {
-        last_cuda_error() = cudaGetLastError();
-        gdpm_context_destroy(c);
-        return GDPM_E_CUDA;
+    const int rc = runner_init(c->run, static_cast<cudaStream_t>(cuda_stream), false);
+    if (rc) {
+        runner_free(c->run);
+        delete c;
+        return rc;
     }
+    c->stream = c->run.stream;
+    c->ev0 = c->run.ev0;
+    c->ev1 = c->run.ev1;
     *out = c;
     return GDPM_OK;
 }
 
 int gdpm_context_destroy(gdpm_ctx* ctx) {
     if (!ctx) return GDPM_E_ARG;
-    if (ctx->worker.joinable()) {
-        {
-            std::lock_guard<std::mutex> lk(ctx->mu);
-            ctx->stop = true;
-        }
-        ctx->cv.notify_all();
-        ctx->worker.join();
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->stop = true;
     }
+    ctx->cv.notify_all();
+    for (std::thread& t : ctx->workers)
+        if (t.joinable()) t.join();
     cudaSetDevice(ctx->device);
-    cudaStreamSynchronize(ctx->stream);
-    if (ctx->side) cudaStreamSynchronize(ctx->side);
-    Workspace& w = ctx->ws;
-    Buffer* bs[] = {&w.edep, &w.edep2, &w.hi2, &w.lo2, &w.s1, &w.s2, &w.hi, &w.lo, &w.qph, &w.qel0, &w.qel1, &w.ctl,
-                    &w.prefix, &w.counters, &w.ledger, &w.status, &w.edges, &w.beamlets,
-                    &w.bl_cdf, &w.stage};
-    for (Buffer* b : bs) release(*b);
-    if (w.pinned_host.p) cudaFreeHost(w.pinned_host.p);
-    for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
-    for (int k = 0; k < 2; ++k) {
-        if (ctx->batch_done[k]) cudaEventDestroy(ctx->batch_done[k]);
-        if (ctx->fold_done[k]) cudaEventDestroy(ctx->fold_done[k]);
-    }
-    if (ctx->side) cudaStreamDestroy(ctx->side);
-    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
-    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (auto& kv : ctx->requests) release(kv.second->result);
+    for (Buffer& b : ctx->result_pool) release(b);
+    runner_free(ctx->run);
     delete ctx;
     return GDPM_OK;
 }
@@ -595,17 +835,40 @@ int gdpm_set_param(gdpm_ctx* ctx, int param, double v) {
         if (v < 1 || v > 64) return GDPM_E_ARG;
         ctx->speculative = int(v);
         return GDPM_OK;
-    case GDPM_PARAM_WARP_AGGREGATE:
+    case GDPM_PARAM_PROFILE:
         if (v != 0 && v != 1) return GDPM_E_ARG;
-        ctx->warp_aggregate = int(v);
+        ctx->profile = int(v);
         return GDPM_OK;
     case GDPM_PARAM_OVERLAP_FOLD:
         if (v != 0 && v != 1) return GDPM_E_ARG;
         ctx->overlap_fold = int(v);
         return GDPM_OK;
-    case GDPM_PARAM_PROFILE:
-        if (v != 0 && v != 1) return GDPM_E_ARG;
-        ctx->profile = int(v);
+    case GDPM_PARAM_SERVE_SLOTS: {
+        if (v < 1 || v > 16) return GDPM_E_ARG;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (!ctx->workers.empty()) return GDPM_E_STATE;
+        ctx->serve_slots = int(v);
+        return GDPM_OK;
+    }
+    case GDPM_PARAM_METRIC_MIN_DENSITY:
+        if (v < 0 || v > 100) return GDPM_E_ARG;
+        ctx->metric_min_rho = float(v);
+        return GDPM_OK;
+    case GDPM_PARAM_BATCH_MODE:
+        if (v != 0 && v != 1 && v != 2) return GDPM_E_ARG;
+        ctx->batch_mode = int(v);
+        return GDPM_OK;
+    case GDPM_PARAM_CONCURRENT_MAX_HIST:
+        if (v < 0 || v > 4.0e9) return GDPM_E_ARG;
+        ctx->concurrent_max_hist = uint64_t(v);
+        return GDPM_OK;
+    case GDPM_PARAM_CONCURRENT_MAX_MB:
+        if (v < 0 || v > 1e7) return GDPM_E_ARG;
+        ctx->concurrent_max_bytes = size_t(v) << 20;
+        return GDPM_OK;
+    case GDPM_PARAM_SERVE_RESERVE_MB:
+        if (v < 0 || v > 1e7) return GDPM_E_ARG;
+        ctx->serve_reserve = size_t(v) << 20;
         return GDPM_OK;
     }
     return GDPM_E_ARG;
@@ -648,7 +911,7 @@ int gdpm_phantom_destroy(gdpm_phantom* ph) {
     release(ph->mat);
     release(ph->rho);
     release(ph->rhomax);
-    release(ph->maj);
+    for (auto& kv : ph->maj) release(kv.second);
     delete ph;
     return GDPM_OK;
 }
@@ -708,37 +971,10 @@ int gdpm_tables_destroy(gdpm_tables* t) {
 
 int gdpm_source_set(gdpm_ctx* ctx, const gdpm_source_desc* s) {
     if (!ctx || !s) return GDPM_E_ARG;
-    if (s->particle != GDPM_PHOTON && s->particle != GDPM_ELECTRON) return GDPM_E_ARG;
-    if (s->geometry < GDPM_GEO_PENCIL || s->geometry > GDPM_GEO_BEAMLETS) return GDPM_E_ARG;
-    if (s->n_bins < 1 || s->n_bins > GDPM_MAX_BINS || !s->bin_edges || !s->bin_weights) return GDPM_E_ARG;
-    double ws = 0;
-    for (int j = 0; j < s->n_bins; ++j) {
-        if (s->bin_weights[j] < 0 || s->bin_edges[j + 1] < s->bin_edges[j]) return GDPM_E_ARG;
-        ws += s->bin_weights[j];
-    }
-    if (!(ws > 0) || !(s->bin_edges[0] >= 0)) return GDPM_E_ARG;
-    if (s->geometry == GDPM_GEO_BEAMLETS) {
-        if (s->n_beamlets < 1 || !s->beamlets) return GDPM_E_ARG;
-        double bw = 0;
-        for (int b = 0; b < s->n_beamlets; ++b) {
-            if (s->beamlets[size_t(b) * 17 + 16] < 0) return GDPM_E_ARG;
-            bw += s->beamlets[size_t(b) * 17 + 16];
-        }
-        if (!(bw > 0)) return GDPM_E_ARG;
-    }
-    const double dn = s->direction[0] * s->direction[0] + s->direction[1] * s->direction[1] +
-                      s->direction[2] * s->direction[2];
-    if (s->geometry == GDPM_GEO_PENCIL && !(dn > 0)) return GDPM_E_ARG;
-    gdpm_source_state& st = ctx->src;
-    st.desc = *s;
-    st.edges.assign(s->bin_edges, s->bin_edges + s->n_bins + 1);
-    st.weights.assign(s->bin_weights, s->bin_weights + s->n_bins);
-    if (s->geometry == GDPM_GEO_BEAMLETS) st.beamlets.assign(s->beamlets, s->beamlets + size_t(s->n_beamlets) * 17);
-    else st.beamlets.clear();
-    st.desc.bin_edges = nullptr;
-    st.desc.bin_weights = nullptr;
-    st.desc.beamlets = nullptr;
-    st.set = true;
+    gdpm_source_state st;
+    const int rc = source_copy(s, st);
+    if (rc) return rc;
+    ctx->src = std::move(st);
     return GDPM_OK;
 }
 
@@ -756,8 +992,9 @@ int gdpm_simulate(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_h
                   int n_batches, double* dose_out, double* sigma_out, gdpm_stats* stats_out) {
     if (!ctx) return GDPM_E_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return GDPM_E_CUDA;
-    return simulate_impl(ctx, ph, tb, ctx->src, ctx->request_id, n_histories, n_batches, dose_out,
-                         sigma_out, stats_out);
+    if (ctx->hrec && ctx->hrec_n < n_histories) return GDPM_E_ARG;
+    return simulate_impl(ctx, ctx->run, ph, tb, ctx->src, ctx->request_id, n_histories, n_batches,
+                         dose_out, sigma_out, stats_out, ctx->hrec, ctx->hrecd);
 }
 
 int gdpm_debug_philox(gdpm_ctx* ctx, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
@@ -787,26 +1024,19 @@ int gdpm_tables_export(gdpm_tables* t, int which, double* out, int64_t* count) {
     const int M = t->n_mat, n = t->n_e;
     std::vector<double> v;
     cudaStream_t s = t->ctx->stream;
-    if (which >= 0 && which <= 5) {
-        std::vector<float> a(size_t(M) * n);
-        if (which <= 2) {
-            std::vector<float> tot(size_t(M) * n);
-            std::vector<float2> cum(size_t(M) * n);
-            GDPM_CUDA_TRY(cudaMemcpyAsync(tot.data(), t->ph_tot.p, tot.size() * 4, cudaMemcpyDeviceToHost, s));
-            GDPM_CUDA_TRY(cudaMemcpyAsync(cum.data(), t->ph_cum.p, cum.size() * 8, cudaMemcpyDeviceToHost, s));
-            GDPM_CUDA_TRY(cudaStreamSynchronize(s));
-            for (size_t k = 0; k < a.size(); ++k) {
-                if (which == 0) v.push_back(cum[k].x);
-                else if (which == 1) v.push_back(cum[k].y);
-                else v.push_back(tot[k]);
-            }
-        } else {
-            std::vector<float4> el(size_t(M) * n);
-            GDPM_CUDA_TRY(cudaMemcpyAsync(el.data(), t->el.p, el.size() * 16, cudaMemcpyDeviceToHost, s));
-            GDPM_CUDA_TRY(cudaStreamSynchronize(s));
-            for (size_t k = 0; k < el.size(); ++k)
-                v.push_back(which == 3 ? el[k].x : (which == 4 ? el[k].z : el[k].w));
-        }
+    if (which >= 0 && which <= 2) {
+        std::vector<float> tot(size_t(M) * n);
+        std::vector<float2> cum(size_t(M) * n);
+        GDPM_CUDA_TRY(cudaMemcpyAsync(tot.data(), t->ph_tot.p, tot.size() * 4, cudaMemcpyDeviceToHost, s));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(cum.data(), t->ph_cum.p, cum.size() * 8, cudaMemcpyDeviceToHost, s));
+        GDPM_CUDA_TRY(cudaStreamSynchronize(s));
+        for (size_t k = 0; k < tot.size(); ++k)
+            v.push_back(which == 0 ? cum[k].x : (which == 1 ? cum[k].y : tot[k]));
+    } else if (which >= 3 && which <= 5) {
+        std::vector<float4> el(size_t(M) * n);
+        GDPM_CUDA_TRY(cudaMemcpyAsync(el.data(), t->el.p, el.size() * 16, cudaMemcpyDeviceToHost, s));
+        GDPM_CUDA_TRY(cudaStreamSynchronize(s));
+        for (size_t k = 0; k < el.size(); ++k) v.push_back(which == 3 ? el[k].x : (which == 4 ? el[k].z : el[k].w));
     } else if (which == 6) {
         for (int i = 0; i < n; ++i)
             v.push_back(std::exp(std::log(t->e_min) + i * (std::log(t->e_max) - std::log(t->e_min)) / (n - 1)));
@@ -824,36 +1054,87 @@ int gdpm_tables_export(gdpm_tables* t, int which, double* out, int64_t* count) {
 
 int gdpm_debug_sources(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_histories,
                        int n_batches, uint64_t first, uint64_t n, double* out) {
-    int rc = validate_run(ctx, ph, tb, ctx ? ctx->src : gdpm_source_state(), n_histories, n_batches);
+    if (!ctx) return GDPM_E_ARG;
+    int rc = validate_run(ctx, ph, tb, ctx->src, n_histories, n_batches);
     if (rc) return rc;
     const uint64_t nb0 = n_histories / n_batches + (n_histories % n_batches ? 1 : 0);
     if (!out || !is_device_ptr(out) || first + n > nb0) return GDPM_E_ARG;
+    Runner& r = ctx->run;
     const int n_bins = int(ctx->src.weights.size());
     std::vector<uint32_t> prefix(n_bins + 1);
     allot_prefix(ctx->src.weights, nb0, prefix.data());
-    if ((rc = ensure(ctx->ws.prefix, prefix.size() * 4))) return rc;
-    GDPM_CUDA_TRY(cudaMemcpyAsync(ctx->ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
-    if ((rc = build_majorant(ctx, ph, tb))) return rc;
+    if ((rc = ensure(r.ws.prefix, prefix.size() * 4))) return rc;
+    GDPM_CUDA_TRY(cudaMemcpyAsync(r.ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, r.stream));
     SimParams P = base_params(ctx, ph, tb, ctx->request_id);
-    if ((rc = source_upload(ctx, ctx->src, P.S))) return rc;
+    if ((rc = get_majorant(ctx, r.stream, ph, tb, &P.maj))) return rc;
+    if ((rc = source_upload(r, ctx->src, P.S))) return rc;
     PhaseArgs A{};
-    A.src_first_local = uint32_t(first);
-    A.batch_first_hist = 0;
-    A.bin_prefix = static_cast<const uint32_t*>(ctx->ws.prefix.p);
+    A.src_first = uint32_t(first);
+    A.nb_small = uint32_t(n_histories / n_batches);
+    A.nb_rem = uint32_t(n_histories % n_batches);
+    A.bin_prefix = static_cast<const uint32_t*>(r.ws.prefix.p);
     if ((rc = launch_debug_sources(ctx, P, A, n, out))) return rc;
-    GDPM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    GDPM_CUDA_TRY(cudaStreamSynchronize(r.stream));
     return GDPM_OK;
 }
 
 int gdpm_request_submit(gdpm_ctx* ctx, const gdpm_request_desc* req, uint64_t* req_id) {
-    (void)ctx; (void)req; (void)req_id;
-    return GDPM_E_STATE;
+    if (!ctx || !req || !req_id || !req->phantom || !req->tables) return GDPM_E_ARG;
+    if (req->n_batches < 2 || req->n_histories < uint64_t(req->n_batches) || req->n_histories >= (1ull << 32))
+        return GDPM_E_ARG;
+    std::unique_ptr<gdpm_request> q(new gdpm_request());
+    int rc = source_copy(&req->source, q->src);
+    if (rc) return rc;
+    if ((rc = validate_run(ctx, req->phantom, req->tables, q->src, req->n_histories, req->n_batches))) return rc;
+    q->desc = *req;
+    q->desc.source = q->src.desc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->stop) return GDPM_E_STATE;
+    if (ctx->pending.size() >= 100000) return GDPM_E_BUSY;
+    if (ctx->workers.empty()) {
+        const int big = std::min(ctx->serve_big_slots, ctx->serve_slots - 1);
+        for (int k = 0; k < ctx->serve_slots; ++k)
+            ctx->workers.emplace_back(serve_worker, ctx, ctx->serve_slots == 1 ? 0 : (k < big ? 1 : 2));
+    }
+    q->id = ctx->next_request++;
+    *req_id = q->id;
+    ctx->pending.push_back(q.get());
+    ctx->requests[q->id] = std::move(q);
+    ctx->cv.notify_all();
+    return GDPM_OK;
 }
 
 int gdpm_request_poll(gdpm_ctx* ctx, uint64_t req_id, int* done, double* dose_out, double* sigma_out,
                       gdpm_stats* stats_out) {
-    (void)ctx; (void)req_id; (void)done; (void)dose_out; (void)sigma_out; (void)stats_out;
-    return GDPM_E_STATE;
+    if (!ctx || !done) return GDPM_E_ARG;
+    std::unique_ptr<gdpm_request> q;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->requests.find(req_id);
+        if (it == ctx->requests.end()) return GDPM_E_ARG;
+        if (it->second->status == 1) {
+            *done = 0;
+            return GDPM_OK;
+        }
+        q = std::move(it->second);
+        ctx->requests.erase(it);
+    }
+    *done = 1;
+    int rc = q->status;
+    if (rc == GDPM_OK) {
+        const gdpm_phantom* ph = q->desc.phantom;
+        const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
+        const double* d = static_cast<const double*>(q->result.p);
+        if (cudaSetDevice(ctx->device) != cudaSuccess ||
+            (dose_out && cudaMemcpy(dose_out, d, V * 8, cudaMemcpyDefault) != cudaSuccess) ||
+            (sigma_out && cudaMemcpy(sigma_out, d + V, V * 8, cudaMemcpyDefault) != cudaSuccess)) {
+            last_cuda_error() = cudaGetLastError();
+            rc = GDPM_E_CUDA;
+        }
+        if (stats_out) *stats_out = q->stats;
+    }
+    result_release(ctx, q->result);
+    return rc;
 }
 
 }  // extern "C"

@@ -74,16 +74,30 @@ __host__ __device__ __forceinline__ uint64_t child_id(uint64_t parent, uint32_t 
 
 // ---------------------------------------------------------------- particle state
 // Register copy of one particle.  flags: bits 0..23 = secondaries banked so
-// far (the child index), bit 31 = positron.
+// far (the child index), bits 24..30 = batch of its history (when batches
+// run side by side), bit 31 = positron.
 struct Part {
     float x, y, z, u, v, w, E;
     int ix, iy, iz;
     uint32_t hist, pidlo, pidhi, ctr, flags;
 };
 constexpr uint32_t kPositron = 0x80000000u;
+constexpr uint32_t kBatchShift = 24, kBatchMask = 0x7F000000u;
+constexpr int kMaxConcurrentBatches = 128;
+
+// One Philox block for the transport kernels.  Out of line (it has no
+// warp-synchronous operations), so its ten unrolled rounds exist once in
+// the kernel instead of at every draw site.
+#ifndef GDPM_PHILOX_ATTR
+#define GDPM_PHILOX_ATTR __noinline__
+#endif
+static __device__ GDPM_PHILOX_ATTR uint4 philox_block(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           uint32_t k0, uint32_t k1) {
+    return philox4x32_10(make_uint4(c0, c1, c2, c3), k0, k1);
+}
 
 __device__ __forceinline__ float4 draw(Part& p, uint32_t k0, uint32_t k1) {
-    const uint4 r = philox4x32_10(make_uint4(p.hist, p.pidlo, p.pidhi, p.ctr), k0, k1);
+    const uint4 r = philox_block(p.hist, p.pidlo, p.pidhi, p.ctr, k0, k1);
     ++p.ctr;
     return make_float4(u01(r.x), u01(r.y), u01(r.z), u01(r.w));
 }

@@ -185,7 +185,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
         GDPM_CUDA_TRY(cudaMemcpyAsync(bl, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, s));
         GDPM_CUDA_TRY(cudaMemcpyAsync(cdf, c.data(), c.size() * 8, cudaMemcpyHostToDevice, s));
     }
-    if ((rc = launch_majorant_into(ctx, ph, tb, maj))) return rc;
+    if ((rc = launch_majorant_into(s, ph, tb, maj))) return rc;
     std::vector<uint32_t> prefix(size_t(n_batches) * (n_bins + 1));
     for (int b = 0; b < n_batches; ++b) {
         const uint64_t nb = n_hist / n_batches + (uint64_t(b) < n_hist % n_batches ? 1 : 0);
@@ -215,7 +215,6 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     P.key0 = uint32_t(ctx->seed);
     P.key1 = uint32_t(ctx->seed >> 32) ^ ctx->request_id;
     P.tally_mode = ctx->tally_mode;
-    P.warp_aggregate = ctx->warp_aggregate;
     P.max_iters = 1u << 22;
     P.edep = edep;
     P.edep_hi = reinterpret_cast<float*>(edep);            // FP32 pair mode: two V-float halves
@@ -260,11 +259,12 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
             if (k + 3 >= max_phases) { run_rc = GDPM_E_TIMEOUT; break; }
             const bool ph_phase = (k % 2) == 0;
             PhaseArgs A{};
-            A.batch_first_hist = uint32_t(first);
-            A.bin_prefix = prefix_d + size_t(b) * (n_bins + 1);
+            A.nb_small = uint32_t(n_hist / n_batches);
+            A.nb_rem = uint32_t(n_hist % n_batches);
+            A.bin_prefix = prefix_d;
             if (ph_phase == photon_src && left > 0) {
                 A.n_src = uint32_t(std::min<uint64_t>(left, chunk));
-                A.src_first_local = uint32_t(next);
+                A.src_first = uint32_t(first + next);
                 next += A.n_src;
                 left -= A.n_src;
             }
@@ -284,7 +284,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
                 A.out_el = qe[((k + 2) / 2) % 2];
                 A.out_el_count = ctl + size_t(k + 2) * 4 + 2;
             }
-            if ((run_rc = launch_phase(ctx, ph_phase ? GDPM_PHOTON : GDPM_ELECTRON, P, A,
+            if ((run_rc = launch_phase(ctx, s, ph_phase ? GDPM_PHOTON : GDPM_ELECTRON, P, A,
                                        A.in_count ? 0u : A.n_src)))
                 break;
             ++phases;
@@ -298,7 +298,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
                 since = 0;
             }
         }
-        if (run_rc == GDPM_OK) run_rc = launch_fold_into(ctx, P, V, uint32_t(nb), s1, s2);
+        if (run_rc == GDPM_OK) run_rc = launch_fold_into(ctx, s, P, V, uint32_t(nb), s1, s2);
         first += nb;
     }
     GDPM_CUDA_TRY(cudaEventRecord(ctx->ev1, s));
@@ -306,7 +306,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
         cudaStreamSynchronize(s);
         return run_rc;
     }
-    if ((rc = launch_finalize_into(ctx, P, V, n_batches, s1, s2, dose_out, sigma_out))) return rc;
+    if ((rc = launch_finalize_into(ctx, s, P, V, n_batches, s1, s2, dose_out, sigma_out))) return rc;
     unsigned long long hc[C_NCOUNT];
     double hl[L_NLEDGER];
     uint32_t hs = 0;

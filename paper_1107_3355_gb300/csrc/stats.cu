@@ -2,6 +2,8 @@
 // Sec. 3.1: sigma/Dmax over the D > 0.5 Dmax region) and the per-phantom
 // Woodcock majorant.  These kernels stream voxel arrays and are bound by
 // HBM bandwidth: coalesced grid-stride loops sized to the SM count.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace gdpm {
@@ -56,35 +58,112 @@ __device__ __forceinline__ double block_sum(double v, double* s_red) {
 
 // End of batch: x = E_b(v)/n_b (energy per history), sum x and x^2, clear
 // the batch tally; accumulate the deposited energy into the ledger.
-__global__ void k_fold(SimParams P, size_t V, double inv_nb, double* __restrict__ s1,
-                       double* __restrict__ s2) {
+// Streams 48 B per voxel; every thread issues the loads of its four voxel
+// pairs before any store, and the grid covers the data once.
+constexpr int kFoldPairs = 4;
+
+__global__ void __launch_bounds__(256) k_fold(SimParams P, size_t V, double inv_nb,
+                                              double* __restrict__ s1, double* __restrict__ s2) {
     __shared__ double s_red[32];
     double dep = 0.0;
-    for (size_t v = blockIdx.x * size_t(blockDim.x) + threadIdx.x; v < V;
-         v += size_t(gridDim.x) * blockDim.x) {
-        double e;
-        if (P.tally_mode == 0) {
-            e = P.edep[v];
-            P.edep[v] = 0.0;
-        } else {
-            e = double(P.edep_hi[v]) + double(P.edep_lo[v]);
-            P.edep_hi[v] = 0.f;
-            P.edep_lo[v] = 0.f;
+    const size_t n2 = V / 2;
+    const size_t base = size_t(blockIdx.x) * blockDim.x * kFoldPairs + threadIdx.x;
+    double2* __restrict__ a2 = reinterpret_cast<double2*>(s1);
+    double2* __restrict__ b2 = reinterpret_cast<double2*>(s2);
+    double2 e[kFoldPairs], a[kFoldPairs], b[kFoldPairs];
+    if (P.tally_mode == 0) {
+        double2* __restrict__ e2 = reinterpret_cast<double2*>(P.edep);
+#pragma unroll
+        for (int u = 0; u < kFoldPairs; ++u) {
+            const size_t i = base + size_t(u) * blockDim.x;
+            if (i < n2) { e[u] = e2[i]; a[u] = a2[i]; b[u] = b2[i]; }
         }
-        dep += e;
-        const double x = e * inv_nb;
-        s1[v] += x;
-        s2[v] += x * x;
+#pragma unroll
+        for (int u = 0; u < kFoldPairs; ++u) {
+            const size_t i = base + size_t(u) * blockDim.x;
+            if (i < n2) e2[i] = make_double2(0.0, 0.0);
+        }
+    } else {
+        float2* __restrict__ h2 = reinterpret_cast<float2*>(P.edep_hi);
+        float2* __restrict__ l2 = reinterpret_cast<float2*>(P.edep_lo);
+#pragma unroll
+        for (int u = 0; u < kFoldPairs; ++u) {
+            const size_t i = base + size_t(u) * blockDim.x;
+            if (i < n2) {
+                const float2 h = h2[i], l = l2[i];
+                e[u] = make_double2(double(h.x) + double(l.x), double(h.y) + double(l.y));
+                a[u] = a2[i];
+                b[u] = b2[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kFoldPairs; ++u) {
+            const size_t i = base + size_t(u) * blockDim.x;
+            if (i < n2) { h2[i] = make_float2(0.f, 0.f); l2[i] = make_float2(0.f, 0.f); }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kFoldPairs; ++u) {
+        const size_t i = base + size_t(u) * blockDim.x;
+        if (i < n2) {
+            dep += e[u].x + e[u].y;
+            const double x0 = e[u].x * inv_nb, x1 = e[u].y * inv_nb;
+            a2[i] = make_double2(a[u].x + x0, a[u].y + x1);
+            b2[i] = make_double2(fma(x0, x0, b[u].x), fma(x1, x1, b[u].y));
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (V & 1)) {
+        double ev;
+        if (P.tally_mode == 0) {
+            ev = P.edep[V - 1];
+            P.edep[V - 1] = 0.0;
+        } else {
+            ev = double(P.edep_hi[V - 1]) + double(P.edep_lo[V - 1]);
+            P.edep_hi[V - 1] = 0.f;
+            P.edep_lo[V - 1] = 0.f;
+        }
+        dep += ev;
+        const double x = ev * inv_nb;
+        s1[V - 1] += x;
+        s2[V - 1] = fma(x, x, s2[V - 1]);
     }
     const double t = block_sum(dep, s_red);
     if (threadIdx.x == 0 && t != 0.0) atomicAdd(&P.ledger[L_DEPOSITED], t);
 }
 
-// Mean and standard error per voxel in MeV/g per history; Dmax.
+// All batches at once (batches run side by side, one tally grid each):
+// s1 = sum_b E_b/n_b, s2 = sum_b (E_b/n_b)^2 per voxel.
+__global__ void __launch_bounds__(256) k_fold_batches(SimParams P, size_t V, int nbatch,
+                                                      double inv_big, double inv_small, int n_big,
+                                                      double* __restrict__ s1, double* __restrict__ s2) {
+    __shared__ double s_red[32];
+    double dep = 0.0;
+    for (size_t v = blockIdx.x * size_t(blockDim.x) + threadIdx.x; v < V;
+         v += size_t(gridDim.x) * blockDim.x) {
+        double acc1 = 0.0, acc2 = 0.0;
+        for (int b = 0; b < nbatch; ++b) {
+            const size_t k = size_t(b) * V + v;
+            const double e = P.tally_mode == 0 ? P.edep[k] : double(P.edep_hi[k]) + double(P.edep_lo[k]);
+            dep += e;
+            const double x = e * (b < n_big ? inv_big : inv_small);
+            acc1 += x;
+            acc2 = fma(x, x, acc2);
+        }
+        s1[v] = acc1;
+        s2[v] = acc2;
+    }
+    const double t = block_sum(dep, s_red);
+    if (threadIdx.x == 0 && t != 0.0) atomicAdd(&P.ledger[L_DEPOSITED], t);
+}
+
+// Mean and standard error per voxel in MeV/g per history; Dmax.  FP64
+// division and square root are slow on this part, so 1/mass and sqrt(var)
+// start from FP32 estimates and take one FP64 Newton step each (relative
+// error ~1e-14).
 __global__ void k_finalize(const double* __restrict__ s1, const double* __restrict__ s2,
                            const float* __restrict__ rho, size_t V, int nb, double dvol,
                            double* __restrict__ dose, double* __restrict__ sigma,
-                           unsigned long long* dmax_bits) {
+                           unsigned long long* dmax_bits, float metric_min_rho) {
     double mx = 0.0;
     const double inv_n = 1.0 / nb;
     const double inv_nn1 = 1.0 / (double(nb) * (nb - 1));
@@ -92,11 +171,20 @@ __global__ void k_finalize(const double* __restrict__ s1, const double* __restri
          v += size_t(gridDim.x) * blockDim.x) {
         const double mean = s1[v] * inv_n;
         const double var = fmax(0.0, (s2[v] - nb * mean * mean) * inv_nn1);
-        const double inv_mass = 1.0 / (double(rho[v]) * dvol);
-        const double d = mean * inv_mass;
+        const float r = rho[v];
+        const double mass = double(r) * dvol;
+        double im = double(1.0f / float(mass));
+        im = im * fma(-mass, im, 2.0);                       // Newton step for 1/mass
+        const double d = mean * im;
+        double sd = 0.0;
+        if (var > 0.0) {
+            double y = double(rsqrtf(float(var)));
+            y = y * fma(-0.5 * var * y, y, 1.5);             // Newton step for 1/sqrt(var)
+            sd = var * y;
+        }
         if (dose) dose[v] = d;
-        if (sigma) sigma[v] = sqrt(var) * inv_mass;
-        mx = fmax(mx, d);
+        if (sigma) sigma[v] = sd * im;
+        if (r >= metric_min_rho) mx = fmax(mx, d);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
@@ -104,15 +192,18 @@ __global__ void k_finalize(const double* __restrict__ s1, const double* __restri
         atomicMax(dmax_bits, (unsigned long long)__double_as_longlong(mx));
 }
 
-// Sec. 3.1 precision metric: mean of sigma over voxels with D > 0.5 Dmax.
-__global__ void k_metric(const double* __restrict__ dose, const double* __restrict__ sigma, size_t V,
-                         const unsigned long long* dmax_bits, double* ledger) {
+// Sec. 3.1 precision metric: mean of sigma over voxels with D > 0.5 Dmax
+// (both over voxels at least as dense as metric_min_rho: air voxels of tiny
+// mass have meaningless dose noise).
+__global__ void k_metric(const double* __restrict__ dose, const double* __restrict__ sigma,
+                         const float* __restrict__ rho, size_t V,
+                         const unsigned long long* dmax_bits, double* ledger, float metric_min_rho) {
     __shared__ double s_red[32];
     const double dmax = __longlong_as_double((long long)*dmax_bits);
     double acc = 0.0, cnt = 0.0;
     for (size_t v = blockIdx.x * size_t(blockDim.x) + threadIdx.x; v < V;
          v += size_t(gridDim.x) * blockDim.x) {
-        if (dose[v] > 0.5 * dmax) {
+        if (dose[v] > 0.5 * dmax && rho[v] >= metric_min_rho) {
             acc += sigma[v];
             cnt += 1.0;
         }
@@ -151,70 +242,48 @@ int phantom_density_max(gdpm_ctx* ctx, gdpm_phantom* ph) {
     return GDPM_OK;
 }
 
-int build_majorant(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* t) {
-    if (ph->maj_tables_id == t->id && ph->maj.p) return GDPM_OK;
-    int rc = ensure(ph->maj, sizeof(float) * t->n_e);
-    if (rc) return rc;
-    k_majorant<<<(t->n_e + 127) / 128, 128, 0, ctx->stream>>>(
-        static_cast<const float*>(t->ph_tot.p), static_cast<const float*>(ph->rhomax.p), t->n_mat,
-        t->n_e, static_cast<float*>(ph->maj.p));
-    GDPM_CUDA_TRY(cudaGetLastError());
-    ph->maj_tables_id = t->id;
-    return GDPM_OK;
-}
-
-int launch_fold(gdpm_ctx* ctx, const SimParams& P, size_t V, uint32_t nb) {
-    k_fold<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(P, V, 1.0 / double(nb),
-                                                         static_cast<double*>(ctx->ws.s1.p),
-                                                         static_cast<double*>(ctx->ws.s2.p));
-    GDPM_CUDA_TRY(cudaGetLastError());
-    return GDPM_OK;
-}
-
-int launch_finalize(gdpm_ctx* ctx, const SimParams& P, size_t V, int n_batches, double* dose,
-                    double* sigma) {
-    const double dvol = double(P.dx) * P.dy * P.dz;
-    unsigned long long* dmax_bits = reinterpret_cast<unsigned long long*>(&P.ledger[L_DMAX]);
-    k_finalize<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(
-        static_cast<const double*>(ctx->ws.s1.p), static_cast<const double*>(ctx->ws.s2.p), P.rho, V,
-        n_batches, dvol, dose, sigma, dmax_bits);
-    GDPM_CUDA_TRY(cudaGetLastError());
-    if (dose && sigma) {
-        k_metric<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(dose, sigma, V, dmax_bits, P.ledger);
-        GDPM_CUDA_TRY(cudaGetLastError());
-    }
-    return GDPM_OK;
-}
-
 }  // namespace gdpm
 
 namespace gdpm {
 
-// Variants of the launchers above that take every buffer explicitly (used by
-// the no-allocation entry point, whose buffers live in a static array).
-int launch_majorant_into(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* t, float* maj) {
-    k_majorant<<<(t->n_e + 127) / 128, 128, 0, ctx->stream>>>(
-        static_cast<const float*>(t->ph_tot.p), static_cast<const float*>(ph->rhomax.p), t->n_mat,
-        t->n_e, maj);
+// Launchers with every buffer and the stream explicit (a dose calculation's
+// buffers belong to its runner, or to the no-allocation static array).
+int launch_majorant_into(cudaStream_t st, gdpm_phantom* ph, gdpm_tables* t, float* maj) {
+    k_majorant<<<(t->n_e + 127) / 128, 128, 0, st>>>(static_cast<const float*>(t->ph_tot.p),
+                                                     static_cast<const float*>(ph->rhomax.p),
+                                                     t->n_mat, t->n_e, maj);
     GDPM_CUDA_TRY(cudaGetLastError());
     return GDPM_OK;
 }
 
-int launch_fold_into(gdpm_ctx* ctx, const SimParams& P, size_t V, uint32_t nb, double* s1, double* s2) {
-    k_fold<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(P, V, 1.0 / double(nb), s1, s2);
+int launch_fold_into(gdpm_ctx* ctx, cudaStream_t st, const SimParams& P, size_t V, uint32_t nb,
+                     double* s1, double* s2) {
+    const size_t per_block = size_t(256) * kFoldPairs;
+    const unsigned grid = unsigned(std::max<size_t>(1, (V / 2 + per_block - 1) / per_block));
+    k_fold<<<grid, 256, 0, st>>>(P, V, 1.0 / double(nb), s1, s2);
     GDPM_CUDA_TRY(cudaGetLastError());
     return GDPM_OK;
 }
 
-int launch_finalize_into(gdpm_ctx* ctx, const SimParams& P, size_t V, int n_batches,
-                         const double* s1, const double* s2, double* dose, double* sigma) {
+int launch_fold_batches(gdpm_ctx* ctx, cudaStream_t st, const SimParams& P, size_t V, int n_batches,
+                        uint32_t nb_small, uint32_t nb_rem, double* s1, double* s2) {
+    k_fold_batches<<<ctx->sm_count * 8, 256, 0, st>>>(P, V, n_batches, 1.0 / double(nb_small + 1),
+                                                        1.0 / double(nb_small), int(nb_rem), s1, s2);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+int launch_finalize_into(gdpm_ctx* ctx, cudaStream_t st, const SimParams& P, size_t V,
+                         int n_batches, const double* s1, const double* s2, double* dose,
+                         double* sigma) {
     const double dvol = double(P.dx) * P.dy * P.dz;
     unsigned long long* dmax_bits = reinterpret_cast<unsigned long long*>(&P.ledger[L_DMAX]);
-    k_finalize<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(s1, s2, P.rho, V, n_batches, dvol, dose,
-                                                             sigma, dmax_bits);
+    k_finalize<<<ctx->sm_count * 4, 256, 0, st>>>(s1, s2, P.rho, V, n_batches, dvol, dose, sigma,
+                                                    dmax_bits, ctx->metric_min_rho);
     GDPM_CUDA_TRY(cudaGetLastError());
     if (dose && sigma) {
-        k_metric<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(dose, sigma, V, dmax_bits, P.ledger);
+        k_metric<<<ctx->sm_count * 4, 256, 0, st>>>(dose, sigma, P.rho, V, dmax_bits, P.ledger,
+                                                      ctx->metric_min_rho);
         GDPM_CUDA_TRY(cudaGetLastError());
     }
     return GDPM_OK;

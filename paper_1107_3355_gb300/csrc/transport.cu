@@ -8,15 +8,21 @@
 // terminates, so warps stay full until the input is drained instead of
 // idling on their longest history.  A lane advances its particle by one
 // step per iteration:
-//   photon:   one Woodcock flight against the majorant (Sec. 2.1) and, if
-//             the collision is real, one Compton / photoelectric / pair event;
+//   photon:   Woodcock flights against the majorant until a real collision
+//             (Sec. 2.1), then one Compton / photoelectric / pair event;
 //   electron: one condensed-history step (CSDA loss over the step, random
 //             hinge multiple scattering, voxel walk depositing along the
 //             path) and, at a hard-event candidate, Moller or
 //             bremsstrahlung (Sec. 2.1).
+// A step runs with whatever lanes it diverges into and uses no warp-wide
+// operation.  It leaves its event counts and the secondaries it created in
+// registers; at the top of the next iteration, where all 32 lanes are
+// present, the warp banks those secondaries into the queues and adds the
+// counts with full-warp ballots and reductions.
 // Tables live in shared memory (Sec. 2.2.2 reads them by linear
 // interpolation); random numbers come from Philox4x32-10 keyed per history
 // and particle, so results do not depend on scheduling.
+#include <algorithm>
 #include <cfloat>
 
 #include "internal.h"
@@ -25,40 +31,38 @@ namespace gdpm {
 namespace {
 
 constexpr float kInf = FLT_MAX;
+constexpr float kEs = 21.2f;            // Rossi-Greisen scattering energy, MeV
+constexpr uint32_t kFull = 0xffffffffu;
 
 #ifndef GDPM_MIN_CTAS
 #define GDPM_MIN_CTAS 4
 #endif
-
-constexpr float kEs = 21.2f;            // Rossi-Greisen scattering energy, MeV
 
 // ---------------------------------------------------------------- ledger/tally
 struct Acc {
     double src, esc, disc;
 };
 
-__device__ __forceinline__ void tally(const SimParams& P, uint32_t vox, float e) {
+// Event bits of one step (counted at the warp-uniform loop top).
+enum : uint32_t {
+    EV_REAL = 1u, EV_COMPTON = 2u, EV_PHOTO = 4u, EV_PAIR = 8u, EV_TERM = 16u, EV_LOCAL = 32u,
+    EV_STEP = 64u, EV_MOLLER = 128u, EV_BREMS = 256u, EV_ANNIHIL = 512u
+};
+
+// Secondaries created by one step: n of them (0..2) at the particle's
+// current position; the second is a positron (pair) or, for photons, the
+// back-to-back partner (annihilation).
+struct Sec {
+    int n;
+    bool photon, pos2;
+    float E1, E2, dx, dy, dz;
+};
+
+// Deposit e MeV in voxel vox of the tally of the batch in `flags`.
+__device__ __forceinline__ void tally(const SimParams& P, uint32_t flags, uint32_t vox0, float e) {
+    const size_t vox = size_t(vox0) + size_t((flags & kBatchMask) >> kBatchShift) * P.batch_stride;
     if (P.tally_mode == 0) {
-        if (P.warp_aggregate) {
-            const uint32_t mask = __activemask();
-            const uint32_t peers = __match_any_sync(mask, vox);
-            const int lane = int(lane_id());
-            const int leader = __ffs(peers) - 1;
-            const uint32_t rounds = __reduce_max_sync(mask, uint32_t(__popc(peers))) - 1u;
-            uint32_t others = peers & ~(1u << lane);
-            double acc = e;
-            for (uint32_t r = 0; r < rounds; ++r) {
-                const int src = (lane == leader && others) ? __ffs(others) - 1 : lane;
-                const float v = __shfl_sync(mask, e, src);
-                if (lane == leader && others) {
-                    acc += v;
-                    others &= others - 1u;
-                }
-            }
-            if (lane == leader) atomicAdd(&P.edep[vox], acc);
-        } else {
-            atomicAdd(&P.edep[vox], double(e));
-        }
+        atomicAdd(&P.edep[vox], double(e));
     } else {
         // FP32 pair: hi accumulates, lo collects the exact rounding error of
         // each addition (TwoSum on the value the atomic returned).
@@ -79,51 +83,6 @@ __device__ __forceinline__ void hist_count(const SimParams& P, uint32_t hist, in
 }
 __device__ __forceinline__ void hist_add(const SimParams& P, uint32_t hist, int k, double v) {
     if (P.hrec) atomicAdd(&P.hrecd[size_t(hist) * 2 + k], v);
-}
-
-// Bank a secondary in queue q (Sec. 2.2.1 stacks).  Electrons and photons
-// below their absorption energy are deposited on the spot (returns false);
-// positrons are always banked.  The child's Philox stream is keyed by a
-// counter-derived id (parent id, child index), so it does not depend on when
-// or where the child is transported.  Kept inline: its warp-synchronous slot
-// reservation needs the caller's converged lane set, which an out-of-line call
-// does not preserve (measured: an out-of-line version lost and duplicated
-// queue slots).
-__device__ __forceinline__ bool bank(const SimParams& P, const Queue& q, uint32_t* tail,
-                                  uint32_t hist, uint32_t pidlo, uint32_t pidhi, uint32_t child,
-                                  int ix, int iy, int iz, bool photon, bool positron, float E,
-                                  float x, float y, float z, float u, float v, float w,
-                                  uint32_t* s_cnt) {
-    if (!positron && E < (photon ? P.T.eabs_ph : P.T.eabs_el)) {
-        tally(P, vox_of(P, ix, iy, iz), E);
-        count_event(s_cnt, C_LOCAL_DEP);
-        return false;
-    }
-    Part c;
-    c.x = x; c.y = y; c.z = z; c.u = u; c.v = v; c.w = w; c.E = E;
-    c.ix = ix; c.iy = iy; c.iz = iz;
-    c.hist = hist;
-    const uint64_t id = child_id(uint64_t(pidlo) | (uint64_t(pidhi) << 32), child);
-    c.pidlo = uint32_t(id);
-    c.pidhi = uint32_t(id >> 32);
-    c.ctr = 0;
-    c.flags = positron ? kPositron : 0u;
-    const uint32_t slot = reserve_slot(tail);
-    if (slot < q.capacity) queue_store(q, slot, c);
-    else atomicOr(P.status, ST_QUEUE_OVERFLOW);
-    count_event(s_cnt, photon ? C_PH_CREATED : C_EL_CREATED);
-    count_event(s_cnt, photon ? C_PUSH_PH : C_PUSH_EL);
-    hist_count(P, hist, 3);
-    return true;
-}
-
-// Bank a secondary of particle p at p's position and voxel.
-__device__ __forceinline__ void bank_from(const SimParams& P, const Queue& q, uint32_t* tail, Part& p,
-                                          bool photon, bool positron, float E, float u, float v,
-                                          float w, uint32_t* s_cnt) {
-    if (bank(P, q, tail, p.hist, p.pidlo, p.pidhi, p.flags & 0xFFFFFFu, p.ix, p.iy, p.iz, photon,
-             positron, E, p.x, p.y, p.z, u, v, w, s_cnt))
-        ++p.flags;
 }
 
 // ---------------------------------------------------------------- samplers
@@ -227,17 +186,30 @@ __device__ bool enter_box(const SimParams& P, Part& p) {
 // spectrum interval allotment (uniform inside the interval), position and
 // direction from the source geometry.  Draw 0 of the primary's stream:
 // (u-position, v-position, energy, beamlet).
-__device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t idx, bool photon,
-                             Part& p, Acc& acc, uint32_t* s_cnt) {
+__device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t idx, Part& p,
+                             Acc& acc) {
     const DevSource& S = P.S;
-    const uint32_t local = A.src_first_local + idx;
-    p.hist = A.batch_first_hist + local;
-    p.pidlo = 1u; p.pidhi = 0u; p.ctr = 0u; p.flags = 0u;
+    // batch b of history h and h's index within it (batches are contiguous;
+    // the first nb_rem hold nb_small + 1 histories)
+    const uint32_t h = A.src_first + idx;
+    const uint32_t big = A.nb_small + 1u, split = A.nb_rem * big;
+    uint32_t b, local;
+    if (h < split) {
+        b = h / big;
+        local = h - b * big;
+    } else {
+        b = A.nb_rem + (h - split) / A.nb_small;
+        local = (h - split) - (b - A.nb_rem) * A.nb_small;
+    }
+    const uint32_t* prefix = A.bin_prefix + size_t(b) * (S.n_bins + 1);
+    p.hist = h;
+    p.pidlo = 1u; p.pidhi = 0u; p.ctr = 0u;
+    p.flags = (b << kBatchShift) & kBatchMask;
     const float4 r = draw(p, P.key0, P.key1);
     int lo = 0, hi = S.n_bins;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (A.bin_prefix[mid] <= local) lo = mid; else hi = mid;
+        if (prefix[mid] <= local) lo = mid; else hi = mid;
     }
     p.E = fmaf(S.edges[lo + 1] - S.edges[lo], r.z, S.edges[lo]);
     if (S.geometry == GDPM_GEO_PENCIL) {
@@ -271,12 +243,9 @@ __device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t id
         p.u = dx * n; p.v = dy * n; p.w = dz * n;
     }
     acc.src += p.E;
-    count_event(s_cnt, C_PRIMARY);
-    count_event(s_cnt, photon ? C_PH_CREATED : C_EL_CREATED);
     if (!enter_box(P, p)) {
         acc.esc += p.E;
         hist_add(P, p.hist, 0, p.E);
-        count_event(s_cnt, photon ? C_PH_TERMINATED : C_EL_TERMINATED);
         return false;
     }
     voxel_of(P, p);
@@ -290,12 +259,12 @@ struct PhSmem {
     const float2* cum;
 };
 
-__device__ void photon_step(const SimParams& P, const PhaseArgs& A, const PhSmem& S, Part& p,
-                            bool& active, Acc& acc, uint32_t* s_cnt) {
+__device__ void photon_step(const SimParams& P, const PhSmem& S, Part& p, bool& active, Acc& acc,
+                            uint32_t& evb, uint32_t& evn, Sec& sec) {
     const DevTables& T = P.T;
     if (p.E < T.eabs_ph) {   // only a source photon below the cutoff reaches here
-        tally(P, vox_of(P, p.ix, p.iy, p.iz), p.E);
-        count_event(s_cnt, C_PH_TERMINATED);
+        tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), p.E);
+        evb |= EV_TERM;
         active = false;
         return;
     }
@@ -310,7 +279,6 @@ __device__ void photon_step(const SimParams& P, const PhaseArgs& A, const PhSmem
     uint32_t vox;
     float mt;
     int mi;
-    uint32_t flights = 0;
     for (;;) {
         r = draw(p, P.key0, P.key1);
         const float s = -__logf(r.x) * inv_mm;
@@ -318,14 +286,13 @@ __device__ void photon_step(const SimParams& P, const PhaseArgs& A, const PhSmem
         p.y = fmaf(s, p.v, p.y);
         p.z = fmaf(s, p.w, p.z);
         if (!inside(P, p.x, p.y, p.z)) {
-            count_n(s_cnt, C_PH_FLIGHTS, flights);
             acc.esc += p.E;
             hist_add(P, p.hist, 0, p.E);
-            count_event(s_cnt, C_PH_TERMINATED);
+            evb |= EV_TERM;
             active = false;
             return;
         }
-        ++flights;
+        ++evn;
         voxel_of(P, p);
         vox = vox_of(P, p.ix, p.iy, p.iz);
         const int m = __ldg(&P.mat[vox]);
@@ -334,48 +301,49 @@ __device__ void photon_step(const SimParams& P, const PhaseArgs& A, const PhSmem
         mt = lerpf(S.tot[mi], S.tot[mi + 1], f);
         if (r.y * mm < mt * rho) break;             // real; otherwise a virtual (delta) collision
     }
-    count_n(s_cnt, C_PH_FLIGHTS, flights);
-    count_event(s_cnt, C_PH_REAL);
+    evb |= EV_REAL;
     hist_count(P, p.hist, 0);
     const float2 c0 = S.cum[mi], c1 = S.cum[mi + 1];
     const float rr = r.z * mt;
+    sec.n = 1;
+    sec.photon = false;
+    sec.dx = p.u; sec.dy = p.v; sec.dz = p.w;
     if (rr < lerpf(c0.x, c1.x, f)) {
         // Compton (Klein-Nishina); recoil electron along E u - E' u'
-        count_event(s_cnt, C_COMPTON);
+        evb |= EV_COMPTON;
         const float E = p.E;
         float eps, cost, rphi;
         sample_kn(p, P, E, eps, cost, rphi);
         float cp, sp;
         cossin_2pi(rphi, cp, sp);
-        const float u0 = p.u, v0 = p.v, w0 = p.w;
         rotate(p.u, p.v, p.w, cost, cp, sp);
-        const float Ep = eps * E, Te = E - Ep;
-        float ex = E * u0 - Ep * p.u, ey = E * v0 - Ep * p.v, ez = E * w0 - Ep * p.w;
-        const float en = rsqrtf(ex * ex + ey * ey + ez * ez);
-        bank_from(P, A.out_el, A.out_el_count, p, false, false, Te, ex * en, ey * en,
-             ez * en, s_cnt);
+        const float Ep = eps * E;
+        sec.E1 = E - Ep;
+        float dx = E * sec.dx - Ep * p.u, dy = E * sec.dy - Ep * p.v, dz = E * sec.dz - Ep * p.w;
+        const float en = rsqrtf(dx * dx + dy * dy + dz * dz);
+        sec.dx = dx * en; sec.dy = dy * en; sec.dz = dz * en;
+        sec.pos2 = false;
         if (Ep < T.eabs_ph) {
-            tally(P, vox, Ep);
-            count_event(s_cnt, C_LOCAL_DEP);
-            count_event(s_cnt, C_PH_TERMINATED);
+            tally(P, p.flags, vox, Ep);
+            evb |= EV_LOCAL | EV_TERM;
             active = false;
         } else {
             p.E = Ep;
         }
     } else if (rr < lerpf(c0.y, c1.y, f)) {
         // photoelectric: photon absorbed, photoelectron along the photon
-        count_event(s_cnt, C_PHOTO);
-        bank_from(P, A.out_el, A.out_el_count, p, false, false, p.E, p.u, p.v, p.w, s_cnt);
-        count_event(s_cnt, C_PH_TERMINATED);
+        evb |= EV_PHOTO | EV_TERM;
+        sec.E1 = p.E;
+        sec.pos2 = false;
         active = false;
     } else {
         // pair: electron takes r.w of the kinetic energy, positron the rest
-        count_event(s_cnt, C_PAIR);
+        evb |= EV_PAIR | EV_TERM;
         const float tav = p.E - 2.f * kMC2f;
-        const float t1 = r.w * tav, t2 = tav - t1;
-        bank_from(P, A.out_el, A.out_el_count, p, false, false, t1, p.u, p.v, p.w, s_cnt);
-        bank_from(P, A.out_el, A.out_el_count, p, false, true, t2, p.u, p.v, p.w, s_cnt);
-        count_event(s_cnt, C_PH_TERMINATED);
+        sec.E1 = r.w * tav;
+        sec.E2 = tav - sec.E1;
+        sec.n = 2;
+        sec.pos2 = true;
         active = false;
     }
 }
@@ -416,7 +384,7 @@ __device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& 
             p.y = fmaf(t, p.v, p.y);
             p.z = fmaf(t, p.w, p.z);
             if (!defer_last) {
-                tally(P, vox, dpm * left);
+                tally(P, p.flags, vox, dpm * left);
                 dep += dpm * left;
             }
             return false;
@@ -426,7 +394,7 @@ __device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& 
         p.z = fmaf(tb, p.w, p.z);
         const float piece = rho * tb;
         if (piece > 0.f) {
-            tally(P, vox, dpm * piece);
+            tally(P, p.flags, vox, dpm * piece);
             dep += dpm * piece;
         }
         left -= piece;
@@ -450,31 +418,7 @@ __device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& 
     return true;
 }
 
-// End of an electron or positron track inside the phantom: residual energy
-// deposited; a positron then annihilates into two back-to-back 0.511 MeV
-// photons (isotropic), or its rest energy is discarded (Sec. 2.1, Sec. 4).
-__device__ void electron_absorb(const SimParams& P, const PhaseArgs& A, Part& p, Acc& acc,
-                                uint32_t* s_cnt) {
-    tally(P, vox_of(P, p.ix, p.iy, p.iz), p.E);
-    count_event(s_cnt, C_EL_TERMINATED);
-    if (!(p.flags & kPositron)) return;
-    if (!P.S.annihilation) {
-        acc.disc += 2.0 * kMC2;
-        return;
-    }
-    const float4 a = draw(p, P.key0, P.key1);
-    const float cost = 2.f * a.x - 1.f;
-    const float sint = sqrtf(fmaxf(0.f, 1.f - cost * cost));
-    float cp, sp;
-    cossin_2pi(a.y, cp, sp);
-    const float dx = sint * cp, dy = sint * sp, dz = cost;
-    count_event(s_cnt, C_ANNIHIL);
-    bank_from(P, A.out_ph, A.out_ph_count, p, true, false, kMC2f, dx, dy, dz, s_cnt);
-    bank_from(P, A.out_ph, A.out_ph_count, p, true, false, kMC2f, -dx, -dy, -dz, s_cnt);
-}
-
-__device__ void electron_escape(const SimParams& P, Part& p, float energy, Acc& acc,
-                                uint32_t* s_cnt) {
+__device__ void electron_escape(const SimParams& P, Part& p, float energy, Acc& acc) {
     double e = energy;
     if (p.flags & kPositron) {
         if (P.S.annihilation) e += 2.0 * kMC2;
@@ -482,127 +426,219 @@ __device__ void electron_escape(const SimParams& P, Part& p, float energy, Acc& 
     }
     acc.esc += e;
     hist_add(P, p.hist, 0, e);
-    count_event(s_cnt, C_EL_TERMINATED);
 }
 
-__device__ void electron_step(const SimParams& P, const PhaseArgs& A, const ElSmem& S, Part& p,
-                              bool& active, Acc& acc, uint32_t* s_cnt) {
+// One condensed-history step of an electron or positron (Sec. 2.1), or its
+// absorption.
+__device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool& active, Acc& acc,
+                              uint32_t& evb, uint32_t& evn, Sec& sec) {
     const DevTables& T = P.T;
-    if (p.E < T.eabs_el) {
-        electron_absorb(P, A, p, acc, s_cnt);
+    bool absorb = p.E < T.eabs_el;
+    if (!absorb) {
+        const float4 r = draw(p, P.key0, P.key1);
+        evb |= EV_STEP;
+        hist_count(P, p.hist, 1);
+        const int m = __ldg(&P.mat[vox_of(P, p.ix, p.iy, p.iz)]);
+        int i;
+        float f;
+        grid_pos(T, p.E, i, f);
+        const int mi = m * T.n_e + i;
+        float4 a0 = S.el[mi], a1 = S.el[mi + 1];
+        // step limits as mass thickness in the start material: reach E_abs,
+        // hard-event candidate, or the multiple-scattering step
+        const float R0 = lerpf(a0.x, a1.x, f);
+        const float xms = lerpf(a0.y, a1.y, f);
+        const float xcut = R0 - T.r_eabs[m];
+        const float xhard = (T.flags & GDPM_FLAG_NO_HARD) ? kInf : -__logf(r.x) * T.inv_sigmax[m];
+        int ev;
+        float xs;
+        if (xcut <= xms && xcut <= xhard) { ev = 0; xs = xcut; }
+        else if (xhard <= xms) { ev = 1; xs = xhard; }
+        else { ev = 2; xs = xms; }
+        xs = fmaxf(xs, 0.f);
+        float Tend;
+        if (ev == 0) {
+            Tend = T.eabs_el;
+        } else {
+            const float rr = (R0 - xs - T.rinv_lo[m]) * T.rinv_idr[m];
+            const int j = min(max(int(floorf(rr)), 0), T.n_r - 2);
+            const float g = fminf(fmaxf(rr - float(j), 0.f), 1.f);
+            const float* ri = S.rinv + m * T.n_r;
+            Tend = fminf(lerpf(ri[j], ri[j + 1], g), p.E);
+        }
+        const float Tk = p.E;
+        const float dT = Tk - Tend;
+        if (P.hrec) hist_add(P, p.hist, 1, double(xs));
+        // multiple scattering at the mid-step energy
+        const float Tm = 0.5f * (Tk + Tend);
+        const float pbc = Tm * (Tm + 2.f * kMC2f) / (Tm + kMC2f);
+        const float q = kEs / pbc;
+        const float G1 = xs * q * q * 0.5f * T.inv_x0[m];
+        float mu;
+        if (G1 >= 1.f) {
+            mu = 2.f * r.z - 1.f;
+        } else {
+            const float Asc = screening_A(T, S.atab, G1);
+            mu = 1.f - 2.f * Asc * r.z / (1.f - r.z + Asc);
+        }
+        float cp, sp;
+        cossin_2pi(r.w, cp, sp);
+        const float dpm = xs > 0.f ? dT / xs : 0.f;
+        float dep = 0.f;
+        // random hinge: zeta*xs straight, deflect, (1-zeta)*xs straight
+        bool out = walk(P, p, r.y * xs, dpm, dep, false, evn);
+        if (!out) {
+            rotate(p.u, p.v, p.w, mu, cp, sp);
+            out = walk(P, p, (1.f - r.y) * xs, dpm, dep, true, evn);
+        }
+        if (out) {
+            electron_escape(P, p, Tk - dep, acc);
+            evb |= EV_TERM;
+            active = false;
+            return;
+        }
+        tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), dT - dep);
+        p.E = Tend;
+        if (ev == 0) {
+            absorb = true;
+        } else if (ev == 1) {
+            // hard-event candidate: accept with Sigma_h(T)/Sigma_max (start material)
+            const float4 v = draw(p, P.key0, P.key1);
+            const float Tn = p.E, wcc = T.eabs_el, wcb = T.eabs_ph;
+            float sm = 0.f, sb = 0.f;
+            if (Tn > wcb || Tn > 2.f * wcc) {
+                grid_pos(T, Tn, i, f);
+                const int mj = m * T.n_e + i;
+                a0 = S.el[mj];
+                a1 = S.el[mj + 1];
+                if (Tn > 2.f * wcc) sm = lerpf(a0.z, a1.z, f);
+                if (Tn > wcb) sb = lerpf(a0.w, a1.w, f);
+            }
+            const float sh = sm + sb;
+            if (v.x * T.sigmax[m] < sh) {
+                hist_count(P, p.hist, 2);
+                sec.n = 1;
+                sec.pos2 = false;
+                if (v.y * sh < sm) {
+                    evb |= EV_MOLLER;
+                    float eps, rphi;
+                    sample_moller(p, P, Tn, wcc, eps, rphi);
+                    float c, sn;
+                    cossin_2pi(rphi, c, sn);
+                    const float W = eps * Tn, Tp = Tn - W;
+                    const float cd = sqrtf(W * (Tn + 2.f * kMC2f) / (Tn * (W + 2.f * kMC2f)));
+                    const float cpr = sqrtf(Tp * (Tn + 2.f * kMC2f) / (Tn * (Tp + 2.f * kMC2f)));
+                    sec.dx = p.u; sec.dy = p.v; sec.dz = p.w;
+                    rotate(sec.dx, sec.dy, sec.dz, cd, c, sn);
+                    sec.photon = false;
+                    sec.E1 = W;
+                    rotate(p.u, p.v, p.w, cpr, -c, -sn);
+                    p.E = Tp;
+                } else {
+                    evb |= EV_BREMS;
+                    const float k = wcb * exp2f(v.z * __log2f(Tn / wcb));
+                    sec.photon = true;
+                    sec.E1 = k;
+                    sec.dx = p.u; sec.dy = p.v; sec.dz = p.w;
+                    p.E = Tn - k;
+                }
+            }
+        }
+    }
+    if (absorb) {
+        // end of track: residual energy deposited here; a positron then
+        // annihilates into two back-to-back 0.511 MeV photons (isotropic),
+        // or its rest energy is discarded (Sec. 2.1, Sec. 4)
+        tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), p.E);
+        evb |= EV_TERM;
         active = false;
-        return;
+        if (p.flags & kPositron) {
+            if (!P.S.annihilation) {
+                acc.disc += 2.0 * kMC2;
+            } else {
+                const float4 a = draw(p, P.key0, P.key1);
+                const float cost = 2.f * a.x - 1.f;
+                const float sint = sqrtf(fmaxf(0.f, 1.f - cost * cost));
+                float cp, sp;
+                cossin_2pi(a.y, cp, sp);
+                evb |= EV_ANNIHIL;
+                sec.n = 2;
+                sec.photon = true;
+                sec.pos2 = false;
+                sec.E1 = sec.E2 = kMC2f;
+                sec.dx = sint * cp; sec.dy = sint * sp; sec.dz = cost;
+            }
+        }
     }
-    const float4 r = draw(p, P.key0, P.key1);
-    count_event(s_cnt, C_EL_STEPS);
-    hist_count(P, p.hist, 1);
-    const int m = __ldg(&P.mat[vox_of(P, p.ix, p.iy, p.iz)]);
-    int i;
-    float f;
-    grid_pos(T, p.E, i, f);
-    const int mi = m * T.n_e + i;
-    float4 a0 = S.el[mi], a1 = S.el[mi + 1];
-    // step limits as mass thickness in the start material: reach E_abs,
-    // hard-event candidate, or the multiple-scattering step
-    const float R0 = lerpf(a0.x, a1.x, f);
-    const float xms = lerpf(a0.y, a1.y, f);
-    const float xcut = R0 - T.r_eabs[m];
-    const float xhard = (T.flags & GDPM_FLAG_NO_HARD) ? kInf : -__logf(r.x) * T.inv_sigmax[m];
-    int ev;
-    float xs;
-    if (xcut <= xms && xcut <= xhard) { ev = 0; xs = xcut; }
-    else if (xhard <= xms) { ev = 1; xs = xhard; }
-    else { ev = 2; xs = xms; }
-    xs = fmaxf(xs, 0.f);
-    float Tend;
-    if (ev == 0) {
-        Tend = T.eabs_el;
-    } else {
-        const float rr = (R0 - xs - T.rinv_lo[m]) * T.rinv_idr[m];
-        const int j = min(max(int(floorf(rr)), 0), T.n_r - 2);
-        const float g = fminf(fmaxf(rr - float(j), 0.f), 1.f);
-        const float* ri = S.rinv + m * T.n_r;
-        Tend = fminf(lerpf(ri[j], ri[j + 1], g), p.E);
+}
+
+// ---------------------------------------------------------------- warp-uniform parts
+// Add this iteration's event counts of all 32 lanes (call with the whole warp).
+template <int PT>
+__device__ __forceinline__ void flush_events(uint32_t evb, uint32_t evn, uint32_t* s_cnt) {
+    const bool lead = lane_id() == 0;
+    const uint32_t n = __reduce_add_sync(kFull, evn);
+    if (lead && n) atomicAdd(&s_cnt[PT == 0 ? C_PH_FLIGHTS : C_CROSS], n);
+    if (!__any_sync(kFull, evb != 0u)) return;
+    const int slots[10] = {C_PH_REAL, C_COMPTON, C_PHOTO, C_PAIR,
+                           PT == 0 ? C_PH_TERMINATED : C_EL_TERMINATED, C_LOCAL_DEP,
+                           C_EL_STEPS, C_MOLLER, C_BREMS, C_ANNIHIL};
+#pragma unroll
+    for (int b = 0; b < 10; ++b) {
+        const uint32_t c = __popc(__ballot_sync(kFull, (evb >> b) & 1u));
+        if (lead && c) atomicAdd(&s_cnt[slots[b]], c);
     }
-    const float Tk = p.E;
-    const float dT = Tk - Tend;
-    if (P.hrec) hist_add(P, p.hist, 1, double(xs));
-    // multiple scattering at the mid-step energy
-    const float Tm = 0.5f * (Tk + Tend);
-    const float pbc = Tm * (Tm + 2.f * kMC2f) / (Tm + kMC2f);
-    const float q = kEs / pbc;
-    const float G1 = xs * q * q * 0.5f * T.inv_x0[m];
-    float mu;
-    if (G1 >= 1.f) {
-        mu = 2.f * r.z - 1.f;
-    } else {
-        const float Asc = screening_A(T, S.atab, G1);
-        mu = 1.f - 2.f * Asc * r.z / (1.f - r.z + Asc);
-    }
-    float cp, sp;
-    cossin_2pi(r.w, cp, sp);
-    const float dpm = xs > 0.f ? dT / xs : 0.f;
-    float dep = 0.f;
-    uint32_t crossings = 0;
-    // random hinge: zeta*xs straight, deflect, (1-zeta)*xs straight
-    const bool out1 = walk(P, p, r.y * xs, dpm, dep, false, crossings);
-    count_n(s_cnt, C_CROSS, crossings);
-    crossings = 0;
-    if (out1) {
-        electron_escape(P, p, Tk - dep, acc, s_cnt);
-        active = false;
-        return;
-    }
-    rotate(p.u, p.v, p.w, mu, cp, sp);
-    const bool out2 = walk(P, p, (1.f - r.y) * xs, dpm, dep, true, crossings);
-    count_n(s_cnt, C_CROSS, crossings);
-    if (out2) {
-        electron_escape(P, p, Tk - dep, acc, s_cnt);
-        active = false;
-        return;
-    }
-    tally(P, vox_of(P, p.ix, p.iy, p.iz), dT - dep);
-    p.E = Tend;
-    if (ev == 0) {
-        electron_absorb(P, A, p, acc, s_cnt);
-        active = false;
-        return;
-    }
-    if (ev != 1) return;
-    // hard-event candidate: accept with Sigma_h(T)/Sigma_max (start material)
-    const float4 v = draw(p, P.key0, P.key1);
-    const float Tn = p.E, wcc = T.eabs_el, wcb = T.eabs_ph;
-    float sm = 0.f, sb = 0.f;
-    if (Tn > wcb || Tn > 2.f * wcc) {
-        grid_pos(T, Tn, i, f);
-        const int mj = m * T.n_e + i;
-        a0 = S.el[mj];
-        a1 = S.el[mj + 1];
-        if (Tn > 2.f * wcc) sm = lerpf(a0.z, a1.z, f);
-        if (Tn > wcb) sb = lerpf(a0.w, a1.w, f);
-    }
-    const float sh = sm + sb;
-    if (!(v.x * T.sigmax[m] < sh)) return;
-    hist_count(P, p.hist, 2);
-    if (v.y * sh < sm) {
-        count_event(s_cnt, C_MOLLER);
-        float eps, rphi;
-        sample_moller(p, P, Tn, wcc, eps, rphi);
-        float c, s;
-        cossin_2pi(rphi, c, s);
-        const float W = eps * Tn, Tp = Tn - W;
-        const float cd = sqrtf(W * (Tn + 2.f * kMC2f) / (Tn * (W + 2.f * kMC2f)));
-        const float cpr = sqrtf(Tp * (Tn + 2.f * kMC2f) / (Tn * (Tp + 2.f * kMC2f)));
-        float du = p.u, dv = p.v, dw = p.w;
-        rotate(du, dv, dw, cd, c, s);
-        bank_from(P, A.out_el, A.out_el_count, p, false, false, W, du, dv, dw, s_cnt);
-        rotate(p.u, p.v, p.w, cpr, -c, -s);
-        p.E = Tp;
-    } else {
-        count_event(s_cnt, C_BREMS);
-        const float k = wcb * exp2f(v.z * __log2f(Tn / wcb));
-        bank_from(P, A.out_ph, A.out_ph_count, p, true, false, k, p.u, p.v, p.w, s_cnt);
-        p.E = Tn - k;
+}
+
+// Bank the secondaries the lanes' last steps created (call with the whole
+// warp): below-cutoff electrons and photons deposit on the spot, the rest
+// get queue slots (one atomic per warp and queue) and counter-derived ids.
+__device__ __forceinline__ void bank_pending(const SimParams& P, const PhaseArgs& A, Part& p,
+                                             const Sec& sec, uint32_t* s_cnt) {
+    const uint32_t lane = lane_id();
+    for (int k = 0; k < 2; ++k) {
+        const bool want = k < sec.n;
+        if (!__any_sync(kFull, want)) return;
+        const bool pos = k == 1 && sec.pos2;
+        const float E = k ? sec.E2 : sec.E1;
+        const float sg = (k == 1 && sec.photon) ? -1.f : 1.f;
+        const bool push = want && (pos || E >= (sec.photon ? P.T.eabs_ph : P.T.eabs_el));
+        if (want && !push) tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), E);
+        const uint32_t nloc = __popc(__ballot_sync(kFull, want && !push));
+        if (lane == 0 && nloc) atomicAdd(&s_cnt[C_LOCAL_DEP], nloc);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {           // q = 0 electron queue, 1 photon queue
+            const bool mine = push && (sec.photon == (q == 1));
+            const uint32_t m = __ballot_sync(kFull, mine);
+            if (!m) continue;
+            const int leader = __ffs(m) - 1;
+            uint32_t base = 0;
+            if (int(lane) == leader) base = atomicAdd(q ? A.out_ph_count : A.out_el_count, uint32_t(__popc(m)));
+            base = __shfl_sync(kFull, base, leader);
+            if (mine) {
+                Part c;
+                c.x = p.x; c.y = p.y; c.z = p.z;
+                c.u = sg * sec.dx; c.v = sg * sec.dy; c.w = sg * sec.dz;
+                c.E = E;
+                c.ix = p.ix; c.iy = p.iy; c.iz = p.iz;
+                c.hist = p.hist;
+                const uint64_t id = child_id(uint64_t(p.pidlo) | (uint64_t(p.pidhi) << 32), p.flags & 0xFFFFFFu);
+                c.pidlo = uint32_t(id);
+                c.pidhi = uint32_t(id >> 32);
+                c.ctr = 0;
+                c.flags = (p.flags & kBatchMask) | (pos ? kPositron : 0u);
+                ++p.flags;
+                const uint32_t slot = base + __popc(m & lanemask_lt());
+                const Queue& Q = q ? A.out_ph : A.out_el;
+                if (slot < Q.capacity) queue_store(Q, slot, c);
+                else atomicOr(P.status, ST_QUEUE_OVERFLOW);
+                hist_count(P, p.hist, 3);
+            }
+            if (lane == 0) {
+                atomicAdd(&s_cnt[q ? C_PUSH_PH : C_PUSH_EL], uint32_t(__popc(m)));
+                atomicAdd(&s_cnt[q ? C_PH_CREATED : C_EL_CREATED], uint32_t(__popc(m)));
+            }
+        }
     }
 }
 
@@ -659,44 +695,67 @@ __global__ void __launch_bounds__(256, GDPM_MIN_CTAS) k_phase(const SimParams P,
 
     Acc acc{0.0, 0.0, 0.0};
     Part p{};
+    Sec sec{};
     bool active = false, exhausted = false;
+    uint32_t evb = 0u, evn = 0u;
     const uint32_t lane = lane_id();
     for (uint32_t it = 0;; ++it) {
+        // ---- whole warp: account and bank the last step, then refill
+        flush_events<PT>(evb, evn, s_cnt);
+        evb = 0u;
+        evn = 0u;
+        bank_pending(P, A, p, sec, s_cnt);
+        sec.n = 0;
         const bool need = !active && !exhausted;
-        const uint32_t nm = __ballot_sync(0xffffffffu, need);
+        const uint32_t nm = __ballot_sync(kFull, need);
         if (nm) {
             const int leader = __ffs(nm) - 1;
             uint32_t base = 0;
             if (int(lane) == leader) base = atomicAdd(A.head, uint32_t(__popc(nm)));
-            base = __shfl_sync(0xffffffffu, base, leader);
+            base = __shfl_sync(kFull, base, leader);
+            bool from_src = false, from_queue = false, missed = false;
             if (need) {
                 const uint32_t idx = base + __popc(nm & lanemask_lt());
                 if (idx < A.n_src) {
-                    active = make_primary(P, A, idx, PT == 0, p, acc, s_cnt);
+                    from_src = true;
+                    active = make_primary(P, A, idx, p, acc);
+                    missed = !active;
                 } else if (idx < total) {
                     queue_load(A.in, idx - A.n_src, p);
-                    count_event(s_cnt, PT == 0 ? C_POP_PH : C_POP_EL);
+                    from_queue = true;
                     active = true;
                 } else {
                     exhausted = true;
                 }
             }
+            const uint32_t ns = __popc(__ballot_sync(kFull, from_src));
+            const uint32_t nq = __popc(__ballot_sync(kFull, from_queue));
+            const uint32_t nmiss = __popc(__ballot_sync(kFull, missed));
+            if (lane == 0) {
+                if (ns) {
+                    atomicAdd(&s_cnt[C_PRIMARY], ns);
+                    atomicAdd(&s_cnt[PT == 0 ? C_PH_CREATED : C_EL_CREATED], ns);
+                }
+                if (nq) atomicAdd(&s_cnt[PT == 0 ? C_POP_PH : C_POP_EL], nq);
+                if (nmiss) atomicAdd(&s_cnt[PT == 0 ? C_PH_TERMINATED : C_EL_TERMINATED], nmiss);
+            }
         }
-        if (__all_sync(0xffffffffu, exhausted)) break;
+        if (__all_sync(kFull, exhausted)) break;
         if (it >= P.max_iters) {
             if (lane == 0) atomicOr(P.status, ST_ITER_CAP);
             break;
         }
+        // ---- each lane on its own: one step
         if (active) {
-            if (PT == 0) photon_step(P, A, ps, p, active, acc, s_cnt);
-            else electron_step(P, A, es, p, active, acc, s_cnt);
+            if (PT == 0) photon_step(P, ps, p, active, acc, evb, evn, sec);
+            else electron_step(P, es, p, active, acc, evb, evn, sec);
         }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        acc.src += __shfl_down_sync(0xffffffffu, acc.src, o);
-        acc.esc += __shfl_down_sync(0xffffffffu, acc.esc, o);
-        acc.disc += __shfl_down_sync(0xffffffffu, acc.disc, o);
+        acc.src += __shfl_down_sync(kFull, acc.src, o);
+        acc.esc += __shfl_down_sync(kFull, acc.esc, o);
+        acc.disc += __shfl_down_sync(kFull, acc.disc, o);
     }
     if (lane == 0) {
         if (acc.src != 0.0) atomicAdd(&P.ledger[L_SOURCE], acc.src);
@@ -757,14 +816,11 @@ __global__ void k_debug_sample(int kind, float a, float b, uint64_t n, uint32_t 
 }
 
 __global__ void k_debug_sources(const SimParams P, const PhaseArgs A, uint64_t n, double* out) {
-    __shared__ uint32_t s_cnt[C_NCOUNT];
-    for (int k = threadIdx.x; k < C_NCOUNT; k += blockDim.x) s_cnt[k] = 0;
-    __syncthreads();
     for (uint64_t s = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; s < n;
          s += uint64_t(gridDim.x) * blockDim.x) {
         Part p{};
         Acc acc{0, 0, 0};
-        const bool in = make_primary(P, A, uint32_t(s), P.S.particle == GDPM_PHOTON, p, acc, s_cnt);
+        const bool in = make_primary(P, A, uint32_t(s), p, acc);
         double* o = out + 8 * s;
         o[0] = p.x; o[1] = p.y; o[2] = p.z; o[3] = p.u; o[4] = p.v; o[5] = p.w; o[6] = p.E;
         o[7] = in ? 1.0 : 0.0;
@@ -784,8 +840,11 @@ static size_t smem_of(const DevTables& T, int particle) {
 int transport_smem(const gdpm_tables* t, int particle) { return int(smem_of(t->dev, particle)); }
 
 // Persistent grid: SM count x resident CTAs per SM for this shared-memory size.
-int launch_phase(gdpm_ctx* ctx, int particle, const SimParams& P, const PhaseArgs& A,
-                 uint32_t n_items_hint) {
+// share = 4 gives the grid three quarters of the GPU: a large request that
+// runs while small ones are active leaves SMs free for them, since
+// persistent CTAs do not yield until their phase's input is drained.
+int launch_phase(gdpm_ctx* ctx, cudaStream_t st, int particle, const SimParams& P,
+                 const PhaseArgs& A, uint32_t n_items_hint, uint32_t share) {
     const size_t smem = smem_of(P.T, particle);
     const void* fn = particle == GDPM_PHOTON ? (const void*)k_phase<0> : (const void*)k_phase<1>;
     GDPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -795,15 +854,16 @@ int launch_phase(gdpm_ctx* ctx, int particle, const SimParams& P, const PhaseArg
         if (bps < 1) return GDPM_E_ARG;
     }
     uint32_t grid = uint32_t(ctx->sm_count) * uint32_t(bps);
+    if (share == 4) grid = std::max<uint32_t>(uint32_t(ctx->sm_count), grid * 3 / 4);
     if (n_items_hint > 0) {
         const uint32_t need = (n_items_hint + ctx->block_threads - 1) / ctx->block_threads;
         grid = need < grid ? need : grid;
     }
     if (grid == 0) grid = 1;
     if (particle == GDPM_PHOTON)
-        k_phase<0><<<grid, ctx->block_threads, smem, ctx->stream>>>(P, A);
+        k_phase<0><<<grid, ctx->block_threads, smem, st>>>(P, A);
     else
-        k_phase<1><<<grid, ctx->block_threads, smem, ctx->stream>>>(P, A);
+        k_phase<1><<<grid, ctx->block_threads, smem, st>>>(P, A);
     GDPM_CUDA_TRY(cudaGetLastError());
     return GDPM_OK;
 }

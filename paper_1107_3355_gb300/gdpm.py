@@ -23,10 +23,22 @@ GDPM_E_CUDA, GDPM_E_STATE, GDPM_E_BUSY = -5, -6, -7
 GDPM_PHOTON, GDPM_ELECTRON = 0, 1
 GDPM_GEO_PENCIL, GDPM_GEO_POINT_FIELD, GDPM_GEO_BEAMLETS = 0, 1, 2
 GDPM_FLAG_COMPTON_ONLY, GDPM_FLAG_NO_HARD = 2, 4
-(GDPM_PARAM_QUEUE_CAPACITY, GDPM_PARAM_BLOCK_THREADS, GDPM_PARAM_BLOCKS_PER_SM,
- GDPM_PARAM_TALLY_MODE, GDPM_PARAM_SOURCE_CHUNK, GDPM_PARAM_MAX_PHASES, GDPM_PARAM_REQUEST_ID,
- GDPM_PARAM_SPECULATIVE, GDPM_PARAM_WARP_AGGREGATE, GDPM_PARAM_PROFILE,
- GDPM_PARAM_OVERLAP_FOLD) = range(1, 12)
+GDPM_PARAM_QUEUE_CAPACITY = 1
+GDPM_PARAM_BLOCK_THREADS = 2
+GDPM_PARAM_BLOCKS_PER_SM = 3
+GDPM_PARAM_TALLY_MODE = 4
+GDPM_PARAM_SOURCE_CHUNK = 5
+GDPM_PARAM_MAX_PHASES = 6
+GDPM_PARAM_REQUEST_ID = 7
+GDPM_PARAM_SPECULATIVE = 8
+GDPM_PARAM_PROFILE = 10
+GDPM_PARAM_OVERLAP_FOLD = 11
+GDPM_PARAM_SERVE_SLOTS = 12
+GDPM_PARAM_SERVE_RESERVE_MB = 13
+GDPM_PARAM_METRIC_MIN_DENSITY = 14
+GDPM_PARAM_BATCH_MODE = 15
+GDPM_PARAM_CONCURRENT_MAX_HIST = 16
+GDPM_PARAM_CONCURRENT_MAX_MB = 17
 MAX_EL, MAX_MAT, MAX_BINS = 16, 8, 256
 
 EXPORTED = ["gdpm_context_create", "gdpm_context_destroy", "gdpm_set_param",
@@ -76,7 +88,7 @@ class gdpm_stats(C.Structure):
 
 class gdpm_request_desc(C.Structure):
     _fields_ = [("phantom", C.c_void_p), ("tables", C.c_void_p), ("source", gdpm_source_desc),
-                ("n_histories", C.c_uint64), ("n_batches", C.c_int)]
+                ("n_histories", C.c_uint64), ("n_batches", C.c_int), ("stream_id", C.c_uint32)]
 
 
 _lib = None
@@ -252,7 +264,8 @@ def gdpm_set_history_records(ctx, rec, recd, n):
            "gdpm_set_history_records")
 
 
-def gdpm_request_submit(ctx, phantom, tables, src: "W.Source", n_histories, n_batches):
+def gdpm_request_submit(ctx, phantom, tables, src: "W.Source", n_histories, n_batches,
+                        stream_id=0):
     keep = _SourceKeep(src)
     r = gdpm_request_desc()
     r.phantom = phantom.value if hasattr(phantom, "value") else phantom
@@ -260,6 +273,7 @@ def gdpm_request_submit(ctx, phantom, tables, src: "W.Source", n_histories, n_ba
     r.source = keep.desc
     r.n_histories = n_histories
     r.n_batches = n_batches
+    r.stream_id = stream_id
     rid = C.c_uint64()
     _check(lib().gdpm_request_submit(ctx, C.byref(r), C.byref(rid)), "gdpm_request_submit")
     return rid.value

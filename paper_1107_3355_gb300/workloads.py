@@ -265,6 +265,112 @@ def field_source(phantom: Phantom, spectrum: Spectrum, particle=PHOTON, ssd=100.
 
 
 # ---------------------------------------------------------------------------
+# Beam geometry: gantry frames, fluence-map beamlets, MLC apertures
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass(frozen=True)
+class BeamFrame:
+    """A beam at gantry angle ``gantry_deg`` rotating about the z axis through
+    the isocentre: point source at distance ``sad`` from the isocentre, beam
+    axis through the isocentre, iso-plane axes ``axis_u`` (in the rotation
+    plane) and ``axis_v`` (= z).  At 0 degrees the source sits on the -y side."""
+    source: Tuple[float, float, float]
+    iso: Tuple[float, float, float]
+    axis_u: Tuple[float, float, float]
+    axis_v: Tuple[float, float, float]
+
+
+def beam_frame(gantry_deg: float, iso, sad: float = 100.0) -> BeamFrame:
+    t = math.radians(gantry_deg)
+    src = (iso[0] + sad * math.sin(t), iso[1] - sad * math.cos(t), iso[2])
+    return BeamFrame(src, tuple(iso), (math.cos(t), math.sin(t), 0.0), (0.0, 0.0, 1.0))
+
+
+def beamlet_row(fr: BeamFrame, u0, u1, v0, v1, weight) -> List[float]:
+    """One beamlet: rectangle [u0,u1] x [v0,v1] (cm) on the iso plane."""
+    return [*fr.source, *fr.iso, *fr.axis_u, *fr.axis_v, u0, u1, v0, v1, weight]
+
+
+def fluence_map_rows(fr: BeamFrame, intensity: np.ndarray, size: float = 1.0) -> List[List[float]]:
+    """Beamlets of a fluence map (rows = v, cols = u) centred on the isocentre;
+    the weight f_I of a beamlet is its intensity times its area (Sec. 2.3.1);
+    beamlets with zero intensity are left out."""
+    nv, nu = intensity.shape
+    rows = []
+    for j in range(nv):
+        for i in range(nu):
+            f = float(intensity[j, i])
+            if f > 0:
+                u0 = (i - nu / 2) * size
+                v0 = (j - nv / 2) * size
+                rows.append(beamlet_row(fr, u0, u0 + size, v0, v0 + size, f * size * size))
+    return rows
+
+
+def aperture_rows(fr: BeamFrame, leaves: np.ndarray, leaf_width: float, v_start: float,
+                  weight: float = 1.0) -> List[List[float]]:
+    """An MLC aperture: leaf pair k spans v in [v_start + k w, v_start + (k+1) w]
+    and is open between leaves[k] = (u_left, u_right); uniform fluence."""
+    rows = []
+    for k, (a, b) in enumerate(leaves):
+        if b > a:
+            v0 = v_start + k * leaf_width
+            rows.append(beamlet_row(fr, float(a), float(b), v0, v0 + leaf_width,
+                                    weight * (b - a) * leaf_width))
+    return rows
+
+
+def beamlet_source(rows, spectrum: "Spectrum", particle=PHOTON) -> "Source":
+    return Source(particle, spectrum, "beamlets", beamlets=np.asarray(rows, np.float64))
+
+
+def imrt_plan(phantom: "Phantom", n_beams: int = 7, map_size: int = 20, beamlet: float = 1.0,
+              seed: int = 11, sad: float = 100.0) -> "Source":
+    """Coplanar IMRT plan: n_beams equally spaced gantry angles, each a
+    map_size^2 fluence map of beamlet-cm beamlets with intensities U[0,1]."""
+    rng = np.random.default_rng(seed)
+    iso = tuple(e / 2 for e in phantom.extent)
+    rows = []
+    for b in range(n_beams):
+        fr = beam_frame(360.0 * b / n_beams, iso, sad)
+        rows += fluence_map_rows(fr, rng.uniform(0, 1, (map_size, map_size)), beamlet)
+    return beamlet_source(rows, kramers_spectrum())
+
+
+def vmat_arc(phantom: "Phantom", n_points: int = 180, step_deg: float = 2.0, field: float = 10.0,
+             leaf_width: float = 0.5, seed: int = 3, sad: float = 100.0) -> "Source":
+    """VMAT arc: n_points control points step_deg apart; at each, the MLC
+    leaf pairs that cover the field are open between seeded leaf positions
+    inside the field."""
+    rng = np.random.default_rng(seed)
+    iso = tuple(e / 2 for e in phantom.extent)
+    n_pairs = int(round(field / leaf_width))
+    rows = []
+    for c in range(n_points):
+        fr = beam_frame(c * step_deg, iso, sad)
+        left = rng.uniform(-field / 2, 0.0, n_pairs)
+        right = rng.uniform(0.0, field / 2, n_pairs)
+        rows += aperture_rows(fr, np.stack([left, right], 1), leaf_width, -field / 2)
+    return beamlet_source(rows, kramers_spectrum())
+
+
+def single_beamlet(phantom: "Phantom", gantry_deg: float, u: float, v: float, size: float,
+                   sad: float = 100.0) -> "Source":
+    iso = tuple(e / 2 for e in phantom.extent)
+    fr = beam_frame(gantry_deg, iso, sad)
+    return beamlet_source([beamlet_row(fr, u, u + size, v, v + size, 1.0)], kramers_spectrum())
+
+
+def ct_imrt_problem(n_histories=250_000_000, n_batches=100, shape=(256, 256, 128),
+                    voxel=(0.25, 0.25, 0.25), seed=12345) -> "Problem":
+    """Patient-like ellipsoid phantom with a 7-beam 20x20 fluence-map IMRT
+    plan, 6 MV-like spectrum (stands in for the paper's DICOM IMRT/VMAT plans)."""
+    ph = ct_phantom(shape, voxel)
+    return Problem(ph, imrt_plan(ph), n_histories, n_batches, eabs_photon=0.05,
+                   eabs_electron=0.2, e_min=0.005, e_max=6.5, seed=seed)
+
+
+# ---------------------------------------------------------------------------
 # Problem = everything one dose calculation needs
 # ---------------------------------------------------------------------------
 

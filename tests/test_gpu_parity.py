@@ -248,11 +248,20 @@ def test_tally_modes_agree():
     assert st32["compton"] == st64["compton"]
 
 
-def test_warp_aggregated_tally_agrees():
-    prob = W.tiny_problem(n_histories=50_000)
-    d0, _, _ = run_gpu(prob)
-    d1, _, _ = run_gpu(prob, params={G.GDPM_PARAM_WARP_AGGREGATE: 1})
-    np.testing.assert_allclose(d1, d0, rtol=1e-9, atol=1e-12 * d0.max())
+@pytest.mark.parametrize("tally", [0, 1])
+def test_batch_modes_agree(tally):
+    """All batches side by side (one grid each) and batches one after another
+    transport the same histories: equal dose, sigma and counts."""
+    prob = W.slab_photon_problem(n_histories=60_000, n_batches=12, shape=(32, 32, 128))
+    d_seq, s_seq, st_seq = run_gpu(prob, params={G.GDPM_PARAM_BATCH_MODE: 1,
+                                                 G.GDPM_PARAM_TALLY_MODE: tally})
+    d_con, s_con, st_con = run_gpu(prob, params={G.GDPM_PARAM_BATCH_MODE: 2,
+                                                 G.GDPM_PARAM_TALLY_MODE: tally})
+    np.testing.assert_allclose(d_con, d_seq, rtol=1e-9, atol=1e-12 * d_seq.max())
+    np.testing.assert_allclose(s_con, s_seq, rtol=1e-6, atol=1e-9 * s_seq.max())
+    for k in ("compton", "el_steps", "moller", "brems", "pushes", "pops"):
+        assert st_con[k] == st_seq[k], k
+    assert st_con["phases"] < st_seq["phases"]
 
 
 def test_host_outputs_equal_device_outputs():
@@ -343,3 +352,22 @@ def test_full_size_slab_sampled_histories():
     r = t_test(g.ravel(), gs.ravel(), np.swapaxes(g, 1, 2).ravel(), np.swapaxes(gs, 1, 2).ravel(),
                high_frac=0.1)
     assert r["P_high"] > 0.9
+
+
+def test_ct_imrt_beamlets_same_seed():
+    """Patient-like ellipsoid phantom (air, water, lung, bone, per-region
+    densities) at 1 cm voxels with the 7-beam fluence-map IMRT plan: the
+    cumulative-fluence beamlet sampling and gantry frames agree with the
+    oracle history by history."""
+    ph = W.ct_phantom(shape=(64, 64, 32), voxel=(1.0, 1.0, 1.0))
+    prob = W.Problem(ph, W.imrt_plan(ph), 20_000, 10, eabs_photon=0.05, eabs_electron=0.2,
+                     e_min=0.005, e_max=6.5)
+    d_o, s_o, led_o, rec_o, _ = O.run(prob, per_history=True)
+    d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
+    check_ledger(st, prob.n_histories, 1e-5)
+    same = np.all(rec_o == rec_g, axis=1)
+    print("ct imrt identical records: %.5f" % same.mean())
+    assert same.mean() > 0.97
+    r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
+    print("ct imrt t-test", r)
+    assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97

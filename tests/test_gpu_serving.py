@@ -1,0 +1,81 @@
+"""Serving (gdpm_request_submit / gdpm_request_poll): requests run side by
+side with continuous admission; a request's result does not depend on what
+else runs (its Philox stream is its own), and equals gdpm_simulate's."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1107_3355_gb300 import gdpm as G
+from paper_1107_3355_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def wait(ctx, rid, V, timeout=120.0):
+    d = torch.empty(V, dtype=torch.float64, device="cuda")
+    s = torch.empty(V, dtype=torch.float64, device="cuda")
+    t0 = time.time()
+    while True:
+        done, st = G.gdpm_request_poll(ctx, rid, d, s)
+        if done:
+            return d.cpu().numpy(), s.cpu().numpy(), st
+        assert time.time() - t0 < timeout
+        time.sleep(0.001)
+
+
+def test_request_alone_equals_in_mix_and_simulate():
+    prob = W.slab_photon_problem(n_histories=200_000, n_batches=10, shape=(64, 64, 128))
+    eng = G.Engine(prob)
+    V = prob.phantom.n_voxels
+    try:
+        # the same calculation through gdpm_simulate with the same stream id
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_REQUEST_ID, 77)
+        d_sim, s_sim, st_sim = eng.run()
+        d_sim = d_sim.cpu().numpy()
+        # alone
+        rid = G.gdpm_request_submit(eng.ctx, eng.phantom, eng.tables, prob.source, 200_000, 10,
+                                    stream_id=77)
+        d_alone, s_alone, st_alone = wait(eng.ctx, rid, V)
+        # in a mix with other requests submitted around it
+        others = []
+        ph = prob.phantom
+        for k in range(6):
+            src = W.single_beamlet(ph, 45.0 * k, -1.0, -1.0, 2.0) if k % 2 else prob.source
+            others.append(G.gdpm_request_submit(eng.ctx, eng.phantom, eng.tables, src,
+                                                100_000 * (k + 1), 10))
+        rid2 = G.gdpm_request_submit(eng.ctx, eng.phantom, eng.tables, prob.source, 200_000, 10,
+                                     stream_id=77)
+        others.append(G.gdpm_request_submit(eng.ctx, eng.phantom, eng.tables, prob.source,
+                                            300_000, 10))
+        d_mix, s_mix, st_mix = wait(eng.ctx, rid2, V)
+        for r in others:
+            wait(eng.ctx, r, V)
+    finally:
+        eng.close()
+    tol = dict(rtol=1e-9, atol=1e-12 * d_sim.max())
+    np.testing.assert_allclose(d_alone, d_sim, **tol)
+    np.testing.assert_allclose(d_mix, d_alone, **tol)
+    np.testing.assert_allclose(s_mix, s_alone, rtol=1e-6, atol=1e-9 * s_alone.max())
+    for k in ("compton", "el_steps", "moller", "brems", "n_primary"):
+        assert st_mix[k] == st_alone[k] == st_sim[k], k
+
+
+def test_many_requests_complete_with_few_slots():
+    prob = W.tiny_problem(n_histories=20_000, n_batches=4)
+    eng = G.Engine(prob)
+    try:
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_SERVE_SLOTS, 2)
+        ids = [G.gdpm_request_submit(eng.ctx, eng.phantom, eng.tables, prob.source, 5_000 + 1000 * k, 4)
+               for k in range(12)]
+        V = prob.phantom.n_voxels
+        for k, rid in enumerate(ids):
+            d, s, st = wait(eng.ctx, rid, V)
+            assert st["n_primary"] == 5_000 + 1000 * k
+            bal = st["deposited"] + st["escaped"] + st["discarded"]
+            assert abs(bal - st["source_energy"]) <= 1e-5 * st["source_energy"]
+        with pytest.raises(G.GdpmError):
+            G.gdpm_request_poll(eng.ctx, ids[0])          # already released
+    finally:
+        eng.close()
