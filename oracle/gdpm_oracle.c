@@ -16,7 +16,9 @@
  *   - Sec. 2.2.1: N_b equal batches; per-voxel mean dose and uncertainty
  *     from the batch spread.
  *   - Sec. 2.2.2: cross sections read from tables by linear interpolation.
- *   - Sec. 2.3.1: beamlet sampling from the cumulative fluence P(I).
+ *   - Sec. 2.3.1: beamlet sampling from the cumulative fluence P(I), and
+ *     the Metropolis chain of Algorithm A1; Walker's alias method is a
+ *     third sampler of the same distribution f_I.
  *   - Sec. 2.3.2: the spectrum split into equal energy intervals, histories
  *     of a batch allotted to intervals by spectrum weight, energy uniform
  *     inside an interval.
@@ -51,6 +53,8 @@
 #define ORC_MAX_MAT 8
 #define ORC_MAX_EL 16
 #define ORC_MAX_BINS 256
+
+enum { ORC_SAMPLE_CDF = 0, ORC_SAMPLE_ALIAS = 1, ORC_SAMPLE_METROPOLIS = 2 };
 
 #define ORC_NO_ANNIHILATION 1
 #define ORC_COMPTON_ONLY 2
@@ -91,6 +95,8 @@ typedef struct {
     unsigned long long seed;
     unsigned int request_id;
     int flags;
+    int beamlet_sampler;           /* ORC_SAMPLE_* */
+    int metro_chains;              /* Metropolis chains C (Algorithm A1) */
 } orc_problem;
 
 typedef struct {
@@ -178,6 +184,13 @@ typedef struct {
     uint64_t hrec_base;            /* history id of record row 0 */
     orc_particle *stack; size_t sp, scap;
     int flags;
+    /* beamlet sampling (Sec. 2.3.1) over the nf beamlets of positive weight */
+    int nf;
+    int *bl_index;                 /* [nf] row of the k-th positive-weight beamlet */
+    double *bl_f;                  /* [nf] its weight f */
+    double *al_prob; int *al_alias;/* [nf] Walker alias table */
+    int *ch_state;                 /* [C] current beamlet of each Metropolis chain */
+    uint64_t *ch_next;             /* [C] next step index of each chain */
 } orc_sim;
 
 /* per-unit-mass number densities */
@@ -886,6 +899,145 @@ static void allot(const orc_problem *P, uint64_t nb, uint64_t *cnt)
     }
 }
 
+/* ------------------------------------------------------- beamlet samplers
+ * Sec. 2.3.1: the beamlet I of a particle is drawn with probability
+ * f_I / sum f, over the beamlets of positive fluence only (the paper drops
+ * zero-fluence beamlets first).  Three samplers of that distribution:
+ *  - cumulative: the I with P(I) <= r < P(I+1), r the history's uniform;
+ *  - Walker alias: a uniform index J and a uniform u; I = J when u is below
+ *    J's cut-off, else J's alias.  Table built by Vose's procedure;
+ *  - Metropolis (Algorithm A1): a chain of beamlet indices; each particle
+ *    proposes a uniform J and moves the chain there with probability
+ *    min(1, f_J / f_Iprev), else repeats Iprev.
+ * READING (chains that do not depend on scheduling): C chains in place of
+ * one per GPU thread.  History h is step floor(h / C) of chain h mod C, so
+ * the seed alone fixes every history's beamlet.  Chain c starts at a
+ * uniform index from the Philox block at counter (c, 0, 1, 0); the step of
+ * history h uses the block at counter (h, 0, 0, 0).  (Particle ids 0 and
+ * 2^32 are never given to a particle.)  Alias and Metropolis read two words
+ * x0, x1 of the block: J = floor(x0 nf / 2^32), u = (x1 + 1/2) / 2^32.
+ * The acceptance u < f_J / f_I is evaluated as u f_I < f_J in FP64. */
+static void source_block(const orc_sim *S, uint32_t c0, uint32_t c2, uint32_t out[4])
+{
+    uint32_t c[4] = {c0, 0u, c2, 0u};
+    philox4x32_10(c, S->key, out);
+}
+
+static int uniform_index(uint32_t x, int n)
+{
+    return (int)(((uint64_t)x * (uint64_t)n) >> 32);
+}
+
+static double word_uniform(uint32_t x)
+{
+    return ((double)x + 0.5) * (1.0 / 4294967296.0);
+}
+
+static void chain_start(orc_sim *S, int c)
+{
+    uint32_t w[4];
+    source_block(S, (uint32_t)c, 1u, w);
+    S->ch_state[c] = uniform_index(w[0], S->nf);
+    S->ch_next[c] = 0;
+}
+
+static void samplers_init(orc_sim *S)
+{
+    const orc_problem *P = S->P;
+    if (P->geometry != GEO_BEAMLETS || P->n_beamlets < 1) return;
+    int n = 0;
+    for (int b = 0; b < P->n_beamlets; b++)
+        if (P->beamlets[b * 17 + 16] > 0) n++;
+    S->nf = n;
+    S->bl_index = malloc(sizeof(int) * n);
+    S->bl_f = malloc(sizeof(double) * n);
+    S->al_prob = malloc(sizeof(double) * n);
+    S->al_alias = malloc(sizeof(int) * n);
+    n = 0;
+    for (int b = 0; b < P->n_beamlets; b++)
+        if (P->beamlets[b * 17 + 16] > 0) {
+            S->bl_index[n] = b;
+            S->bl_f[n] = P->beamlets[b * 17 + 16];
+            n++;
+        }
+    /* Vose: scaled weights q_k = f_k nf / sum f; repeatedly pair the last
+     * "small" (q < 1) with the last "large" entry, which gives the small one
+     * its cut-off and donates 1 - q_small of its own mass. */
+    double sum = 0;
+    for (int k = 0; k < n; k++) sum += S->bl_f[k];
+    double scale = (double)n / sum;
+    double *q = malloc(sizeof(double) * n);
+    int *small = malloc(sizeof(int) * n), *large = malloc(sizeof(int) * n);
+    int ns = 0, nl = 0;
+    for (int k = 0; k < n; k++) {
+        q[k] = S->bl_f[k] * scale;
+        if (q[k] < 1.0) small[ns++] = k; else large[nl++] = k;
+    }
+    while (ns > 0 && nl > 0) {
+        int l = small[--ns], g = large[--nl];
+        S->al_prob[l] = q[l];
+        S->al_alias[l] = g;
+        q[g] = (q[g] + q[l]) - 1.0;
+        if (q[g] < 1.0) small[ns++] = g; else large[nl++] = g;
+    }
+    while (nl > 0) { int g = large[--nl]; S->al_prob[g] = 1.0; S->al_alias[g] = g; }
+    while (ns > 0) { int l = small[--ns]; S->al_prob[l] = 1.0; S->al_alias[l] = l; }
+    free(q); free(small); free(large);
+    if (P->beamlet_sampler == ORC_SAMPLE_METROPOLIS) {
+        int C = P->metro_chains;
+        S->ch_state = malloc(sizeof(int) * C);
+        S->ch_next = malloc(sizeof(uint64_t) * C);
+        for (int c = 0; c < C; c++) chain_start(S, c);
+    }
+}
+
+static void samplers_free(orc_sim *S)
+{
+    free(S->bl_index); free(S->bl_f); free(S->al_prob); free(S->al_alias);
+    free(S->ch_state); free(S->ch_next);
+    S->bl_index = S->al_alias = S->ch_state = NULL;
+    S->bl_f = S->al_prob = NULL;
+    S->ch_next = NULL;
+}
+
+/* Beamlet (position k in the positive-weight list) of history h; r is the
+ * history's own uniform, used by the cumulative sampler. */
+static int pick_beamlet(orc_sim *S, uint32_t h, double r)
+{
+    const orc_problem *P = S->P;
+    int nf = S->nf;
+    uint32_t w[4];
+    if (P->beamlet_sampler == ORC_SAMPLE_ALIAS) {
+        source_block(S, h, 0u, w);
+        int J = uniform_index(w[0], nf);
+        return word_uniform(w[1]) < S->al_prob[J] ? J : S->al_alias[J];
+    }
+    if (P->beamlet_sampler == ORC_SAMPLE_METROPOLIS) {
+        uint64_t C = (uint64_t)P->metro_chains;
+        int c = (int)(h % C);
+        uint64_t step = h / C;
+        if (S->ch_next[c] > step) chain_start(S, c);
+        while (S->ch_next[c] <= step) {
+            uint32_t hs = (uint32_t)((uint64_t)c + S->ch_next[c] * C);
+            source_block(S, hs, 0u, w);
+            int J = uniform_index(w[0], nf);
+            int I = S->ch_state[c];
+            if (word_uniform(w[1]) * S->bl_f[I] < S->bl_f[J]) S->ch_state[c] = J;
+            S->ch_next[c]++;
+        }
+        return S->ch_state[c];
+    }
+    /* cumulative P(I), summed over all beamlets as given */
+    double tot = 0;
+    for (int b = 0; b < P->n_beamlets; b++) tot += P->beamlets[b * 17 + 16];
+    double x = r * tot, acc = 0;
+    for (int k = 0; k < nf; k++) {
+        acc += S->bl_f[k];
+        if (x < acc) return k;
+    }
+    return nf - 1;
+}
+
 static void make_primary(orc_sim *S, uint32_t h, double elo, double ehi, orc_particle *p)
 {
     const orc_problem *P = S->P;
@@ -906,15 +1058,7 @@ static void make_primary(orc_sim *S, uint32_t h, double elo, double ehi, orc_par
             src = P->origin; cen = P->center; au = P->axis_u; av = P->axis_v;
             a0 = -P->half_u; a1 = P->half_u; b0 = -P->half_v; b1 = P->half_v;
         } else {
-            /* beamlet index from the cumulative fluence P(I) (Sec. 2.3.1) */
-            double tot = 0;
-            for (int b = 0; b < P->n_beamlets; b++) tot += P->beamlets[b * 17 + 16];
-            double r = u[3] * tot, acc = 0;
-            int I = P->n_beamlets - 1;
-            for (int b = 0; b < P->n_beamlets; b++) {
-                acc += P->beamlets[b * 17 + 16];
-                if (r < acc) { I = b; break; }
-            }
+            int I = S->bl_index[pick_beamlet(S, h, u[3])];
             const double *row = P->beamlets + (size_t)I * 17;
             src = row; cen = row + 3; au = row + 6; av = row + 9;
             a0 = row[12]; a1 = row[13]; b0 = row[14]; b1 = row[15];
@@ -971,6 +1115,7 @@ static int sim_init(orc_sim *S, const orc_problem *P, orc_result *res)
         S->T.r_eabs[m] = tab_at(&S->T, S->T.range, m, P->eabs_el);
     S->key[0] = (uint32_t)P->seed;
     S->key[1] = (uint32_t)(P->seed >> 32) ^ P->request_id;
+    samplers_init(S);
     return 0;
 }
 
@@ -981,6 +1126,9 @@ int orc_run(const orc_problem *P, double *dose, double *sigma, orc_result *res,
 {
     if (P->n_batches < 2 || P->n_hist < (unsigned long long)P->n_batches || P->n_mat < 1 ||
         P->n_mat > ORC_MAX_MAT || P->n_bins < 1 || P->n_bins > ORC_MAX_BINS)
+        return -1;
+    if (P->beamlet_sampler < ORC_SAMPLE_CDF || P->beamlet_sampler > ORC_SAMPLE_METROPOLIS ||
+        (P->beamlet_sampler == ORC_SAMPLE_METROPOLIS && P->metro_chains < 1))
         return -1;
     orc_sim S;
     sim_init(&S, P, res);
@@ -1034,6 +1182,7 @@ int orc_run(const orc_problem *P, double *dose, double *sigma, orc_result *res,
     res->sigma_over_dmax = (na > 0 && dmax > 0) ? acc / na / dmax : 0.0;
     free(s1); free(s2); free(S.edep); free(S.stack);
     tables_free(&S.T);
+    samplers_free(&S);
     return 0;
 }
 
@@ -1224,6 +1373,7 @@ int orc_first_interaction(const orc_problem *P, long long n, double *out_z, int 
         }
     }
     tables_free(&S.T);
+    samplers_free(&S);
     return 0;
 }
 
@@ -1266,6 +1416,47 @@ int orc_sources(const orc_problem *P, unsigned long long first, unsigned long lo
         o[6] = p.E; o[7] = in ? 1.0 : 0.0;
     }
     tables_free(&S.T);
+    samplers_free(&S);
+    return 0;
+}
+
+/* The positive-weight beamlet list and its Walker alias table: index[k]
+ * is the beamlet row of list entry k; returns nf. */
+int orc_beamlet_tables(const orc_problem *P, int *index, double *prob, int *alias)
+{
+    orc_sim S;
+    orc_result res;
+    sim_init(&S, P, &res);
+    int nf = S.nf;
+    for (int k = 0; k < nf; k++) {
+        index[k] = S.bl_index[k];
+        prob[k] = S.al_prob[k];
+        alias[k] = S.al_alias[k];
+    }
+    tables_free(&S.T);
+    samplers_free(&S);
+    return nf;
+}
+
+/* Beamlet rows picked for histories [first, first+n) by the problem's
+ * sampler, histories taken in increasing order as the transport does. */
+int orc_beamlet_picks(const orc_problem *P, unsigned long long first, unsigned long long n,
+                      int *out)
+{
+    orc_sim S;
+    orc_result res;
+    sim_init(&S, P, &res);
+    for (uint64_t s = 0; s < n; s++) {
+        uint32_t h = (uint32_t)(first + s);
+        orc_particle p;
+        memset(&p, 0, sizeof p);
+        p.hist = h; p.pid = 1; p.ctr = 0;
+        double u[4];
+        draw4(&S, &p, u);
+        out[s] = S.bl_index[pick_beamlet(&S, h, u[3])];
+    }
+    tables_free(&S.T);
+    samplers_free(&S);
     return 0;
 }
 
@@ -1308,5 +1499,6 @@ int orc_history_records(const orc_problem *P, unsigned long long first, unsigned
     }
     free(S.edep); free(S.stack);
     tables_free(&S.T);
+    samplers_free(&S);
     return 0;
 }

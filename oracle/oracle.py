@@ -53,7 +53,10 @@ class OrcProblem(C.Structure):
                 ("weights", C.c_double * MAX_BINS),
                 ("n_beamlets", C.c_int), ("beamlets", C.POINTER(C.c_double)),
                 ("n_hist", C.c_ulonglong), ("n_batches", C.c_int), ("seed", C.c_ulonglong),
-                ("request_id", C.c_uint), ("flags", C.c_int)]
+                ("request_id", C.c_uint), ("flags", C.c_int),
+                ("beamlet_sampler", C.c_int), ("metro_chains", C.c_int)]
+
+SAMPLERS = {"cdf": 0, "alias": 1, "metropolis": 2}
 
 
 _RESULT_FIELDS = ["source_energy", "deposited", "escaped", "discarded", "n_primary",
@@ -106,6 +109,11 @@ def lib():
         L.orc_allot.argtypes = [C.POINTER(OrcProblem), C.c_ulonglong, C.c_void_p]
         L.orc_rotate.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p]
         L.orc_sources.argtypes = [C.POINTER(OrcProblem), C.c_ulonglong, C.c_ulonglong, C.c_void_p]
+        L.orc_beamlet_tables.argtypes = [C.POINTER(OrcProblem), C.c_void_p, C.c_void_p,
+                                         C.c_void_p]
+        L.orc_beamlet_tables.restype = C.c_int
+        L.orc_beamlet_picks.argtypes = [C.POINTER(OrcProblem), C.c_ulonglong, C.c_ulonglong,
+                                        C.c_void_p]
         L.orc_history_records.argtypes = [C.POINTER(OrcProblem), C.c_ulonglong, C.c_ulonglong,
                                           C.c_void_p, C.c_void_p]
         _lib = L
@@ -155,6 +163,8 @@ class _Prepared:
             self.beamlets = np.ascontiguousarray(src.beamlets, np.float64)
             p.n_beamlets = self.beamlets.shape[0]
             p.beamlets = self.beamlets.ctypes.data_as(C.POINTER(C.c_double))
+        p.beamlet_sampler = SAMPLERS[src.sampler]
+        p.metro_chains = src.chains
         p.n_hist, p.n_batches = prob.n_histories, prob.n_batches
         p.seed, p.request_id = prob.seed, prob.request_id
         flags = prob.flags
@@ -257,6 +267,26 @@ def sources(prob, first: int, n: int) -> np.ndarray:
     prep = _Prepared(prob)
     out = np.zeros((n, 8))
     lib().orc_sources(C.byref(prep.c), first, n, _ptr(out))
+    return out
+
+
+def beamlet_tables(prob):
+    """(index, prob, alias): the positive-weight beamlet list (rows of the
+    fluence map) and its Walker alias table, positions in that list."""
+    prep = _Prepared(prob)
+    nb = prep.beamlets.shape[0]
+    index = np.zeros(nb, np.int32)
+    cut = np.zeros(nb)
+    alias = np.zeros(nb, np.int32)
+    nf = lib().orc_beamlet_tables(C.byref(prep.c), _ptr(index), _ptr(cut), _ptr(alias))
+    return index[:nf], cut[:nf], alias[:nf]
+
+
+def beamlet_picks(prob, first: int, n: int) -> np.ndarray:
+    """Beamlet rows chosen for histories [first, first+n) by the source's sampler."""
+    prep = _Prepared(prob)
+    out = np.zeros(n, np.int32)
+    lib().orc_beamlet_picks(C.byref(prep.c), first, n, _ptr(out))
     return out
 
 

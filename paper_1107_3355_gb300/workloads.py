@@ -246,6 +246,8 @@ class Source:
     half_v: float = 0.0
     beamlets: Optional[np.ndarray] = None
     annihilation: bool = True
+    sampler: str = "cdf"           # beamlet sampler: "cdf", "alias" or "metropolis"
+    chains: int = 4096             # Metropolis chains (Algorithm A1)
 
 
 def pencil_source(phantom: Phantom, energy: float, particle=PHOTON) -> Source:
