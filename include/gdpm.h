@@ -65,6 +65,19 @@ typedef struct {
 
 enum { GDPM_PHOTON = 0, GDPM_ELECTRON = 1 };
 enum { GDPM_GEO_PENCIL = 0, GDPM_GEO_POINT_FIELD = 1, GDPM_GEO_BEAMLETS = 2 };
+/* Beamlet samplers of a fluence map (Sec. 2.3.1), all drawing beamlet I with
+ * probability f_I / sum f over the beamlets of positive weight:
+ *   GDPM_SAMPLE_CDF: the I with P(I) <= r < P(I+1) on the cumulative
+ *     fluence (binary search; r is the primary's own uniform);
+ *   GDPM_SAMPLE_ALIAS: Walker's alias method (table by Vose's procedure);
+ *   GDPM_SAMPLE_METROPOLIS: the Metropolis chain of Algorithm A1 -- propose
+ *     a uniform J, move there with probability min(1, f_J / f_Iprev).
+ *     metropolis_chains C independent chains; history h is step h div C of
+ *     chain h mod C, so results depend on the seed, not on scheduling.
+ * Alias and Metropolis take their proposal and acceptance words from the
+ * Philox block at counter (h, 0, 0, 0); chain c starts at a uniform index
+ * from the block at (c, 0, 1, 0). */
+enum { GDPM_SAMPLE_CDF = 0, GDPM_SAMPLE_ALIAS = 1, GDPM_SAMPLE_METROPOLIS = 2 };
 
 /* Table/transport flags (gdpm_tables_build). */
 #define GDPM_FLAG_COMPTON_ONLY 2   /* zero photoelectric and pair cross sections */
@@ -78,6 +91,9 @@ enum { GDPM_GEO_PENCIL = 0, GDPM_GEO_POINT_FIELD = 1, GDPM_GEO_BEAMLETS = 2 };
  *   GDPM_GEO_BEAMLETS: fluence map (Sec. 2.3.1); `beamlets` holds
  *     n_beamlets rows of 17 doubles: source(3) centre(3) axis_u(3) axis_v(3)
  *     u0 u1 v0 v1 (beamlet rectangle in the axis frame, cm) weight f_I.
+ *     `beamlet_sampler` picks the sampler (GDPM_SAMPLE_*, default 0) and
+ *     `metropolis_chains` the chain count C of the Metropolis sampler
+ *     (0 means 4096; at most 1<<24).
  * Energy: n_bins intervals with edges bin_edges[0..n_bins] and relative
  * weights bin_weights[0..n_bins-1]; a monoenergetic source is one interval
  * with equal edges.  Histories of each batch are allotted to intervals by
@@ -95,6 +111,8 @@ typedef struct {
     int n_beamlets;
     const double *beamlets;
     int annihilation;              /* 1: positrons end in two 0.511 MeV photons (Sec. 2.1) */
+    int beamlet_sampler;           /* GDPM_SAMPLE_* (fluence maps only) */
+    int metropolis_chains;         /* chains C of GDPM_SAMPLE_METROPOLIS; 0 = 4096 */
 } gdpm_source_desc;
 
 /* Run statistics: energy ledger (FP64, MeV) and exact integer counts. */
@@ -270,6 +288,14 @@ int gdpm_tables_export(gdpm_tables *t, int which, double *out, int64_t *count);
 int gdpm_debug_sources(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
                        int n_batches, uint64_t first, uint64_t n, double *out);
 
+/* Beamlet picked for each history of [first, first+n) by the current
+ * source's sampler (Sec. 2.3.1; the source must be a fluence map), written
+ * as the beamlet's row in the map to the device array `out` (n int32).  The
+ * Metropolis chains are run from their start up to history first+n-1.
+ * Errors: GDPM_E_ARG (not a fluence map, host `out`, first+n > 2^32),
+ * GDPM_E_STATE (no source set). */
+int gdpm_debug_beamlets(gdpm_ctx *ctx, uint64_t first, uint64_t n, int32_t *out);
+
 /* ------------------------------------------------------------------ no allocation */
 
 /* gdpm_simulate_noalloc -- the same dose calculation as gdpm_simulate, for
@@ -281,7 +307,7 @@ int gdpm_debug_sources(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_
  *
  * All work buffers (batch tally, batch sums, particle queues, counters,
  * source arrays, Woodcock majorant) come from one file-scope device array of
- * GDPM_NOALLOC_SCRATCH_BYTES (about 3.6 MB).  Every GPU that loads this
+ * GDPM_NOALLOC_SCRATCH_BYTES (about 3.9 MB).  Every GPU that loads this
  * library holds that array until the process exits.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) for that
  * device; make that first call before any stream capture begins.
@@ -289,7 +315,8 @@ int gdpm_debug_sources(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_
  * Limits (GDPM_E_ARG beyond them): nx*ny*nz <= GDPM_NOALLOC_MAX_VOXELS, at
  * most GDPM_NOALLOC_QUEUE_CAPACITY banked particles per queue fill (more is
  * reported as GDPM_E_QUEUE_OVERFLOW), n_batches*(n_bins+1) <=
- * GDPM_NOALLOC_MAX_PREFIX, n_beamlets <= GDPM_NOALLOC_MAX_BEAMLETS, table
+ * GDPM_NOALLOC_MAX_PREFIX, n_beamlets <= GDPM_NOALLOC_MAX_BEAMLETS,
+ * Metropolis chains <= GDPM_NOALLOC_MAX_CHAINS, table
  * grid <= 8192 energies.  dose_out and sigma_out must be device arrays (or
  * NULL); stats_out is a host struct (or NULL).  The phantom, tables and
  * source are the caller's existing handles on this context; the context's
@@ -306,7 +333,8 @@ int gdpm_debug_sources(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_
 #define GDPM_NOALLOC_QUEUE_CAPACITY 16384
 #define GDPM_NOALLOC_MAX_PREFIX 65536
 #define GDPM_NOALLOC_MAX_BEAMLETS 1024
-#define GDPM_NOALLOC_SCRATCH_BYTES 3729408
+#define GDPM_NOALLOC_MAX_CHAINS 65536
+#define GDPM_NOALLOC_SCRATCH_BYTES 4024320
 int gdpm_simulate_noalloc(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
                           int n_batches, double *dose_out, double *sigma_out,
                           gdpm_stats *stats_out);

@@ -193,6 +193,9 @@ static int source_copy(const gdpm_source_desc* s, gdpm_source_state& st) {
             bw += s->beamlets[size_t(b) * 17 + 16];
         }
         if (!(bw > 0)) return GDPM_E_ARG;
+        if (s->beamlet_sampler < GDPM_SAMPLE_CDF || s->beamlet_sampler > GDPM_SAMPLE_METROPOLIS ||
+            s->metropolis_chains < 0 || s->metropolis_chains > (1 << 24))
+            return GDPM_E_ARG;
     }
     const double dn = s->direction[0] * s->direction[0] + s->direction[1] * s->direction[1] +
                       s->direction[2] * s->direction[2];
@@ -207,9 +210,57 @@ static int source_copy(const gdpm_source_desc* s, gdpm_source_state& st) {
     st.desc.bin_edges = nullptr;
     st.desc.bin_weights = nullptr;
     st.desc.beamlets = nullptr;
+    if (st.desc.metropolis_chains == 0) st.desc.metropolis_chains = 4096;
     st.set = true;
     return GDPM_OK;
 }
+
+// Beamlets of positive weight, their cumulative weights and Walker's alias
+// table (Vose's procedure: scaled weights q = f nf / sum f; the last "small"
+// entry (q < 1) takes its cut-off q and the last "large" entry as alias,
+// which gives up 1 - q of its own mass).  Pure additions and single
+// products, so the table is the same on every host.
+void beamlet_tables_host(const std::vector<double>& rows17, BeamletHost& out) {
+    const int nb = int(rows17.size() / 17);
+    out = BeamletHost{};
+    double tot = 0;
+    for (int b = 0; b < nb; ++b) tot += rows17[size_t(b) * 17 + 16];
+    double acc = 0;
+    for (int b = 0; b < nb; ++b) {
+        const double w = rows17[size_t(b) * 17 + 16];
+        acc += w;
+        if (!(w > 0)) continue;
+        for (int k = 0; k < 16; ++k) out.rows.push_back(float(rows17[size_t(b) * 17 + k]));
+        out.row.push_back(b);
+        out.f.push_back(w);
+        out.cdf.push_back(acc / tot);
+    }
+    const int n = int(out.f.size());
+    if (n == 0) return;
+    out.cdf[n - 1] = 1.0;
+    double sum = 0;
+    for (double w : out.f) sum += w;
+    const double scale = double(n) / sum;
+    std::vector<double> q(n);
+    std::vector<int> small, large;
+    for (int k = 0; k < n; ++k) {
+        q[k] = out.f[k] * scale;
+        (q[k] < 1.0 ? small : large).push_back(k);
+    }
+    out.cut.assign(n, 1.0);
+    out.alias.resize(n);
+    for (int k = 0; k < n; ++k) out.alias[k] = k;
+    while (!small.empty() && !large.empty()) {
+        const int l = small.back(), g = large.back();
+        small.pop_back();
+        large.pop_back();
+        out.cut[l] = q[l];
+        out.alias[l] = g;
+        q[g] = (q[g] + q[l]) - 1.0;
+        (q[g] < 1.0 ? small : large).push_back(g);
+    }
+}
+
 
 static int source_upload(Runner& r, const gdpm_source_state& s, DevSource& d) {
     const gdpm_source_desc& g = s.desc;
@@ -217,7 +268,9 @@ static int source_upload(Runner& r, const gdpm_source_state& s, DevSource& d) {
     d.geometry = g.geometry;
     d.annihilation = g.annihilation ? 1 : 0;
     d.n_bins = int(s.weights.size());
-    d.n_beamlets = g.geometry == GDPM_GEO_BEAMLETS ? int(s.beamlets.size() / 17) : 0;
+    d.n_beamlets = 0;
+    d.sampler = g.beamlet_sampler;
+    d.n_chains = uint32_t(g.metropolis_chains);
     for (int a = 0; a < 3; ++a) {
         d.origin[a] = float(g.origin[a]);
         d.center[a] = float(g.center[a]);
@@ -236,25 +289,32 @@ static int source_upload(Runner& r, const gdpm_source_state& s, DevSource& d) {
     d.edges = static_cast<const float*>(r.ws.edges.p);
     d.beamlets = nullptr;
     d.bl_cdf = nullptr;
-    if (d.n_beamlets > 0) {
-        const int nbl = d.n_beamlets;
-        std::vector<float> rows(size_t(nbl) * 16);
-        std::vector<double> cdf(nbl);
-        double tot = 0;
-        for (int b = 0; b < nbl; ++b) tot += s.beamlets[size_t(b) * 17 + 16];
-        double acc = 0;
-        for (int b = 0; b < nbl; ++b) {
-            for (int k = 0; k < 16; ++k) rows[size_t(b) * 16 + k] = float(s.beamlets[size_t(b) * 17 + k]);
-            acc += s.beamlets[size_t(b) * 17 + 16];
-            cdf[b] = acc / tot;
-        }
-        cdf[nbl - 1] = 1.0;
-        if ((rc = ensure(r.ws.beamlets, rows.size() * 4)) || (rc = ensure(r.ws.bl_cdf, cdf.size() * 8)))
+    d.bl_row = nullptr;
+    d.bl_f = nullptr;
+    d.al_cut = nullptr;
+    d.al_alias = nullptr;
+    BeamletHost bh;
+    if (g.geometry == GDPM_GEO_BEAMLETS) beamlet_tables_host(s.beamlets, bh);
+    if (!bh.f.empty()) {
+        const size_t nbl = bh.f.size();
+        Workspace& w = r.ws;
+        if ((rc = ensure(w.beamlets, nbl * 64)) || (rc = ensure(w.bl_cdf, nbl * 8)) ||
+            (rc = ensure(w.bl_row, nbl * 4)) || (rc = ensure(w.bl_f, nbl * 8)) ||
+            (rc = ensure(w.al_cut, nbl * 8)) || (rc = ensure(w.al_alias, nbl * 4)))
             return rc;
-        GDPM_CUDA_TRY(cudaMemcpyAsync(r.ws.beamlets.p, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, r.stream));
-        GDPM_CUDA_TRY(cudaMemcpyAsync(r.ws.bl_cdf.p, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, r.stream));
-        d.beamlets = static_cast<const float*>(r.ws.beamlets.p);
-        d.bl_cdf = static_cast<const double*>(r.ws.bl_cdf.p);
+        GDPM_CUDA_TRY(cudaMemcpyAsync(w.beamlets.p, bh.rows.data(), nbl * 64, cudaMemcpyHostToDevice, r.stream));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(w.bl_cdf.p, bh.cdf.data(), nbl * 8, cudaMemcpyHostToDevice, r.stream));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(w.bl_row.p, bh.row.data(), nbl * 4, cudaMemcpyHostToDevice, r.stream));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(w.bl_f.p, bh.f.data(), nbl * 8, cudaMemcpyHostToDevice, r.stream));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(w.al_cut.p, bh.cut.data(), nbl * 8, cudaMemcpyHostToDevice, r.stream));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(w.al_alias.p, bh.alias.data(), nbl * 4, cudaMemcpyHostToDevice, r.stream));
+        d.n_beamlets = int(nbl);
+        d.beamlets = static_cast<const float*>(w.beamlets.p);
+        d.bl_cdf = static_cast<const double*>(w.bl_cdf.p);
+        d.bl_row = static_cast<const int*>(w.bl_row.p);
+        d.bl_f = static_cast<const double*>(w.bl_f.p);
+        d.al_cut = static_cast<const double*>(w.al_cut.p);
+        d.al_alias = static_cast<const int*>(w.al_alias.p);
     }
     // the host vectors above are staged by the copies; make the copies
     // complete before they go out of scope
@@ -387,7 +447,7 @@ static size_t bytes_needed(gdpm_ctx* ctx, const Runner& r, size_t V, uint64_t n_
 // ctl row k: [0] pop counter of phase k, [1] count of P[k], [2] count of E[k].
 static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_source_state& src,
                       uint64_t first, uint64_t n, uint32_t nb_small, uint32_t nb_rem, uint32_t chunk,
-                      int64_t& phases) {
+                      int64_t& phases, int64_t& aux) {
     Workspace& ws = r.ws;
     cudaStream_t s = r.stream;
     uint32_t* ctl = static_cast<uint32_t*>(ws.ctl.p);
@@ -411,6 +471,15 @@ static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_s
             A.src_first = uint32_t(next);
             next += A.n_src;
             left -= A.n_src;
+            if (P.S.sampler == GDPM_SAMPLE_METROPOLIS && P.S.n_beamlets > 0) {
+                // this phase's beamlets: advance the chains (Algorithm A1)
+                uint32_t* pick = static_cast<uint32_t*>(ws.pick.p);
+                const int rc = launch_metropolis(s, P, A.src_first, A.n_src,
+                                                 static_cast<uint32_t*>(ws.chains.p), pick);
+                if (rc) return rc;
+                A.bl_pick = pick;
+                ++aux;
+            }
         }
         A.head = ctl + size_t(k) * 4 + 0;
         if (ph) {
@@ -514,6 +583,13 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
     }
     GDPM_CUDA_TRY(cudaMemcpyAsync(ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, s));
     if ((rc = source_upload(r, src, P.S))) return rc;
+    int64_t aux = 0;          // launches besides the transport phases
+    if (P.S.sampler == GDPM_SAMPLE_METROPOLIS && P.S.n_beamlets > 0) {
+        if ((rc = ensure(ws.chains, size_t(P.S.n_chains) * 4)) || (rc = ensure(ws.pick, size_t(chunk) * 4)))
+            return rc;
+        if ((rc = launch_metropolis_init(s, P, static_cast<uint32_t*>(ws.chains.p)))) return rc;
+        ++aux;
+    }
     P.counters = static_cast<unsigned long long*>(ws.counters.p);
     P.ledger = static_cast<double*>(ws.ledger.p);
     P.status = static_cast<uint32_t*>(ws.status.p);
@@ -550,7 +626,8 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
         P.edep = static_cast<double*>(ws.edep.p);
         P.edep_hi = static_cast<float*>(ws.edep.p);
         P.edep_lo = static_cast<float*>(ws.edep.p) + V * size_t(n_batches);
-        run_rc = run_phases(ctx, r, P, src, 0, n_hist, nb_small, nb_rem, chunk, phases);
+        run_rc = run_phases(ctx, r, P, src, 0, n_hist, nb_small, nb_rem, chunk, phases, aux);
+        ++aux;
         if (run_rc == GDPM_OK) {
             const size_t pi = prof_begin(ctx, r, s, 2);
             run_rc = launch_fold_batches(ctx, s, P, V, n_batches, nb_small, nb_rem,
@@ -570,7 +647,8 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
             const int buf = ctx->overlap_fold ? (b & 1) : 0;
             select_tally(r, P, buf);
             GDPM_CUDA_TRY(cudaStreamWaitEvent(s, r.fold_done[buf], 0));
-            run_rc = run_phases(ctx, r, P, src, first, nb, nb_small, nb_rem, chunk, phases);
+            run_rc = run_phases(ctx, r, P, src, first, nb, nb_small, nb_rem, chunk, phases, aux);
+            ++aux;
             if (run_rc == GDPM_OK) {
                 GDPM_CUDA_TRY(cudaEventRecord(r.batch_done[buf], s));
                 GDPM_CUDA_TRY(cudaStreamWaitEvent(side, r.batch_done[buf], 0));
@@ -619,7 +697,7 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
         std::memset(st, 0, sizeof(*st));
         fill_stats(hc, hl, st);
         st->phases = phases;
-        st->launches = phases + n_batches + 2;
+        st->launches = phases + aux + 2;    // + finalize and metric
         float ms = 0;
         cudaEventElapsedTime(&ms, r.ev0, r.ev1);
         st->transport_ms = ms;
@@ -1052,6 +1130,39 @@ int gdpm_tables_export(gdpm_tables* t, int which, double* out, int64_t* count) {
     return GDPM_OK;
 }
 
+// Checks: run the Metropolis chains from their start through history
+// n_hist - 1 into the pick buffer (nothing to do for the other samplers).
+static int run_chains(Runner& r, const SimParams& P, uint64_t n_hist) {
+    if (P.S.sampler != GDPM_SAMPLE_METROPOLIS || P.S.n_beamlets == 0) return GDPM_OK;
+    int rc;
+    if ((rc = ensure(r.ws.chains, size_t(P.S.n_chains) * 4)) || (rc = ensure(r.ws.pick, n_hist * 4)))
+        return rc;
+    uint32_t* chains = static_cast<uint32_t*>(r.ws.chains.p);
+    if ((rc = launch_metropolis_init(r.stream, P, chains))) return rc;
+    return launch_metropolis(r.stream, P, 0, uint32_t(n_hist), chains, static_cast<uint32_t*>(r.ws.pick.p));
+}
+
+int gdpm_debug_beamlets(gdpm_ctx* ctx, uint64_t first, uint64_t n, int32_t* out) {
+    if (!ctx) return GDPM_E_ARG;
+    if (!ctx->src.set) return GDPM_E_STATE;
+    if (ctx->src.desc.geometry != GDPM_GEO_BEAMLETS || !out || !is_device_ptr(out) ||
+        first + n > (1ull << 32) || n == 0)
+        return GDPM_E_ARG;
+    GDPM_CUDA_TRY(cudaSetDevice(ctx->device));
+    Runner& r = ctx->run;
+    SimParams P{};
+    P.key0 = uint32_t(ctx->seed);
+    P.key1 = uint32_t(ctx->seed >> 32) ^ ctx->request_id;
+    int rc;
+    if ((rc = source_upload(r, ctx->src, P.S))) return rc;
+    if ((rc = run_chains(r, P, first + n))) return rc;
+    const uint32_t* pick = P.S.sampler == GDPM_SAMPLE_METROPOLIS ? static_cast<const uint32_t*>(r.ws.pick.p) + first
+                                                                  : nullptr;
+    if ((rc = launch_debug_beamlets(r.stream, P, uint32_t(first), uint32_t(n), pick, out))) return rc;
+    GDPM_CUDA_TRY(cudaStreamSynchronize(r.stream));
+    return GDPM_OK;
+}
+
 int gdpm_debug_sources(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_histories,
                        int n_batches, uint64_t first, uint64_t n, double* out) {
     if (!ctx) return GDPM_E_ARG;
@@ -1073,6 +1184,9 @@ int gdpm_debug_sources(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_
     A.nb_small = uint32_t(n_histories / n_batches);
     A.nb_rem = uint32_t(n_histories % n_batches);
     A.bin_prefix = static_cast<const uint32_t*>(r.ws.prefix.p);
+    if ((rc = run_chains(r, P, first + n))) return rc;
+    if (P.S.sampler == GDPM_SAMPLE_METROPOLIS && P.S.n_beamlets > 0)
+        A.bl_pick = static_cast<const uint32_t*>(r.ws.pick.p) + first;
     if ((rc = launch_debug_sources(ctx, P, A, n, out))) return rc;
     GDPM_CUDA_TRY(cudaStreamSynchronize(r.stream));
     return GDPM_OK;

@@ -22,6 +22,8 @@ constexpr size_t kNaMaxVoxels = GDPM_NOALLOC_MAX_VOXELS;
 constexpr uint32_t kNaQueueCap = GDPM_NOALLOC_QUEUE_CAPACITY;
 constexpr size_t kNaMaxPrefix = GDPM_NOALLOC_MAX_PREFIX;
 constexpr int kNaMaxBeamlets = GDPM_NOALLOC_MAX_BEAMLETS;
+constexpr uint32_t kNaMaxChains = GDPM_NOALLOC_MAX_CHAINS;
+constexpr uint32_t kNaChunk = kNaQueueCap / 8;      // primaries per photon phase
 constexpr int kNaMaxEnergy = 8192;
 constexpr int kNaCtlRows = 1024;
 
@@ -41,7 +43,13 @@ constexpr size_t kOffMaj = kOffStatus + al(16);
 constexpr size_t kOffEdges = kOffMaj + al(size_t(kNaMaxEnergy) * 4);
 constexpr size_t kOffBeamlets = kOffEdges + al((GDPM_MAX_BINS + 1) * 4);
 constexpr size_t kOffCdf = kOffBeamlets + al(size_t(kNaMaxBeamlets) * 16 * 4);
-constexpr size_t kScratchBytes = kOffCdf + al(size_t(kNaMaxBeamlets) * 8);
+constexpr size_t kOffRow = kOffCdf + al(size_t(kNaMaxBeamlets) * 8);
+constexpr size_t kOffF = kOffRow + al(size_t(kNaMaxBeamlets) * 4);
+constexpr size_t kOffCut = kOffF + al(size_t(kNaMaxBeamlets) * 8);
+constexpr size_t kOffAlias = kOffCut + al(size_t(kNaMaxBeamlets) * 8);
+constexpr size_t kOffChains = kOffAlias + al(size_t(kNaMaxBeamlets) * 4);
+constexpr size_t kOffPick = kOffChains + al(size_t(kNaMaxChains) * 4);
+constexpr size_t kScratchBytes = kOffPick + al(size_t(kNaChunk) * 4);
 static_assert(kScratchBytes == GDPM_NOALLOC_SCRATCH_BYTES, "header and layout disagree");
 
 // The scratch.  In host code `g_scratch` only names a host-side stand-in; its
@@ -129,9 +137,13 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     if (!src.set) return GDPM_E_STATE;
     const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
     const int n_bins = int(src.weights.size());
-    const int n_bl = src.desc.geometry == GDPM_GEO_BEAMLETS ? int(src.beamlets.size() / 17) : 0;
+    BeamletHost bh;
+    if (src.desc.geometry == GDPM_GEO_BEAMLETS) beamlet_tables_host(src.beamlets, bh);
+    const int n_bl = int(bh.f.size());
+    const bool metro = n_bl > 0 && src.desc.beamlet_sampler == GDPM_SAMPLE_METROPOLIS;
     // limits of the fixed scratch
     if (V > kNaMaxVoxels || tb->n_e > kNaMaxEnergy || n_bl > kNaMaxBeamlets ||
+        (metro && uint32_t(src.desc.metropolis_chains) > kNaMaxChains) ||
         size_t(n_batches) * (n_bins + 1) > kNaMaxPrefix)
         return GDPM_E_ARG;
     if (n_batches < 2 || n_hist < uint64_t(n_batches) || n_hist >= (1ull << 32)) return GDPM_E_ARG;
@@ -167,23 +179,23 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     float* edges = reinterpret_cast<float*>(base + kOffEdges);
     float* bl = reinterpret_cast<float*>(base + kOffBeamlets);
     double* cdf = reinterpret_cast<double*>(base + kOffCdf);
+    int* bl_row = reinterpret_cast<int*>(base + kOffRow);
+    double* bl_f = reinterpret_cast<double*>(base + kOffF);
+    double* al_cut = reinterpret_cast<double*>(base + kOffCut);
+    int* al_alias = reinterpret_cast<int*>(base + kOffAlias);
+    uint32_t* chains = reinterpret_cast<uint32_t*>(base + kOffChains);
+    uint32_t* pick = reinterpret_cast<uint32_t*>(base + kOffPick);
 
     // source arrays and majorant into the scratch
     std::vector<float> ef(src.edges.begin(), src.edges.end());
     GDPM_CUDA_TRY(cudaMemcpyAsync(edges, ef.data(), ef.size() * 4, cudaMemcpyHostToDevice, s));
     if (n_bl > 0) {
-        std::vector<float> rows(size_t(n_bl) * 16);
-        std::vector<double> c(n_bl);
-        double tot = 0, acc = 0;
-        for (int b = 0; b < n_bl; ++b) tot += src.beamlets[size_t(b) * 17 + 16];
-        for (int b = 0; b < n_bl; ++b) {
-            for (int k = 0; k < 16; ++k) rows[size_t(b) * 16 + k] = float(src.beamlets[size_t(b) * 17 + k]);
-            acc += src.beamlets[size_t(b) * 17 + 16];
-            c[b] = acc / tot;
-        }
-        c[n_bl - 1] = 1.0;
-        GDPM_CUDA_TRY(cudaMemcpyAsync(bl, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, s));
-        GDPM_CUDA_TRY(cudaMemcpyAsync(cdf, c.data(), c.size() * 8, cudaMemcpyHostToDevice, s));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(bl, bh.rows.data(), size_t(n_bl) * 64, cudaMemcpyHostToDevice, s));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(cdf, bh.cdf.data(), size_t(n_bl) * 8, cudaMemcpyHostToDevice, s));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(bl_row, bh.row.data(), size_t(n_bl) * 4, cudaMemcpyHostToDevice, s));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(bl_f, bh.f.data(), size_t(n_bl) * 8, cudaMemcpyHostToDevice, s));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(al_cut, bh.cut.data(), size_t(n_bl) * 8, cudaMemcpyHostToDevice, s));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(al_alias, bh.alias.data(), size_t(n_bl) * 4, cudaMemcpyHostToDevice, s));
     }
     if ((rc = launch_majorant_into(s, ph, tb, maj))) return rc;
     std::vector<uint32_t> prefix(size_t(n_batches) * (n_bins + 1));
@@ -239,9 +251,20 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     S.edges = edges;
     S.beamlets = n_bl ? bl : nullptr;
     S.bl_cdf = n_bl ? cdf : nullptr;
+    S.bl_row = n_bl ? bl_row : nullptr;
+    S.bl_f = n_bl ? bl_f : nullptr;
+    S.al_cut = n_bl ? al_cut : nullptr;
+    S.al_alias = n_bl ? al_alias : nullptr;
+    S.sampler = g.beamlet_sampler;
+    S.n_chains = uint32_t(g.metropolis_chains);
+    int64_t aux = 0;
+    if (metro) {
+        if ((rc = launch_metropolis_init(s, P, chains))) return rc;
+        ++aux;
+    }
 
     const uint64_t nb_max = (n_hist + n_batches - 1) / n_batches;
-    const uint32_t chunk = uint32_t(std::min<uint64_t>(kNaQueueCap / 8, nb_max));
+    const uint32_t chunk = uint32_t(std::min<uint64_t>(kNaChunk, nb_max));
     const int max_phases = std::min(ctx->max_phases, kNaCtlRows - 4);
     const bool photon_src = g.particle == GDPM_PHOTON;
     GDPM_CUDA_TRY(cudaEventRecord(ctx->ev0, s));
@@ -267,6 +290,11 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
                 A.src_first = uint32_t(first + next);
                 next += A.n_src;
                 left -= A.n_src;
+                if (metro) {
+                    if ((run_rc = launch_metropolis(s, P, A.src_first, A.n_src, chains, pick))) break;
+                    A.bl_pick = pick;
+                    ++aux;
+                }
             }
             A.head = ctl + size_t(k) * 4;
             if (ph_phase) {
@@ -341,7 +369,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
         st->pops[1] = int64_t(hc[C_POP_EL]);
         st->crossings = int64_t(hc[C_CROSS]);
         st->phases = phases;
-        st->launches = phases + n_batches + 3;
+        st->launches = phases + aux + n_batches + 3;   // + majorant, folds, finalize, metric
         double dmax;
         std::memcpy(&dmax, &hl[L_DMAX], 8);
         st->dmax = dmax;

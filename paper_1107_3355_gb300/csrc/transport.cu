@@ -182,6 +182,29 @@ __device__ bool enter_box(const SimParams& P, Part& p) {
     return true;
 }
 
+// Beamlet of history h as its position in the list of positive-weight
+// beamlets (Sec. 2.3.1).  Metropolis picks were made by k_metropolis before
+// the phase; the alias method reads the Philox block at (h, 0, 0, 0); the
+// cumulative search uses the primary's own uniform rw.
+__device__ __forceinline__ int pick_beamlet(const DevSource& S, const PhaseArgs& A, uint32_t idx,
+                                            uint32_t h, float rw, uint32_t k0, uint32_t k1) {
+    if (S.sampler == GDPM_SAMPLE_METROPOLIS) return int(A.bl_pick[idx]);
+    if (S.sampler == GDPM_SAMPLE_ALIAS) {
+        const uint4 w = philox_block(h, 0u, 0u, 0u, k0, k1);
+        const int J = int(__umulhi(w.x, uint32_t(S.n_beamlets)));
+        const double u = (double(w.y) + 0.5) * 0x1p-32;
+        return u < S.al_cut[J] ? J : S.al_alias[J];
+    }
+    // the I with P(I) <= r < P(I+1)
+    const double rr = double(rw);
+    int l = 0, hi = S.n_beamlets - 1;
+    while (l < hi) {
+        const int mid = (l + hi) >> 1;
+        if (rr < S.bl_cdf[mid]) hi = mid; else l = mid + 1;
+    }
+    return l;
+}
+
 // Primary number `idx` of this phase (Sec. 2.3): energy from the batch's
 // spectrum interval allotment (uniform inside the interval), position and
 // direction from the source geometry.  Draw 0 of the primary's stream:
@@ -222,14 +245,8 @@ __device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t id
             src = S.origin; cen = S.center; au = S.axis_u; av = S.axis_v;
             a0 = -S.half_u; a1 = S.half_u; b0 = -S.half_v; b1 = S.half_v;
         } else {
-            // beamlet I with P(I) <= r < P(I+1) on the cumulative fluence (Sec. 2.3.1)
-            const double rr = double(r.w);
-            int l = 0, h = S.n_beamlets - 1;
-            while (l < h) {
-                const int mid = (l + h) >> 1;
-                if (rr < S.bl_cdf[mid]) h = mid; else l = mid + 1;
-            }
-            const float* row = S.beamlets + size_t(l) * 16;
+            const int k = pick_beamlet(S, A, idx, h, r.w, P.key0, P.key1);
+            const float* row = S.beamlets + size_t(k) * 16;
             src = row; cen = row + 3; au = row + 6; av = row + 9;
             a0 = row[12]; a1 = row[13]; b0 = row[14]; b1 = row[15];
         }
@@ -815,6 +832,57 @@ __global__ void k_debug_sample(int kind, float a, float b, uint64_t n, uint32_t 
     }
 }
 
+// Metropolis chains of Algorithm A1, one thread per chain c.  Chain c starts
+// at a uniform beamlet from the Philox block at (c, 0, 1, 0).
+__global__ void k_metropolis_init(const SimParams P, uint32_t* chains) {
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.S.n_chains) return;
+    const uint4 w = philox_block(c, 0u, 1u, 0u, P.key0, P.key1);
+    chains[c] = __umulhi(w.x, uint32_t(P.S.n_beamlets));
+}
+
+// Advance every chain through the histories of [first, first+n) that belong
+// to it (h = c, c + C, c + 2C, ...), in order: propose J uniform, accept
+// when u f_I < f_J (u < f_J / f_I without the division), record the state
+// as the beamlet of history h.
+__global__ void k_metropolis(const SimParams P, uint32_t first, uint32_t n, uint32_t* chains,
+                             uint32_t* pick) {
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t C = P.S.n_chains;
+    if (c >= C) return;
+    const uint32_t nf = uint32_t(P.S.n_beamlets);
+    const double* f = P.S.bl_f;
+    uint32_t I = chains[c];
+    double fI = f[I];
+    const uint64_t end = uint64_t(first) + n;
+    for (uint64_t h = uint64_t(first) + (uint64_t(c) + C - first % C) % C; h < end; h += C) {
+        const uint4 w = philox_block(uint32_t(h), 0u, 0u, 0u, P.key0, P.key1);
+        const uint32_t J = __umulhi(w.x, nf);
+        const double fJ = f[J];
+        const double u = (double(w.y) + 0.5) * 0x1p-32;
+        if (u * fI < fJ) {
+            I = J;
+            fI = fJ;
+        }
+        pick[h - first] = I;
+    }
+    chains[c] = I;
+}
+
+// Beamlet rows of histories [first, first+n) (checks of the samplers).
+__global__ void k_debug_beamlets(const SimParams P, uint32_t first, uint32_t n,
+                                 const uint32_t* pick, int32_t* out) {
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        Part p{};
+        p.hist = first + s;
+        p.pidlo = 1u;
+        const float4 r = draw(p, P.key0, P.key1);
+        PhaseArgs A{};
+        A.bl_pick = pick;
+        out[s] = P.S.bl_row[pick_beamlet(P.S, A, s, first + s, r.w, P.key0, P.key1)];
+    }
+}
+
 __global__ void k_debug_sources(const SimParams P, const PhaseArgs A, uint64_t n, double* out) {
     for (uint64_t s = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; s < n;
          s += uint64_t(gridDim.x) * blockDim.x) {
@@ -889,6 +957,29 @@ int launch_debug_sources(gdpm_ctx* ctx, const SimParams& P, const PhaseArgs& A, 
                          double* out) {
     const uint32_t grid = uint32_t(ctx->sm_count) * 2u;
     k_debug_sources<<<grid, 256, 0, ctx->stream>>>(P, A, n, out);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+int launch_metropolis_init(cudaStream_t st, const SimParams& P, uint32_t* chains) {
+    k_metropolis_init<<<(P.S.n_chains + 255) / 256, 256, 0, st>>>(P, chains);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+int launch_metropolis(cudaStream_t st, const SimParams& P, uint32_t first, uint32_t n,
+                      uint32_t* chains, uint32_t* pick) {
+    // a chain's steps are sequential: one thread per chain, 128 per block to
+    // spread a few thousand chains over all SMs
+    k_metropolis<<<(P.S.n_chains + 127) / 128, 128, 0, st>>>(P, first, n, chains, pick);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+int launch_debug_beamlets(cudaStream_t st, const SimParams& P, uint32_t first, uint32_t n,
+                          const uint32_t* pick, int32_t* out) {
+    const uint32_t grid = std::max(1u, std::min(1024u, (n + 255) / 256));
+    k_debug_beamlets<<<grid, 256, 0, st>>>(P, first, n, pick, out);
     GDPM_CUDA_TRY(cudaGetLastError());
     return GDPM_OK;
 }

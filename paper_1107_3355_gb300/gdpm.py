@@ -46,7 +46,7 @@ EXPORTED = ["gdpm_context_create", "gdpm_context_destroy", "gdpm_set_param",
             "gdpm_tables_destroy", "gdpm_source_set", "gdpm_simulate",
             "gdpm_set_history_records", "gdpm_request_submit", "gdpm_request_poll",
             "gdpm_strerror", "gdpm_debug_philox", "gdpm_debug_sample", "gdpm_tables_export",
-            "gdpm_debug_sources", "gdpm_simulate_noalloc"]
+            "gdpm_debug_sources", "gdpm_debug_beamlets", "gdpm_simulate_noalloc"]
 
 
 class gdpm_material_desc(C.Structure):
@@ -61,7 +61,12 @@ class gdpm_source_desc(C.Structure):
                 ("axis_v", C.c_double * 3), ("half_u", C.c_double), ("half_v", C.c_double),
                 ("n_bins", C.c_int), ("bin_edges", C.POINTER(C.c_double)),
                 ("bin_weights", C.POINTER(C.c_double)), ("n_beamlets", C.c_int),
-                ("beamlets", C.POINTER(C.c_double)), ("annihilation", C.c_int)]
+                ("beamlets", C.POINTER(C.c_double)), ("annihilation", C.c_int),
+                ("beamlet_sampler", C.c_int), ("metropolis_chains", C.c_int)]
+
+GDPM_SAMPLE_CDF, GDPM_SAMPLE_ALIAS, GDPM_SAMPLE_METROPOLIS = 0, 1, 2
+SAMPLERS = {"cdf": GDPM_SAMPLE_CDF, "alias": GDPM_SAMPLE_ALIAS,
+            "metropolis": GDPM_SAMPLE_METROPOLIS}
 
 
 _STAT_D1 = ["source_energy", "deposited", "escaped", "discarded"]
@@ -133,6 +138,7 @@ def lib():
                 "gdpm_debug_sample": [vp, i, d, d, u64, u64, vp, vp],
                 "gdpm_tables_export": [vp, i, vp, C.POINTER(C.c_int64)],
                 "gdpm_debug_sources": [vp, vp, vp, u64, i, u64, u64, vp],
+                "gdpm_debug_beamlets": [vp, u64, u64, vp],
                 "gdpm_simulate_noalloc": [vp, vp, vp, u64, i, vp, vp, C.POINTER(gdpm_stats)],
             }
             for name, args in sig.items():
@@ -244,6 +250,8 @@ class _SourceKeep:
             d.n_beamlets = self.beamlets.shape[0]
             d.beamlets = self.beamlets.ctypes.data_as(C.POINTER(C.c_double))
         d.annihilation = 1 if src.annihilation else 0
+        d.beamlet_sampler = SAMPLERS[src.sampler]
+        d.metropolis_chains = src.chains
         self.desc = d
 
 
@@ -305,6 +313,12 @@ def gdpm_tables_export(tables, which, out=None):
 def gdpm_debug_sources(ctx, phantom, tables, n_histories, n_batches, first, n, out):
     _check(lib().gdpm_debug_sources(ctx, phantom, tables, n_histories, n_batches, first, n,
                                     _ptr(out)), "gdpm_debug_sources")
+
+
+def gdpm_debug_beamlets(ctx, first, n, out):
+    """Beamlet rows the current source's sampler picks for histories
+    [first, first+n), into the device int32 array ``out``."""
+    _check(lib().gdpm_debug_beamlets(ctx, first, n, _ptr(out)), "gdpm_debug_beamlets")
 
 
 def gdpm_simulate_noalloc(ctx, phantom, tables, n_histories, n_batches, dose_out=None,

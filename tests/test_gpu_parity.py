@@ -354,13 +354,17 @@ def test_full_size_slab_sampled_histories():
     assert r["P_high"] > 0.9
 
 
-def test_ct_imrt_beamlets_same_seed():
+@pytest.mark.parametrize("sampler", ["cdf", "alias", "metropolis"])
+def test_ct_imrt_beamlets_same_seed(sampler):
     """Patient-like ellipsoid phantom (air, water, lung, bone, per-region
-    densities) at 1 cm voxels with the 7-beam fluence-map IMRT plan: the
-    cumulative-fluence beamlet sampling and gantry frames agree with the
+    densities) at 1 cm voxels with the 7-beam fluence-map IMRT plan: each
+    beamlet sampler of Sec. 2.3.1 and the gantry frames agree with the
     oracle history by history."""
     ph = W.ct_phantom(shape=(64, 64, 32), voxel=(1.0, 1.0, 1.0))
-    prob = W.Problem(ph, W.imrt_plan(ph), 20_000, 10, eabs_photon=0.05, eabs_electron=0.2,
+    src = W.imrt_plan(ph)
+    src.sampler = sampler
+    src.chains = 256
+    prob = W.Problem(ph, src, 20_000, 10, eabs_photon=0.05, eabs_electron=0.2,
                      e_min=0.005, e_max=6.5)
     d_o, s_o, led_o, rec_o, _ = O.run(prob, per_history=True)
     d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
