@@ -162,10 +162,11 @@ enum {
     GDPM_PARAM_METRIC_MIN_DENSITY = 14,/* sigma/Dmax only over voxels at least this dense
                                           (g/cm3, default 0.05: excludes air) */
     GDPM_PARAM_BATCH_MODE = 15,      /* 0 auto, 1 batches one after another, 2 all batches side
-                                        by side (one tally grid per batch, n_batches <= 128) */
+                                        by side (one tally grid per batch, n_batches <= 128,
+                                        phases of up to 8M primaries shared by all batches) */
     GDPM_PARAM_CONCURRENT_MAX_HIST = 16, /* auto: side by side when histories per batch <= this
-                                            (default 131072) ... */
-    GDPM_PARAM_CONCURRENT_MAX_MB = 17    /* ... and the per-batch grids fit in this (default 4096) */
+                                            (default 4e9, no limit) ... */
+    GDPM_PARAM_CONCURRENT_MAX_MB = 17    /* ... and the per-batch grids fit in this (default 16384) */
 };
 
 /* ------------------------------------------------------------------ inputs */

@@ -374,9 +374,13 @@ static int validate_run(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const 
 }
 
 // Primaries per phase: up to 2^20, and no more than one batch (or run) holds.
-static uint32_t chunk_of(gdpm_ctx* ctx, uint64_t n_per_run, int parts) {
+// Primaries per transport phase.  Batches side by side share their phases,
+// so those phases can be long (8M primaries): a phase ends with a tail in
+// which lanes run out of particles, and longer phases make the tail a
+// smaller share.  Batches one after another have one batch per phase.
+static uint32_t chunk_of(gdpm_ctx* ctx, uint64_t n_per_run, int parts, bool concurrent) {
     const uint64_t per = (n_per_run + parts - 1) / parts;
-    const uint32_t chunk = ctx->source_chunk ? ctx->source_chunk : (1u << 20);
+    const uint32_t chunk = ctx->source_chunk ? ctx->source_chunk : concurrent ? (1u << 23) : (1u << 20);
     return uint32_t(std::min<uint64_t>(chunk, per));
 }
 static uint32_t capacity_of(gdpm_ctx* ctx, uint32_t chunk) {
@@ -428,7 +432,7 @@ static int prepare_workspace(gdpm_ctx* ctx, Runner& r, size_t V, uint32_t cap, i
 static size_t bytes_needed(gdpm_ctx* ctx, const Runner& r, size_t V, uint64_t n_hist, int n_batches,
                            bool with_result) {
     const bool conc = side_by_side(ctx, V, n_hist, n_batches);
-    const uint32_t cap = capacity_of(ctx, chunk_of(ctx, conc ? n_hist : n_hist / n_batches + 1, 1));
+    const uint32_t cap = capacity_of(ctx, chunk_of(ctx, conc ? n_hist : n_hist / n_batches + 1, 1, conc));
     auto grow = [](const Buffer& b, size_t want) { return b.bytes >= want ? size_t(0) : want; };
     const Workspace& w = r.ws;
     size_t n = grow(w.s1, V * 8) + grow(w.s2, V * 8);
@@ -568,7 +572,7 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
     const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
     const bool conc = side_by_side(ctx, V, n_hist, n_batches);
     const uint32_t nb_small = uint32_t(n_hist / n_batches), nb_rem = uint32_t(n_hist % n_batches);
-    uint32_t chunk = conc ? chunk_of(ctx, n_hist, 1) : chunk_of(ctx, n_hist, n_batches);
+    uint32_t chunk = conc ? chunk_of(ctx, n_hist, 1, true) : chunk_of(ctx, n_hist, n_batches, false);
     const uint32_t cap = capacity_of(ctx, chunk);
     const int n_bins = int(src.weights.size());
     if ((rc = prepare_workspace(ctx, r, V, cap, n_batches, n_bins, conc))) return rc;

@@ -34,8 +34,14 @@ constexpr float kInf = FLT_MAX;
 constexpr float kEs = 21.2f;            // Rossi-Greisen scattering energy, MeV
 constexpr uint32_t kFull = 0xffffffffu;
 
-#ifndef GDPM_MIN_CTAS
-#define GDPM_MIN_CTAS 4
+// Resident 256-thread CTAs per SM the phase kernels are compiled for: the
+// photon kernel fits 64 registers (4 CTAs); the electron kernel's step has
+// more live state and runs best with up to 85 registers (3 CTAs).
+#ifndef GDPM_MIN_CTAS_PHOTON
+#define GDPM_MIN_CTAS_PHOTON 4
+#endif
+#ifndef GDPM_MIN_CTAS_ELECTRON
+#define GDPM_MIN_CTAS_ELECTRON 3
 #endif
 
 // ---------------------------------------------------------------- ledger/tally
@@ -43,11 +49,18 @@ struct Acc {
     double src, esc, disc;
 };
 
-// Event bits of one step (counted at the warp-uniform loop top).
-enum : uint32_t {
-    EV_REAL = 1u, EV_COMPTON = 2u, EV_PHOTO = 4u, EV_PAIR = 8u, EV_TERM = 16u, EV_LOCAL = 32u,
-    EV_STEP = 64u, EV_MOLLER = 128u, EV_BREMS = 256u, EV_ANNIHIL = 512u
+// Per-lane event counters: one byte per kind of event, four kinds to a
+// word, plus the flight (photon) or voxel-crossing (electron) count.  Each
+// kind happens at most once per lane and iteration, so folding the bytes
+// into the block's counters every kFlushEvery (< 256) iterations keeps them
+// from overflowing.
+struct Ev {
+    uint32_t a, b, c, n;
 };
+constexpr uint32_t EV_REAL = 1u, EV_COMPTON = 1u << 8, EV_PHOTO = 1u << 16, EV_PAIR = 1u << 24;  // a
+constexpr uint32_t EV_TERM = 1u, EV_LOCAL = 1u << 8, EV_STEP = 1u << 16, EV_MOLLER = 1u << 24;   // b
+constexpr uint32_t EV_BREMS = 1u, EV_ANNIHIL = 1u << 8;                                          // c
+constexpr uint32_t kFlushEvery = 128u;
 
 // Secondaries created by one step: n of them (0..2) at the particle's
 // current position; the second is a positron (pair) or, for photons, the
@@ -277,11 +290,11 @@ struct PhSmem {
 };
 
 __device__ void photon_step(const SimParams& P, const PhSmem& S, Part& p, bool& active, Acc& acc,
-                            uint32_t& evb, uint32_t& evn, Sec& sec) {
+                            Ev& ev, Sec& sec) {
     const DevTables& T = P.T;
     if (p.E < T.eabs_ph) {   // only a source photon below the cutoff reaches here
         tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), p.E);
-        evb |= EV_TERM;
+        ev.b += EV_TERM;
         active = false;
         return;
     }
@@ -305,11 +318,11 @@ __device__ void photon_step(const SimParams& P, const PhSmem& S, Part& p, bool& 
         if (!inside(P, p.x, p.y, p.z)) {
             acc.esc += p.E;
             hist_add(P, p.hist, 0, p.E);
-            evb |= EV_TERM;
+            ev.b += EV_TERM;
             active = false;
             return;
         }
-        ++evn;
+        ++ev.n;
         voxel_of(P, p);
         vox = vox_of(P, p.ix, p.iy, p.iz);
         const int m = __ldg(&P.mat[vox]);
@@ -318,7 +331,7 @@ __device__ void photon_step(const SimParams& P, const PhSmem& S, Part& p, bool& 
         mt = lerpf(S.tot[mi], S.tot[mi + 1], f);
         if (r.y * mm < mt * rho) break;             // real; otherwise a virtual (delta) collision
     }
-    evb |= EV_REAL;
+    ev.a += EV_REAL;
     hist_count(P, p.hist, 0);
     const float2 c0 = S.cum[mi], c1 = S.cum[mi + 1];
     const float rr = r.z * mt;
@@ -327,7 +340,7 @@ __device__ void photon_step(const SimParams& P, const PhSmem& S, Part& p, bool& 
     sec.dx = p.u; sec.dy = p.v; sec.dz = p.w;
     if (rr < lerpf(c0.x, c1.x, f)) {
         // Compton (Klein-Nishina); recoil electron along E u - E' u'
-        evb |= EV_COMPTON;
+        ev.a += EV_COMPTON;
         const float E = p.E;
         float eps, cost, rphi;
         sample_kn(p, P, E, eps, cost, rphi);
@@ -342,20 +355,22 @@ __device__ void photon_step(const SimParams& P, const PhSmem& S, Part& p, bool& 
         sec.pos2 = false;
         if (Ep < T.eabs_ph) {
             tally(P, p.flags, vox, Ep);
-            evb |= EV_LOCAL | EV_TERM;
+            ev.b += EV_LOCAL + EV_TERM;
             active = false;
         } else {
             p.E = Ep;
         }
     } else if (rr < lerpf(c0.y, c1.y, f)) {
         // photoelectric: photon absorbed, photoelectron along the photon
-        evb |= EV_PHOTO | EV_TERM;
+        ev.a += EV_PHOTO;
+        ev.b += EV_TERM;
         sec.E1 = p.E;
         sec.pos2 = false;
         active = false;
     } else {
         // pair: electron takes r.w of the kinetic energy, positron the rest
-        evb |= EV_PAIR | EV_TERM;
+        ev.a += EV_PAIR;
+        ev.b += EV_TERM;
         const float tav = p.E - 2.f * kMC2f;
         sec.E1 = r.w * tav;
         sec.E2 = tav - sec.E1;
@@ -448,12 +463,12 @@ __device__ void electron_escape(const SimParams& P, Part& p, float energy, Acc& 
 // One condensed-history step of an electron or positron (Sec. 2.1), or its
 // absorption.
 __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool& active, Acc& acc,
-                              uint32_t& evb, uint32_t& evn, Sec& sec) {
+                              Ev& ev, Sec& sec) {
     const DevTables& T = P.T;
     bool absorb = p.E < T.eabs_el;
     if (!absorb) {
         const float4 r = draw(p, P.key0, P.key1);
-        evb |= EV_STEP;
+        ev.b += EV_STEP;
         hist_count(P, p.hist, 1);
         const int m = __ldg(&P.mat[vox_of(P, p.ix, p.iy, p.iz)]);
         int i;
@@ -467,14 +482,14 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
         const float xms = lerpf(a0.y, a1.y, f);
         const float xcut = R0 - T.r_eabs[m];
         const float xhard = (T.flags & GDPM_FLAG_NO_HARD) ? kInf : -__logf(r.x) * T.inv_sigmax[m];
-        int ev;
+        int lim;   // what ends the step: 0 reach E_abs, 1 hard candidate, 2 MS step
         float xs;
-        if (xcut <= xms && xcut <= xhard) { ev = 0; xs = xcut; }
-        else if (xhard <= xms) { ev = 1; xs = xhard; }
-        else { ev = 2; xs = xms; }
+        if (xcut <= xms && xcut <= xhard) { lim = 0; xs = xcut; }
+        else if (xhard <= xms) { lim = 1; xs = xhard; }
+        else { lim = 2; xs = xms; }
         xs = fmaxf(xs, 0.f);
         float Tend;
-        if (ev == 0) {
+        if (lim == 0) {
             Tend = T.eabs_el;
         } else {
             const float rr = (R0 - xs - T.rinv_lo[m]) * T.rinv_idr[m];
@@ -503,22 +518,22 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
         const float dpm = xs > 0.f ? dT / xs : 0.f;
         float dep = 0.f;
         // random hinge: zeta*xs straight, deflect, (1-zeta)*xs straight
-        bool out = walk(P, p, r.y * xs, dpm, dep, false, evn);
+        bool out = walk(P, p, r.y * xs, dpm, dep, false, ev.n);
         if (!out) {
             rotate(p.u, p.v, p.w, mu, cp, sp);
-            out = walk(P, p, (1.f - r.y) * xs, dpm, dep, true, evn);
+            out = walk(P, p, (1.f - r.y) * xs, dpm, dep, true, ev.n);
         }
         if (out) {
             electron_escape(P, p, Tk - dep, acc);
-            evb |= EV_TERM;
+            ev.b += EV_TERM;
             active = false;
             return;
         }
         tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), dT - dep);
         p.E = Tend;
-        if (ev == 0) {
+        if (lim == 0) {
             absorb = true;
-        } else if (ev == 1) {
+        } else if (lim == 1) {
             // hard-event candidate: accept with Sigma_h(T)/Sigma_max (start material)
             const float4 v = draw(p, P.key0, P.key1);
             const float Tn = p.E, wcc = T.eabs_el, wcb = T.eabs_ph;
@@ -537,7 +552,7 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
                 sec.n = 1;
                 sec.pos2 = false;
                 if (v.y * sh < sm) {
-                    evb |= EV_MOLLER;
+                    ev.b += EV_MOLLER;
                     float eps, rphi;
                     sample_moller(p, P, Tn, wcc, eps, rphi);
                     float c, sn;
@@ -552,7 +567,7 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
                     rotate(p.u, p.v, p.w, cpr, -c, -sn);
                     p.E = Tp;
                 } else {
-                    evb |= EV_BREMS;
+                    ev.c += EV_BREMS;
                     const float k = wcb * exp2f(v.z * __log2f(Tn / wcb));
                     sec.photon = true;
                     sec.E1 = k;
@@ -567,7 +582,7 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
         // annihilates into two back-to-back 0.511 MeV photons (isotropic),
         // or its rest energy is discarded (Sec. 2.1, Sec. 4)
         tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), p.E);
-        evb |= EV_TERM;
+        ev.b += EV_TERM;
         active = false;
         if (p.flags & kPositron) {
             if (!P.S.annihilation) {
@@ -578,7 +593,7 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
                 const float sint = sqrtf(fmaxf(0.f, 1.f - cost * cost));
                 float cp, sp;
                 cossin_2pi(a.y, cp, sp);
-                evb |= EV_ANNIHIL;
+                ev.c += EV_ANNIHIL;
                 sec.n = 2;
                 sec.photon = true;
                 sec.pos2 = false;
@@ -590,28 +605,89 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
 }
 
 // ---------------------------------------------------------------- warp-uniform parts
-// Add this iteration's event counts of all 32 lanes (call with the whole warp).
+// Fold the lanes' event counters into the block's (call with the whole warp).
 template <int PT>
-__device__ __forceinline__ void flush_events(uint32_t evb, uint32_t evn, uint32_t* s_cnt) {
+__device__ __forceinline__ void flush_events(Ev& ev, uint32_t* s_cnt) {
     const bool lead = lane_id() == 0;
-    const uint32_t n = __reduce_add_sync(kFull, evn);
+    const uint32_t n = __reduce_add_sync(kFull, ev.n);
     if (lead && n) atomicAdd(&s_cnt[PT == 0 ? C_PH_FLIGHTS : C_CROSS], n);
-    if (!__any_sync(kFull, evb != 0u)) return;
+    const uint32_t w[3] = {ev.a, ev.b, ev.c};
     const int slots[10] = {C_PH_REAL, C_COMPTON, C_PHOTO, C_PAIR,
                            PT == 0 ? C_PH_TERMINATED : C_EL_TERMINATED, C_LOCAL_DEP,
                            C_EL_STEPS, C_MOLLER, C_BREMS, C_ANNIHIL};
 #pragma unroll
-    for (int b = 0; b < 10; ++b) {
-        const uint32_t c = __popc(__ballot_sync(kFull, (evb >> b) & 1u));
-        if (lead && c) atomicAdd(&s_cnt[slots[b]], c);
+    for (int k = 0; k < 10; ++k) {
+        const uint32_t c = __reduce_add_sync(kFull, (w[k >> 2] >> (8 * (k & 3))) & 0xFFu);
+        if (lead && c) atomicAdd(&s_cnt[slots[k]], c);
     }
+    ev = Ev{0u, 0u, 0u, 0u};
+}
+
+// Warp-uniform tallies of the loop top (identical in every lane), two
+// 16-bit counts to a word: (local deposits, electron pushes), (photon
+// pushes, primaries), (pops, primaries that miss the phantom).  At most 32
+// per count and iteration, folded with the event counters.
+struct WarpCnt {
+    uint32_t w0, w1, w2;
+};
+
+template <int PT>
+__device__ __forceinline__ void flush_warp_counts(WarpCnt& wc, uint32_t* s_cnt) {
+    if (lane_id() == 0) {
+        const uint32_t local = wc.w0 & 0xFFFFu, push_el = wc.w0 >> 16;
+        const uint32_t push_ph = wc.w1 & 0xFFFFu, primary = wc.w1 >> 16;
+        const uint32_t pop = wc.w2 & 0xFFFFu, missed = wc.w2 >> 16;
+        if (local) atomicAdd(&s_cnt[C_LOCAL_DEP], local);
+        if (push_el) {
+            atomicAdd(&s_cnt[C_PUSH_EL], push_el);
+            atomicAdd(&s_cnt[C_EL_CREATED], push_el);
+        }
+        if (push_ph) {
+            atomicAdd(&s_cnt[C_PUSH_PH], push_ph);
+            atomicAdd(&s_cnt[C_PH_CREATED], push_ph);
+        }
+        if (primary) {
+            atomicAdd(&s_cnt[C_PRIMARY], primary);
+            atomicAdd(&s_cnt[PT == 0 ? C_PH_CREATED : C_EL_CREATED], primary);
+        }
+        if (pop) atomicAdd(&s_cnt[PT == 0 ? C_POP_PH : C_POP_EL], pop);
+        if (missed) atomicAdd(&s_cnt[PT == 0 ? C_PH_TERMINATED : C_EL_TERMINATED], missed);
+    }
+    wc = WarpCnt{0u, 0u, 0u};
+}
+
+// Queue slots a warp holds: [base, base + left) reserved but not yet written.
+struct Slots {
+    uint32_t base, left;
+};
+
+// `c` consecutive slots for the warp's pushes to one queue: from the
+// reservation first, then a new reservation of max(missing, block) slots
+// (one atomic).  Returns the first slot of the new reservation (or of the
+// old one when it sufficed); a lane of rank r < old left writes slot
+// old.base + r, the others new + (r - old left).
+__device__ __forceinline__ uint32_t reserve(Slots& sl, uint32_t c, uint32_t* count, uint32_t block,
+                                            int leader) {
+    if (c <= sl.left) {
+        const uint32_t b = sl.base;
+        sl.base += c;
+        sl.left -= c;
+        return b;
+    }
+    const uint32_t miss = c - sl.left, want = max(miss, block);
+    uint32_t nb = 0;
+    if (int(lane_id()) == leader) nb = atomicAdd(count, want);
+    nb = __shfl_sync(kFull, nb, leader);
+    sl.base = nb + miss;
+    sl.left = want - miss;
+    return nb;
 }
 
 // Bank the secondaries the lanes' last steps created (call with the whole
 // warp): below-cutoff electrons and photons deposit on the spot, the rest
-// get queue slots (one atomic per warp and queue) and counter-derived ids.
+// get slots in the warp's reservations and counter-derived ids.
 __device__ __forceinline__ void bank_pending(const SimParams& P, const PhaseArgs& A, Part& p,
-                                             const Sec& sec, uint32_t* s_cnt) {
+                                             const Sec& sec, Slots (&sl)[2], WarpCnt& wc) {
     const uint32_t lane = lane_id();
     for (int k = 0; k < 2; ++k) {
         const bool want = k < sec.n;
@@ -621,40 +697,37 @@ __device__ __forceinline__ void bank_pending(const SimParams& P, const PhaseArgs
         const float sg = (k == 1 && sec.photon) ? -1.f : 1.f;
         const bool push = want && (pos || E >= (sec.photon ? P.T.eabs_ph : P.T.eabs_el));
         if (want && !push) tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), E);
-        const uint32_t nloc = __popc(__ballot_sync(kFull, want && !push));
-        if (lane == 0 && nloc) atomicAdd(&s_cnt[C_LOCAL_DEP], nloc);
+        wc.w0 += __popc(__ballot_sync(kFull, want && !push));
 #pragma unroll
         for (int q = 0; q < 2; ++q) {           // q = 0 electron queue, 1 photon queue
             const bool mine = push && (sec.photon == (q == 1));
             const uint32_t m = __ballot_sync(kFull, mine);
             if (!m) continue;
-            const int leader = __ffs(m) - 1;
-            uint32_t base = 0;
-            if (int(lane) == leader) base = atomicAdd(q ? A.out_ph_count : A.out_el_count, uint32_t(__popc(m)));
-            base = __shfl_sync(kFull, base, leader);
+            const uint32_t c = __popc(m);
+            const uint32_t left0 = sl[q].left, base0 = sl[q].base;
+            const uint32_t nb = reserve(sl[q], c, q ? A.out_ph_count : A.out_el_count, A.bank_block,
+                                        __ffs(m) - 1);
             if (mine) {
-                Part c;
-                c.x = p.x; c.y = p.y; c.z = p.z;
-                c.u = sg * sec.dx; c.v = sg * sec.dy; c.w = sg * sec.dz;
-                c.E = E;
-                c.ix = p.ix; c.iy = p.iy; c.iz = p.iz;
-                c.hist = p.hist;
+                Part ch;
+                ch.x = p.x; ch.y = p.y; ch.z = p.z;
+                ch.u = sg * sec.dx; ch.v = sg * sec.dy; ch.w = sg * sec.dz;
+                ch.E = E;
+                ch.ix = p.ix; ch.iy = p.iy; ch.iz = p.iz;
+                ch.hist = p.hist;
                 const uint64_t id = child_id(uint64_t(p.pidlo) | (uint64_t(p.pidhi) << 32), p.flags & 0xFFFFFFu);
-                c.pidlo = uint32_t(id);
-                c.pidhi = uint32_t(id >> 32);
-                c.ctr = 0;
-                c.flags = (p.flags & kBatchMask) | (pos ? kPositron : 0u);
+                ch.pidlo = uint32_t(id);
+                ch.pidhi = uint32_t(id >> 32);
+                ch.ctr = 0;
+                ch.flags = (p.flags & kBatchMask) | (pos ? kPositron : 0u);
                 ++p.flags;
-                const uint32_t slot = base + __popc(m & lanemask_lt());
+                const uint32_t r = __popc(m & lanemask_lt());
+                const uint32_t slot = c <= left0 ? base0 + r : (r < left0 ? base0 + r : nb + (r - left0));
                 const Queue& Q = q ? A.out_ph : A.out_el;
-                if (slot < Q.capacity) queue_store(Q, slot, c);
+                if (slot < Q.capacity) queue_store(Q, slot, ch);
                 else atomicOr(P.status, ST_QUEUE_OVERFLOW);
                 hist_count(P, p.hist, 3);
             }
-            if (lane == 0) {
-                atomicAdd(&s_cnt[q ? C_PUSH_PH : C_PUSH_EL], uint32_t(__popc(m)));
-                atomicAdd(&s_cnt[q ? C_PH_CREATED : C_EL_CREATED], uint32_t(__popc(m)));
-            }
+            if (q) wc.w1 += c; else wc.w0 += c << 16;
         }
     }
 }
@@ -673,8 +746,17 @@ __device__ __forceinline__ void copy_to_smem(void* dst, const void* src, size_t 
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
+// Indices of this phase's work a warp takes at a time (primaries first,
+// then queued particles): one atomic per block instead of one per refill.
+constexpr uint32_t kGrab = 32u;
+
+// One transport phase (Sec. 2.2.1 Step 3): a persistent loop per warp.
+// Loop top (whole warp): fold event counters now and then, bank the
+// secondaries of the last step, refill lanes whose particle ended.  Then
+// each lane takes one step of its own particle.
 template <int PT>
-__global__ void __launch_bounds__(256, GDPM_MIN_CTAS) k_phase(const SimParams P, const PhaseArgs A) {
+__global__ void __launch_bounds__(256, PT == 0 ? GDPM_MIN_CTAS_PHOTON : GDPM_MIN_CTAS_ELECTRON)
+k_phase(const SimParams P, const PhaseArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t n_in = A.in_count ? min(*A.in_count, A.in.capacity) : 0u;
     const uint32_t total = A.n_src + n_in;
@@ -713,49 +795,60 @@ __global__ void __launch_bounds__(256, GDPM_MIN_CTAS) k_phase(const SimParams P,
     Acc acc{0.0, 0.0, 0.0};
     Part p{};
     Sec sec{};
+    Ev ev{0u, 0u, 0u, 0u};
+    WarpCnt wc{0u, 0u, 0u};
+    Slots sl[2] = {{0u, 0u}, {0u, 0u}};
     bool active = false, exhausted = false;
-    uint32_t evb = 0u, evn = 0u;
+    // the warp's block of work indices [st_base, st_base + st_left); near
+    // the end of the phase (less than two per lane of the grid left) the
+    // warp takes exactly what it needs, so no warp sits on spare work
+    uint32_t st_base = 0u, st_left = 0u;
+    bool st_exact = false;
     const uint32_t lane = lane_id();
     for (uint32_t it = 0;; ++it) {
         // ---- whole warp: account and bank the last step, then refill
-        flush_events<PT>(evb, evn, s_cnt);
-        evb = 0u;
-        evn = 0u;
-        bank_pending(P, A, p, sec, s_cnt);
+        if ((it % kFlushEvery) == kFlushEvery - 1u) {
+            flush_events<PT>(ev, s_cnt);
+            flush_warp_counts<PT>(wc, s_cnt);
+        }
+        bank_pending(P, A, p, sec, sl, wc);
         sec.n = 0;
         const bool need = !active && !exhausted;
         const uint32_t nm = __ballot_sync(kFull, need);
         if (nm) {
-            const int leader = __ffs(nm) - 1;
-            uint32_t base = 0;
-            if (int(lane) == leader) base = atomicAdd(A.head, uint32_t(__popc(nm)));
-            base = __shfl_sync(kFull, base, leader);
+            const uint32_t k = __popc(nm);
+            const uint32_t left0 = st_left, base0 = st_base;
+            uint32_t nb = 0u;
+            if (k > st_left) {
+                const uint32_t miss = k - st_left, want = st_exact ? miss : max(miss, kGrab);
+                if (lane == 0) nb = atomicAdd(A.head, want);
+                nb = __shfl_sync(kFull, nb, 0);
+                st_base = nb + miss;
+                st_left = want - miss;
+                if (nb >= total || total - nb < 2u * gridDim.x * blockDim.x) st_exact = true;
+            } else {
+                st_base += k;
+                st_left -= k;
+            }
             bool from_src = false, from_queue = false, missed = false;
             if (need) {
-                const uint32_t idx = base + __popc(nm & lanemask_lt());
+                const uint32_t r = __popc(nm & lanemask_lt());
+                const uint32_t idx = r < left0 ? base0 + r : nb + (r - left0);
                 if (idx < A.n_src) {
                     from_src = true;
                     active = make_primary(P, A, idx, p, acc);
                     missed = !active;
                 } else if (idx < total) {
                     queue_load(A.in, idx - A.n_src, p);
-                    from_queue = true;
-                    active = true;
+                    // a slot reserved but never written holds E < 0
+                    from_queue = p.E >= 0.f;
+                    active = from_queue;
                 } else {
                     exhausted = true;
                 }
             }
-            const uint32_t ns = __popc(__ballot_sync(kFull, from_src));
-            const uint32_t nq = __popc(__ballot_sync(kFull, from_queue));
-            const uint32_t nmiss = __popc(__ballot_sync(kFull, missed));
-            if (lane == 0) {
-                if (ns) {
-                    atomicAdd(&s_cnt[C_PRIMARY], ns);
-                    atomicAdd(&s_cnt[PT == 0 ? C_PH_CREATED : C_EL_CREATED], ns);
-                }
-                if (nq) atomicAdd(&s_cnt[PT == 0 ? C_POP_PH : C_POP_EL], nq);
-                if (nmiss) atomicAdd(&s_cnt[PT == 0 ? C_PH_TERMINATED : C_EL_TERMINATED], nmiss);
-            }
+            wc.w1 += __popc(__ballot_sync(kFull, from_src)) << 16;
+            wc.w2 += __popc(__ballot_sync(kFull, from_queue)) + (__popc(__ballot_sync(kFull, missed)) << 16);
         }
         if (__all_sync(kFull, exhausted)) break;
         if (it >= P.max_iters) {
@@ -764,9 +857,18 @@ __global__ void __launch_bounds__(256, GDPM_MIN_CTAS) k_phase(const SimParams P,
         }
         // ---- each lane on its own: one step
         if (active) {
-            if (PT == 0) photon_step(P, ps, p, active, acc, evb, evn, sec);
-            else electron_step(P, es, p, active, acc, evb, evn, sec);
+            if (PT == 0) photon_step(P, ps, p, active, acc, ev, sec);
+            else electron_step(P, es, p, active, acc, ev, sec);
         }
+    }
+    flush_events<PT>(ev, s_cnt);
+    flush_warp_counts<PT>(wc, s_cnt);
+    // reserved queue slots never written: mark them empty for the consumer
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const Queue& Q = q ? A.out_ph : A.out_el;
+        const uint32_t slot = sl[q].base + lane;
+        if (lane < sl[q].left && slot < Q.capacity) Q.E[slot] = -1.f;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -928,10 +1030,17 @@ int launch_phase(gdpm_ctx* ctx, cudaStream_t st, int particle, const SimParams& 
         grid = need < grid ? need : grid;
     }
     if (grid == 0) grid = 1;
+    // queue slots a warp reserves at a time: up to 32, while all warps'
+    // spare slots stay below an eighth of the queue; exact below 8
+    PhaseArgs B = A;
+    const uint64_t warps = uint64_t(grid) * uint64_t(ctx->block_threads / 32);
+    const uint64_t cap = std::min(A.out_el.capacity, A.out_ph.capacity);
+    const uint64_t bb = std::min<uint64_t>(32u, cap / (8u * warps));
+    B.bank_block = bb >= 8u ? uint32_t(bb) : 0u;
     if (particle == GDPM_PHOTON)
-        k_phase<0><<<grid, ctx->block_threads, smem, st>>>(P, A);
+        k_phase<0><<<grid, ctx->block_threads, smem, st>>>(P, B);
     else
-        k_phase<1><<<grid, ctx->block_threads, smem, st>>>(P, A);
+        k_phase<1><<<grid, ctx->block_threads, smem, st>>>(P, B);
     GDPM_CUDA_TRY(cudaGetLastError());
     return GDPM_OK;
 }
