@@ -517,11 +517,16 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
         cossin_2pi(r.w, cp, sp);
         const float dpm = xs > 0.f ? dT / xs : 0.f;
         float dep = 0.f;
-        // random hinge: zeta*xs straight, deflect, (1-zeta)*xs straight
-        bool out = walk(P, p, r.y * xs, dpm, dep, false, ev.n);
-        if (!out) {
+        // random hinge: zeta*xs straight, deflect, (1-zeta)*xs straight.  One
+        // walk call site in a two-pass loop keeps a single copy of the voxel
+        // walk in the kernel (two inlined copies overflow the instruction
+        // cache and stall the warps on instruction fetch).
+        bool out = false;
+#pragma unroll 1
+        for (int leg = 0; leg < 2; ++leg) {
+            out = walk(P, p, leg ? (1.f - r.y) * xs : r.y * xs, dpm, dep, leg == 1, ev.n);
+            if (out || leg == 1) break;
             rotate(p.u, p.v, p.w, mu, cp, sp);
-            out = walk(P, p, (1.f - r.y) * xs, dpm, dep, true, ev.n);
         }
         if (out) {
             electron_escape(P, p, Tk - dep, acc);
