@@ -256,14 +256,35 @@ def serve_bench(args):
     print(json.dumps(line))
 
 
+def rank_env():
+    """(world size, rank, local rank) as torchrun sets them (1, 0, 0 alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value, world, device=None):
+    """The largest value over all ranks (the timed region of the slowest rank)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, n_hist, t_max_ms):
+    """Histories per second of the whole job: every rank runs n_hist histories
+    per step (replicas with disjoint random streams), timed by the slowest."""
+    return world * steps * n_hist / (t_max_ms / 1e3)
+
+
 def main():
     args = parse()
     if args.mode == "serve":
         serve_bench(args)
         return
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     n_hist = int(args.histories)
     make = WORKLOADS[args.workload]
     config = {"workload": args.workload, "histories_per_step": n_hist, "batches": args.batches,
@@ -341,13 +362,8 @@ def main():
         last = st
     barrier()
     clk = clocks.stop()
-    t_max = total_ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps * n_hist / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, world, dev)
+    value = whole_job_rate(world, args.steps, n_hist, t_max)
 
     # end to end through the C ABI with host buffers: tables, phantom upload
     # (pinned host), source, simulate into host outputs
@@ -370,7 +386,7 @@ def main():
         G.gdpm_phantom_destroy(ph)
         G.gdpm_tables_destroy(tb)
         e2e_s += time.perf_counter() - t0
-    e2e_value = world * args.e2e_steps * n_hist / e2e_s
+    e2e_value = world * args.e2e_steps * n_hist / e2e_s if args.e2e_steps > 0 else None
 
     # roofline of the dominant kernel kind, from its live event time
     kinds = ["photon phase", "electron phase", "batch fold"]
