@@ -214,6 +214,26 @@ int gdpm_source_set(gdpm_ctx *ctx, const gdpm_source_desc *src);
 int gdpm_simulate(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
                   int n_batches, double *dose_out, double *sigma_out, gdpm_stats *stats_out);
 
+/* Beamlet dose matrix: every row k of the current source's fluence map
+ * (GDPM_GEO_BEAMLETS; its weight is ignored) is a calculation of its own --
+ * the beamlet's rectangle as the field of a point source, n_histories[k]
+ * primaries in n_batches batches (Sec. 2.2.1, 2.3.1) -- and all of them run
+ * through one sequence of transport phases, each with its own tally grids.
+ * Beamlet k's histories have ids sum_{j<k} n_histories[j] + 0, 1, ..., so
+ * its result equals gdpm_simulate of that beamlet alone with those history
+ * ids.  dose_out (and sigma_out, which may be NULL) hold K x nx*ny*nz
+ * doubles, beamlet-major, in MeV/g per history of that beamlet; host or
+ * device memory.  n_batches >= 2 when sigma_out is given, else >= 1.  The
+ * tally grids take K * n_batches * nx*ny*nz * 8 bytes of device memory.
+ * stats_out sums the counts and ledger over all beamlets (no sigma/Dmax).
+ * Errors: GDPM_E_ARG (source not a fluence map, K * n_batches > 32767, a
+ * beamlet with fewer histories than batches, sum >= 2^32, energies outside
+ * the tables), GDPM_E_STATE (no source), GDPM_E_NOMEM, GDPM_E_QUEUE_OVERFLOW,
+ * GDPM_E_TIMEOUT, GDPM_E_CUDA. */
+int gdpm_simulate_beamlets(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb,
+                           const uint64_t *n_histories, int n_batches, double *dose_out,
+                           double *sigma_out, gdpm_stats *stats_out);
+
 /* Optional per-history records for the next gdpm_simulate on this context:
  * rec (device, n*4 int32: real photon interactions, electron steps, hard
  * electron events, banked secondaries) and recd (device, n*2 doubles:

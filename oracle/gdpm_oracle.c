@@ -97,6 +97,8 @@ typedef struct {
     int flags;
     int beamlet_sampler;           /* ORC_SAMPLE_* */
     int metro_chains;              /* Metropolis chains C (Algorithm A1) */
+    unsigned long long first_hist; /* id of the problem's first history (the
+                                      histories are first_hist .. first_hist+n_hist-1) */
 } orc_problem;
 
 typedef struct {
@@ -1130,16 +1132,18 @@ int orc_run(const orc_problem *P, double *dose, double *sigma, orc_result *res,
     if (P->beamlet_sampler < ORC_SAMPLE_CDF || P->beamlet_sampler > ORC_SAMPLE_METROPOLIS ||
         (P->beamlet_sampler == ORC_SAMPLE_METROPOLIS && P->metro_chains < 1))
         return -1;
+    if (P->first_hist + P->n_hist > (1ull << 32)) return -1;   /* history ids are 32-bit */
     orc_sim S;
     sim_init(&S, P, res);
     S.hrec = hist_rec; S.hrecd = hist_recd;
+    S.hrec_base = P->first_hist;
     if (hist_rec) memset(hist_rec, 0, sizeof(int) * HR_NI * P->n_hist);
     if (hist_recd) memset(hist_recd, 0, sizeof(double) * HD_ND * P->n_hist);
     size_t V = (size_t)P->nx * P->ny * P->nz;
     double *s1 = calloc(V, sizeof(double)), *s2 = calloc(V, sizeof(double));
     S.edep = calloc(V, sizeof(double));
     uint64_t cnt[ORC_MAX_BINS];
-    uint64_t first = 0;
+    uint64_t first = P->first_hist;
     int NB = P->n_batches;
     for (int b = 0; b < NB; b++) {
         uint64_t nb = P->n_hist / NB + ((uint64_t)b < P->n_hist % NB ? 1 : 0);

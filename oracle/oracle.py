@@ -54,7 +54,8 @@ class OrcProblem(C.Structure):
                 ("n_beamlets", C.c_int), ("beamlets", C.POINTER(C.c_double)),
                 ("n_hist", C.c_ulonglong), ("n_batches", C.c_int), ("seed", C.c_ulonglong),
                 ("request_id", C.c_uint), ("flags", C.c_int),
-                ("beamlet_sampler", C.c_int), ("metro_chains", C.c_int)]
+                ("beamlet_sampler", C.c_int), ("metro_chains", C.c_int),
+                ("first_hist", C.c_ulonglong)]
 
 SAMPLERS = {"cdf": 0, "alias": 1, "metropolis": 2}
 
@@ -166,6 +167,7 @@ class _Prepared:
         p.beamlet_sampler = SAMPLERS[src.sampler]
         p.metro_chains = src.chains
         p.n_hist, p.n_batches = prob.n_histories, prob.n_batches
+        p.first_hist = prob.first_history
         p.seed, p.request_id = prob.seed, prob.request_id
         flags = prob.flags
         if not src.annihilation:

@@ -220,7 +220,7 @@ static int source_copy(const gdpm_source_desc* s, gdpm_source_state& st) {
 // entry (q < 1) takes its cut-off q and the last "large" entry as alias,
 // which gives up 1 - q of its own mass).  Pure additions and single
 // products, so the table is the same on every host.
-void beamlet_tables_host(const std::vector<double>& rows17, BeamletHost& out) {
+void beamlet_tables_host(const std::vector<double>& rows17, BeamletHost& out, bool all_rows) {
     const int nb = int(rows17.size() / 17);
     out = BeamletHost{};
     double tot = 0;
@@ -229,14 +229,20 @@ void beamlet_tables_host(const std::vector<double>& rows17, BeamletHost& out) {
     for (int b = 0; b < nb; ++b) {
         const double w = rows17[size_t(b) * 17 + 16];
         acc += w;
-        if (!(w > 0)) continue;
+        if (!(w > 0) && !all_rows) continue;
         for (int k = 0; k < 16; ++k) out.rows.push_back(float(rows17[size_t(b) * 17 + k]));
         out.row.push_back(b);
         out.f.push_back(w);
-        out.cdf.push_back(acc / tot);
+        out.cdf.push_back(tot > 0 ? acc / tot : 0.0);
     }
     const int n = int(out.f.size());
     if (n == 0) return;
+    if (all_rows) {            // rows are sub-problems, not sampled: neutral tables
+        out.cut.assign(n, 1.0);
+        out.alias.resize(n);
+        for (int k = 0; k < n; ++k) out.alias[k] = k;
+        return;
+    }
     out.cdf[n - 1] = 1.0;
     double sum = 0;
     for (double w : out.f) sum += w;
@@ -262,7 +268,7 @@ void beamlet_tables_host(const std::vector<double>& rows17, BeamletHost& out) {
 }
 
 
-static int source_upload(Runner& r, const gdpm_source_state& s, DevSource& d) {
+static int source_upload(Runner& r, const gdpm_source_state& s, DevSource& d, bool all_rows = false) {
     const gdpm_source_desc& g = s.desc;
     d.particle = g.particle;
     d.geometry = g.geometry;
@@ -294,7 +300,7 @@ static int source_upload(Runner& r, const gdpm_source_state& s, DevSource& d) {
     d.al_cut = nullptr;
     d.al_alias = nullptr;
     BeamletHost bh;
-    if (g.geometry == GDPM_GEO_BEAMLETS) beamlet_tables_host(s.beamlets, bh);
+    if (g.geometry == GDPM_GEO_BEAMLETS) beamlet_tables_host(s.beamlets, bh, all_rows);
     if (!bh.f.empty()) {
         const size_t nbl = bh.f.size();
         Workspace& w = r.ws;
@@ -451,7 +457,8 @@ static size_t bytes_needed(gdpm_ctx* ctx, const Runner& r, size_t V, uint64_t n_
 // ctl row k: [0] pop counter of phase k, [1] count of P[k], [2] count of E[k].
 static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_source_state& src,
                       uint64_t first, uint64_t n, uint32_t nb_small, uint32_t nb_rem, uint32_t chunk,
-                      int64_t& phases, int64_t& aux) {
+                      int64_t& phases, int64_t& aux, uint32_t n_sub = 0, uint32_t sub_batches = 0,
+                      const uint32_t* sub_first = nullptr) {
     Workspace& ws = r.ws;
     cudaStream_t s = r.stream;
     uint32_t* ctl = static_cast<uint32_t*>(ws.ctl.p);
@@ -469,6 +476,9 @@ static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_s
         PhaseArgs A{};
         A.nb_small = nb_small;
         A.nb_rem = nb_rem;
+        A.n_sub = n_sub;
+        A.sub_batches = sub_batches;
+        A.sub_first = sub_first;
         A.bin_prefix = static_cast<const uint32_t*>(ws.prefix.p);
         if (ph == photon_src && left > 0) {
             A.n_src = uint32_t(std::min<uint64_t>(left, chunk));
@@ -1077,6 +1087,142 @@ int gdpm_simulate(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_h
     if (ctx->hrec && ctx->hrec_n < n_histories) return GDPM_E_ARG;
     return simulate_impl(ctx, ctx->run, ph, tb, ctx->src, ctx->request_id, n_histories, n_batches,
                          dose_out, sigma_out, stats_out, ctx->hrec, ctx->hrecd);
+}
+
+int gdpm_simulate_beamlets(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb,
+                           const uint64_t* n_histories, int n_batches, double* dose_out,
+                           double* sigma_out, gdpm_stats* st) {
+    if (!ctx || !n_histories || !dose_out) return GDPM_E_ARG;
+    const gdpm_source_state& src = ctx->src;
+    if (!src.set) return GDPM_E_STATE;
+    if (src.desc.geometry != GDPM_GEO_BEAMLETS) return GDPM_E_ARG;
+    const uint32_t K = uint32_t(src.beamlets.size() / 17);
+    const int nb = n_batches;
+    if (nb < 1 || (nb < 2 && sigma_out) || size_t(K) * nb > size_t(kMaxSlots)) return GDPM_E_ARG;
+    uint64_t total = 0;
+    std::vector<uint32_t> first(K + 1, 0u);
+    for (uint32_t k = 0; k < K; ++k) {
+        if (n_histories[k] < uint64_t(nb)) return GDPM_E_ARG;
+        first[k] = uint32_t(total);
+        total += n_histories[k];
+        if (total >= (1ull << 32)) return GDPM_E_ARG;
+    }
+    first[K] = uint32_t(total);
+    // the checks of a single calculation (tables cover the spectrum, ...)
+    int rc = validate_run(ctx, ph, tb, src, std::max<uint64_t>(total, 2), 2);
+    if (rc) return rc;
+    GDPM_CUDA_TRY(cudaSetDevice(ctx->device));
+    Runner& r = ctx->run;
+    cudaStream_t s = r.stream;
+    const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
+    const uint32_t slots = K * uint32_t(nb);
+    const uint32_t chunk = chunk_of(ctx, total, 1, true);
+    const uint32_t cap = capacity_of(ctx, chunk);
+    const int n_bins = int(src.weights.size());
+    if ((rc = prepare_workspace(ctx, r, V, cap, int(slots), n_bins, true))) return rc;
+    Workspace& ws = r.ws;
+    SimParams P = base_params(ctx, ph, tb, ctx->request_id);
+    if ((rc = get_majorant(ctx, s, ph, tb, &P.maj))) return rc;
+    // spectrum allotment of every (sub-problem, batch) slot; batch sizes
+    std::vector<uint32_t> prefix(size_t(slots) * (n_bins + 1));
+    std::vector<double> inv(2 * size_t(K));
+    std::vector<uint32_t> nbig(K);
+    for (uint32_t k = 0; k < K; ++k) {
+        const uint64_t nk = n_histories[k];
+        for (int b = 0; b < nb; ++b) {
+            const uint64_t n = nk / nb + (uint64_t(b) < nk % nb ? 1 : 0);
+            allot_prefix(src.weights, n, &prefix[(size_t(k) * nb + b) * (n_bins + 1)]);
+        }
+        inv[2 * k] = 1.0 / double(nk / nb + 1);
+        inv[2 * k + 1] = 1.0 / double(nk / nb);
+        nbig[k] = uint32_t(nk % nb);
+    }
+    if ((rc = ensure(ws.sub_first, first.size() * 4)) || (rc = ensure(ws.sub_inv, inv.size() * 8)) ||
+        (rc = ensure(ws.sub_nbig, nbig.size() * 4)))
+        return rc;
+    GDPM_CUDA_TRY(cudaMemcpyAsync(ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, s));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(ws.sub_first.p, first.data(), first.size() * 4, cudaMemcpyHostToDevice, s));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(ws.sub_inv.p, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, s));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(ws.sub_nbig.p, nbig.data(), nbig.size() * 4, cudaMemcpyHostToDevice, s));
+    if ((rc = source_upload(r, src, P.S, true))) return rc;    // syncs: host vectors may go
+    P.counters = static_cast<unsigned long long*>(ws.counters.p);
+    P.ledger = static_cast<double*>(ws.ledger.p);
+    P.status = static_cast<uint32_t*>(ws.status.p);
+    P.batch_stride = V;
+    P.edep = static_cast<double*>(ws.edep.p);
+    P.edep_hi = static_cast<float*>(ws.edep.p);
+    P.edep_lo = static_cast<float*>(ws.edep.p) + V * size_t(slots);
+    if (ctx->hrec) {
+        if (ctx->hrec_n < total) return GDPM_E_ARG;
+        P.hrec = ctx->hrec;
+        P.hrecd = ctx->hrecd;
+        GDPM_CUDA_TRY(cudaMemsetAsync(ctx->hrec, 0, total * 16, s));
+        GDPM_CUDA_TRY(cudaMemsetAsync(ctx->hrecd, 0, total * 16, s));
+    }
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep.p, 0, V * size_t(slots) * 8, s));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.counters.p, 0, C_NCOUNT * 8, s));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.ledger.p, 0, L_NLEDGER * 8, s));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, 16, s));
+    r.prof_kind.clear();
+    GDPM_CUDA_TRY(cudaEventRecord(r.ev0, s));
+    int64_t phases = 0, aux = 0;
+    int run_rc = run_phases(ctx, r, P, src, 0, total, 0, 0, chunk, phases, aux, K, uint32_t(nb),
+                            static_cast<const uint32_t*>(ws.sub_first.p));
+    GDPM_CUDA_TRY(cudaEventRecord(r.ev1, s));
+    if (run_rc != GDPM_OK) {
+        cudaStreamSynchronize(s);
+        r.prof_kind.clear();
+        return run_rc;
+    }
+    // per sub-problem dose (and sigma): straight into device outputs, or in
+    // groups of sub-problems through a staging buffer for host outputs
+    const bool dev_out = is_device_ptr(dose_out) && (!sigma_out || is_device_ptr(sigma_out));
+    const double* sinv = static_cast<const double*>(ws.sub_inv.p);
+    const uint32_t* snb = static_cast<const uint32_t*>(ws.sub_nbig.p);
+    if (dev_out) {
+        for (uint32_t k0 = 0; k0 < K; k0 += 65535u) {
+            const uint32_t nk = std::min(K - k0, 65535u);
+            if ((rc = launch_fold_sub(ctx, s, P, V, k0, nk, nb, sinv, snb, dose_out + size_t(k0) * V,
+                                      sigma_out ? sigma_out + size_t(k0) * V : nullptr)))
+                return rc;
+            ++aux;
+        }
+    } else {
+        const uint32_t group = uint32_t(std::max<size_t>(1, std::min<size_t>(K, (size_t(256) << 20) / (V * 16))));
+        if ((rc = ensure(ws.stage, size_t(group) * V * 16))) return rc;
+        double* sd = static_cast<double*>(ws.stage.p);
+        double* ss = sd + size_t(group) * V;
+        for (uint32_t k0 = 0; k0 < K; k0 += group) {
+            const uint32_t nk = std::min(K - k0, group);
+            if ((rc = launch_fold_sub(ctx, s, P, V, k0, nk, nb, sinv, snb, sd, sigma_out ? ss : nullptr)))
+                return rc;
+            ++aux;
+            GDPM_CUDA_TRY(cudaMemcpyAsync(dose_out + size_t(k0) * V, sd, size_t(nk) * V * 8, cudaMemcpyDefault, s));
+            if (sigma_out)
+                GDPM_CUDA_TRY(cudaMemcpyAsync(sigma_out + size_t(k0) * V, ss, size_t(nk) * V * 8, cudaMemcpyDefault, s));
+        }
+    }
+    unsigned char* h = static_cast<unsigned char*>(ws.pinned_host.p);
+    unsigned long long* hc = reinterpret_cast<unsigned long long*>(h + 64);
+    double* hl = reinterpret_cast<double*>(h + 64 + C_NCOUNT * 8);
+    uint32_t* hs = reinterpret_cast<uint32_t*>(h + 64 + C_NCOUNT * 8 + L_NLEDGER * 8);
+    GDPM_CUDA_TRY(cudaMemcpyAsync(hc, ws.counters.p, C_NCOUNT * 8, cudaMemcpyDeviceToHost, s));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(hl, ws.ledger.p, L_NLEDGER * 8, cudaMemcpyDeviceToHost, s));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(hs, ws.status.p, 4, cudaMemcpyDeviceToHost, s));
+    GDPM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        fill_stats(hc, hl, st);
+        st->phases = phases;
+        st->launches = phases + aux;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r.ev0, r.ev1);
+        st->transport_ms = ms;
+    }
+    prof_collect(r, st);
+    if (*hs & ST_QUEUE_OVERFLOW) return GDPM_E_QUEUE_OVERFLOW;
+    if (*hs & ST_ITER_CAP) return GDPM_E_TIMEOUT;
+    return GDPM_OK;
 }
 
 int gdpm_debug_philox(gdpm_ctx* ctx, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,

@@ -73,17 +73,21 @@ __host__ __device__ __forceinline__ uint64_t child_id(uint64_t parent, uint32_t 
 }
 
 // ---------------------------------------------------------------- particle state
-// Register copy of one particle.  flags: bits 0..23 = secondaries banked so
-// far (the child index), bits 24..30 = batch of its history (when batches
-// run side by side), bit 31 = positron.
+// Register copy of one particle (flags as above).
 struct Part {
     float x, y, z, u, v, w, E;
     int ix, iy, iz;
     uint32_t hist, pidlo, pidhi, ctr, flags;
 };
 constexpr uint32_t kPositron = 0x80000000u;
-constexpr uint32_t kBatchShift = 24, kBatchMask = 0x7F000000u;
+// flags: bits 0..15 count the secondaries a particle has banked (the child
+// index of the next one), bits 16..30 its tally slot (the batch of its
+// history when batches run side by side; beamlet x batch in a dose-matrix
+// run), bit 31 marks a positron.
+constexpr uint32_t kChildMask = 0xFFFFu;
+constexpr uint32_t kBatchShift = 16, kBatchMask = 0x7FFF0000u;
 constexpr int kMaxConcurrentBatches = 128;
+constexpr int kMaxSlots = 32767;
 
 // One Philox block for the transport kernels.  Out of line (it has no
 // warp-synchronous operations), so its ten unrolled rounds exist once in

@@ -156,6 +156,53 @@ __global__ void __launch_bounds__(256) k_fold_batches(SimParams P, size_t V, int
     if (threadIdx.x == 0 && t != 0.0) atomicAdd(&P.ledger[L_DEPOSITED], t);
 }
 
+// Dose matrix: sub-problem k (row k of the fluence map; blockIdx.y) tallied
+// into slots k*nb .. k*nb+nb-1.  Writes its mean dose and standard error per
+// voxel (MeV/g per history of that sub-problem) to dose[(k-k0)*V + v] and
+// sigma[...]; with one batch only the dose.  inv_n[2k], inv_n[2k+1] are
+// 1/(histories of a long batch) and 1/(histories of a short batch) of
+// sub-problem k, whose first nbig[k] batches are the long ones.
+__global__ void __launch_bounds__(256) k_fold_sub(SimParams P, size_t V, uint32_t k0, int nb,
+                                                  const double* __restrict__ inv_n,
+                                                  const uint32_t* __restrict__ nbig, double dvol,
+                                                  double* __restrict__ dose, double* __restrict__ sigma) {
+    __shared__ double s_red[32];
+    const uint32_t k = k0 + blockIdx.y;
+    const double ib = inv_n[2 * k], is = inv_n[2 * k + 1];
+    const uint32_t n_big = nbig[k];
+    double dep = 0.0;
+    for (size_t v = blockIdx.x * size_t(blockDim.x) + threadIdx.x; v < V;
+         v += size_t(gridDim.x) * blockDim.x) {
+        double a1 = 0.0, a2 = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const size_t i = (size_t(k) * nb + b) * V + v;
+            const double e = P.tally_mode == 0 ? P.edep[i] : double(P.edep_hi[i]) + double(P.edep_lo[i]);
+            dep += e;
+            const double x = e * (uint32_t(b) < n_big ? ib : is);
+            a1 += x;
+            a2 = fma(x, x, a2);
+        }
+        const double mass = double(P.rho[v]) * dvol;
+        double im = double(1.0f / float(mass));
+        im = im * fma(-mass, im, 2.0);                       // Newton step for 1/mass
+        const size_t o = size_t(blockIdx.y) * V + v;
+        const double mean = a1 / nb;
+        dose[o] = mean * im;
+        if (sigma && nb > 1) {
+            const double var = fmax(0.0, (a2 - nb * mean * mean) / (double(nb) * (nb - 1)));
+            double sd = 0.0;
+            if (var > 0.0) {
+                double y = double(rsqrtf(float(var)));
+                y = y * fma(-0.5 * var * y, y, 1.5);         // Newton step for 1/sqrt(var)
+                sd = var * y;
+            }
+            sigma[o] = sd * im;
+        }
+    }
+    const double t = block_sum(dep, s_red);
+    if (threadIdx.x == 0 && t != 0.0) atomicAdd(&P.ledger[L_DEPOSITED], t);
+}
+
 // Mean and standard error per voxel in MeV/g per history; Dmax.  FP64
 // division and square root are slow on this part, so 1/mass and sqrt(var)
 // start from FP32 estimates and take one FP64 Newton step each (relative
@@ -269,6 +316,16 @@ int launch_fold_batches(gdpm_ctx* ctx, cudaStream_t st, const SimParams& P, size
                         uint32_t nb_small, uint32_t nb_rem, double* s1, double* s2) {
     k_fold_batches<<<ctx->sm_count * 8, 256, 0, st>>>(P, V, n_batches, 1.0 / double(nb_small + 1),
                                                         1.0 / double(nb_small), int(nb_rem), s1, s2);
+    GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+int launch_fold_sub(gdpm_ctx* ctx, cudaStream_t st, const SimParams& P, size_t V, uint32_t k0,
+                    uint32_t nk, int nb, const double* inv_n, const uint32_t* nbig, double* dose,
+                    double* sigma) {
+    const double dvol = double(P.dx) * P.dy * P.dz;
+    const uint32_t gx = uint32_t(std::min<size_t>((V + 255) / 256, size_t(ctx->sm_count) * 4));
+    k_fold_sub<<<dim3(gx, nk), 256, 0, st>>>(P, V, k0, nb, inv_n, nbig, dvol, dose, sigma);
     GDPM_CUDA_TRY(cudaGetLastError());
     return GDPM_OK;
 }

@@ -225,22 +225,39 @@ __device__ __forceinline__ int pick_beamlet(const DevSource& S, const PhaseArgs&
 __device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t idx, Part& p,
                              Acc& acc) {
     const DevSource& S = P.S;
+    const uint32_t h = A.src_first + idx;
+    // a dose-matrix run: sub-problem k holds histories [sub_first[k],
+    // sub_first[k+1]); its batches are slots k*nb .. k*nb+nb-1
+    uint32_t k = 0u, h0 = 0u, nb_small = A.nb_small, nb_rem = A.nb_rem;
+    if (A.n_sub) {
+        uint32_t lo = 0u, hi = A.n_sub;
+        while (hi - lo > 1u) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (A.sub_first[mid] <= h) lo = mid; else hi = mid;
+        }
+        k = lo;
+        h0 = A.sub_first[k];
+        const uint32_t nk = A.sub_first[k + 1] - h0;
+        nb_small = nk / A.sub_batches;
+        nb_rem = nk % A.sub_batches;
+    }
     // batch b of history h and h's index within it (batches are contiguous;
     // the first nb_rem hold nb_small + 1 histories)
-    const uint32_t h = A.src_first + idx;
-    const uint32_t big = A.nb_small + 1u, split = A.nb_rem * big;
+    const uint32_t hl = h - h0;
+    const uint32_t big = nb_small + 1u, split = nb_rem * big;
     uint32_t b, local;
-    if (h < split) {
-        b = h / big;
-        local = h - b * big;
+    if (hl < split) {
+        b = hl / big;
+        local = hl - b * big;
     } else {
-        b = A.nb_rem + (h - split) / A.nb_small;
-        local = (h - split) - (b - A.nb_rem) * A.nb_small;
+        b = nb_rem + (hl - split) / nb_small;
+        local = (hl - split) - (b - nb_rem) * nb_small;
     }
-    const uint32_t* prefix = A.bin_prefix + size_t(b) * (S.n_bins + 1);
+    const uint32_t slot = A.n_sub ? k * A.sub_batches + b : b;
+    const uint32_t* prefix = A.bin_prefix + size_t(slot) * (S.n_bins + 1);
     p.hist = h;
     p.pidlo = 1u; p.pidhi = 0u; p.ctr = 0u;
-    p.flags = (b << kBatchShift) & kBatchMask;
+    p.flags = (slot << kBatchShift) & kBatchMask;
     const float4 r = draw(p, P.key0, P.key1);
     int lo = 0, hi = S.n_bins;
     while (hi - lo > 1) {
@@ -258,8 +275,9 @@ __device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t id
             src = S.origin; cen = S.center; au = S.axis_u; av = S.axis_v;
             a0 = -S.half_u; a1 = S.half_u; b0 = -S.half_v; b1 = S.half_v;
         } else {
-            const int k = pick_beamlet(S, A, idx, h, r.w, P.key0, P.key1);
-            const float* row = S.beamlets + size_t(k) * 16;
+            // a dose-matrix sub-problem is its own beamlet; otherwise sample one
+            const int kb = A.n_sub ? int(k) : pick_beamlet(S, A, idx, h, r.w, P.key0, P.key1);
+            const float* row = S.beamlets + size_t(kb) * 16;
             src = row; cen = row + 3; au = row + 6; av = row + 9;
             a0 = row[12]; a1 = row[13]; b0 = row[14]; b1 = row[15];
         }
@@ -719,7 +737,10 @@ __device__ __forceinline__ void bank_pending(const SimParams& P, const PhaseArgs
                 ch.E = E;
                 ch.ix = p.ix; ch.iy = p.iy; ch.iz = p.iz;
                 ch.hist = p.hist;
-                const uint64_t id = child_id(uint64_t(p.pidlo) | (uint64_t(p.pidhi) << 32), p.flags & 0xFFFFFFu);
+                const uint64_t id = child_id(uint64_t(p.pidlo) | (uint64_t(p.pidhi) << 32), p.flags & kChildMask);
+                // the child index cannot wrap into the slot bits (no particle
+                // comes near 65535 secondaries; flag it if one ever did)
+                if ((p.flags & kChildMask) == kChildMask) atomicOr(P.status, ST_QUEUE_OVERFLOW);
                 ch.pidlo = uint32_t(id);
                 ch.pidhi = uint32_t(id >> 32);
                 ch.ctr = 0;

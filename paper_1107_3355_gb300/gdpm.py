@@ -46,7 +46,8 @@ EXPORTED = ["gdpm_context_create", "gdpm_context_destroy", "gdpm_set_param",
             "gdpm_tables_destroy", "gdpm_source_set", "gdpm_simulate",
             "gdpm_set_history_records", "gdpm_request_submit", "gdpm_request_poll",
             "gdpm_strerror", "gdpm_debug_philox", "gdpm_debug_sample", "gdpm_tables_export",
-            "gdpm_debug_sources", "gdpm_debug_beamlets", "gdpm_simulate_noalloc"]
+            "gdpm_debug_sources", "gdpm_debug_beamlets", "gdpm_simulate_noalloc",
+            "gdpm_simulate_beamlets"]
 
 
 class gdpm_material_desc(C.Structure):
@@ -140,6 +141,7 @@ def lib():
                 "gdpm_debug_sources": [vp, vp, vp, u64, i, u64, u64, vp],
                 "gdpm_debug_beamlets": [vp, u64, u64, vp],
                 "gdpm_simulate_noalloc": [vp, vp, vp, u64, i, vp, vp, C.POINTER(gdpm_stats)],
+                "gdpm_simulate_beamlets": [vp, vp, vp, vp, i, vp, vp, C.POINTER(gdpm_stats)],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -267,6 +269,19 @@ def gdpm_simulate(ctx, phantom, tables, n_histories, n_batches, dose_out=None, s
     return st.as_dict()
 
 
+def gdpm_simulate_beamlets(ctx, phantom, tables, n_histories, n_batches, dose_out,
+                           sigma_out=None):
+    """Beamlet dose matrix: row k of the current fluence map is its own
+    calculation of n_histories[k] histories; dose_out/sigma_out hold
+    K x n_voxels doubles (host or device)."""
+    n = np.ascontiguousarray(np.asarray(n_histories, dtype=np.uint64))
+    st = gdpm_stats()
+    _check(lib().gdpm_simulate_beamlets(ctx, phantom, tables, n.ctypes.data_as(C.c_void_p),
+                                        n_batches, _ptr(dose_out), _ptr(sigma_out), C.byref(st)),
+           "gdpm_simulate_beamlets")
+    return st.as_dict()
+
+
 def gdpm_set_history_records(ctx, rec, recd, n):
     _check(lib().gdpm_set_history_records(ctx, _ptr(rec), _ptr(recd), n),
            "gdpm_set_history_records")
@@ -381,6 +396,18 @@ class Engine:
         if sigma is None:
             sigma = torch.empty(V, dtype=torch.float64, device=f"cuda:{self.device}")
         st = gdpm_simulate(self.ctx, self.phantom, self.tables, n, nb, dose, sigma)
+        return dose, sigma, st
+
+    def run_beamlets(self, n_batches=None, with_sigma=True):
+        """The problem's beamlet dose matrix (its sub_histories per fluence
+        row): (dose, sigma or None, stats) with K x n_voxels device tensors."""
+        import torch
+        nb = self.prob.n_batches if n_batches is None else n_batches
+        K, V = len(self.prob.sub_histories), self.prob.phantom.n_voxels
+        dose = torch.empty((K, V), dtype=torch.float64, device=f"cuda:{self.device}")
+        sigma = torch.empty((K, V), dtype=torch.float64, device=f"cuda:{self.device}") if with_sigma else None
+        st = gdpm_simulate_beamlets(self.ctx, self.phantom, self.tables, self.prob.sub_histories, nb,
+                                    dose, sigma)
         return dose, sigma, st
 
     def close(self):

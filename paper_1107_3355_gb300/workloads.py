@@ -396,9 +396,24 @@ class Problem:
     seed: int = 12345
     request_id: int = 0
     flags: int = 0
+    first_history: int = 0         # id of the first history (Philox counter word 0)
+    # beamlet dose matrix: one sub-problem per fluence-map row, with these
+    # histories each (n_histories is then their sum)
+    sub_histories: Optional[Tuple[int, ...]] = None
 
     def with_(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)
+
+    def sub_problem(self, k: int) -> "Problem":
+        """Beamlet k of a dose-matrix problem as a problem of its own: that
+        row alone as the source, its histories, and its range of history ids."""
+        n = [int(v) for v in self.sub_histories]
+        rows = np.asarray(self.source.beamlets[k:k + 1], np.float64).copy()
+        rows[0, 16] = 1.0
+        src = dataclasses.replace(self.source, beamlets=rows, sampler="cdf")
+        return dataclasses.replace(self, source=src, n_histories=n[k],
+                                   first_history=self.first_history + sum(n[:k]),
+                                   sub_histories=None)
 
 
 def tiny_problem(n_histories=100_000, seed=12345, n_batches=100) -> Problem:
@@ -416,6 +431,27 @@ def slab_photon_problem(n_histories=100_000_000, seed=12345, n_batches=100,
     ph = slab_phantom(shape, voxel)
     return Problem(ph, field_source(ph, kramers_spectrum()), n_histories, n_batches,
                    eabs_photon=0.05, eabs_electron=0.2, e_min=0.005, e_max=6.5, seed=seed)
+
+
+def beamlet_matrix_problem(n_beamlets=400, seed=7, n_batches=1, hist_range=(1e5, 5e6),
+                           shape=(128, 128, 128), voxel=(0.25, 0.25, 0.25)) -> Problem:
+    """Beamlet dose matrix on the 128^3 slab: n_beamlets square beamlets of
+    side U{0.5, 1, 1.5, 2} cm centred U within +-8 cm of the axis on the z = 0
+    face, point source at SSD 100 cm on the axis, 6 MV-like spectrum; each
+    beamlet gets log-uniform(hist_range) histories and its own tally."""
+    ph = slab_phantom(shape, voxel)
+    X, Y, _ = ph.extent
+    fr = BeamFrame((X / 2, Y / 2, -100.0), (X / 2, Y / 2, 0.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.0))
+    rng = np.random.default_rng(seed)
+    rows, hist = [], []
+    for _ in range(n_beamlets):
+        a = float(rng.choice([0.5, 1.0, 1.5, 2.0]))
+        cu, cv = rng.uniform(-8.0, 8.0, 2)
+        rows.append(beamlet_row(fr, cu - a / 2, cu + a / 2, cv - a / 2, cv + a / 2, 1.0))
+        hist.append(int(round(math.exp(rng.uniform(math.log(hist_range[0]), math.log(hist_range[1]))))))
+    return Problem(ph, beamlet_source(rows, kramers_spectrum()), sum(hist), n_batches,
+                   eabs_photon=0.05, eabs_electron=0.2, e_min=0.005, e_max=6.5,
+                   sub_histories=tuple(hist))
 
 
 def slab_electron_problem(n_histories=10_000_000, seed=12345, n_batches=100,
