@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "serve"])
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "serve", "beamlets"])
+    ap.add_argument("--matrix-beamlets", type=int, default=400)
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-arc-histories", type=float, default=5e8)
@@ -256,6 +257,66 @@ def serve_bench(args):
     print(json.dumps(line))
 
 
+def beamlet_matrix_bench(args):
+    """Beamlet dose matrix on the 128^3 slab: 400 beamlets (sides U{0.5, 1,
+    1.5, 2} cm, centres within +-8 cm, log-uniform 1e5..5e6 histories each,
+    seed 7), one tally per beamlet.  Timed as one gdpm_simulate_beamlets call
+    (all beamlets in one sequence of phases) and as 400 gdpm_simulate calls,
+    one beamlet at a time; same histories either way."""
+    import numpy as np
+    import torch
+    from paper_1107_3355_gb300 import gdpm as G
+
+    prob = W.beamlet_matrix_problem(n_beamlets=args.matrix_beamlets, n_batches=1)
+    K, V, total = len(prob.sub_histories), prob.phantom.n_voxels, prob.n_histories
+    eng = G.Engine(prob, params={G.GDPM_PARAM_PROFILE: 1})
+    dose = torch.empty((K, V), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        G.gdpm_simulate_beamlets(eng.ctx, eng.phantom, eng.tables, prob.sub_histories, 1, dose)
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = G.gdpm_simulate_beamlets(eng.ctx, eng.phantom, eng.tables, prob.sub_histories, 1, dose)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    batched = total / (float(np.median(ms)) / 1e3)
+    # one beamlet at a time (dose of each beamlet alone, 2 batches: the
+    # smallest a single calculation allows)
+    one = torch.empty(V, dtype=torch.float64, device="cuda")
+    single = W.beamlet_source(prob.source.beamlets[:1], prob.source.spectrum)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K):
+        single.beamlets = prob.source.beamlets[k:k + 1]
+        G.gdpm_source_set(eng.ctx, single)
+        G.gdpm_simulate(eng.ctx, eng.phantom, eng.tables, int(prob.sub_histories[k]), 2, one, None)
+    torch.cuda.synchronize()
+    serial = total / (time.perf_counter() - t0)
+    eng.close()
+    line = {"metric": "histories/s", "mode": "beamlet_matrix", "value": batched,
+            "unit": "histories/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.median(ms)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "slab128_beamlet_matrix", "beamlets": K, "histories": total,
+                       "tally": "one FP64 grid per beamlet (%.1f GB)" % (K * V * 8 / 1e9),
+                       "l2": "flushed between steps (256 MB write)"},
+            "one_beamlet_at_a_time": {"value": serial, "unit": "histories/s",
+                                      "calls": K, "batches_per_call": 2},
+            "kernel_ms_per_step": list(st["kernel_ms"]),
+            "gpu_launches": int(st["launches"]), "clocks": clk}
+    print(json.dumps(line))
+
+
 def rank_env():
     """(world size, rank, local rank) as torchrun sets them (1, 0, 0 alone)."""
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
@@ -283,6 +344,9 @@ def main():
     args = parse()
     if args.mode == "serve":
         serve_bench(args)
+        return
+    if args.mode == "beamlets":
+        beamlet_matrix_bench(args)
         return
     world, rank, local = rank_env()
     n_hist = int(args.histories)

@@ -234,6 +234,27 @@ int gdpm_simulate_beamlets(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb,
                            const uint64_t *n_histories, int n_batches, double *dose_out,
                            double *sigma_out, gdpm_stats *stats_out);
 
+/* Launch configuration chosen by gdpm_autotune. */
+typedef struct {
+    int batch_mode;            /* GDPM_PARAM_BATCH_MODE value: 1 one after another, 2 side by side */
+    uint32_t source_chunk;     /* GDPM_PARAM_SOURCE_CHUNK: primaries per transport phase */
+    int speculative;           /* GDPM_PARAM_SPECULATIVE: phase pairs per host check */
+    int candidates_tried;
+    double histories_per_s;    /* of the best candidate (wall clock, whole call) */
+} gdpm_tune_result;
+
+/* Autotuner: run the calculation gdpm_simulate(ph, tb, n_histories,
+ * n_batches) with the current source under each candidate launch
+ * configuration -- batches side by side (when their grids fit) or one after
+ * another, 1M / 4M / 8M primaries per phase, 1 / 2 / 4 phase pairs per host
+ * check -- until the wall-clock budget is spent, keep the fastest, and set
+ * it on the context (GDPM_PARAM_BATCH_MODE, _SOURCE_CHUNK, _SPECULATIVE).
+ * Results do not depend on the configuration (per-history random streams),
+ * only the time does.  `out` is a host struct.
+ * Errors: those of gdpm_simulate; GDPM_E_ARG (budget_ms <= 0, NULL out). */
+int gdpm_autotune(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
+                  int n_batches, double budget_ms, gdpm_tune_result *out);
+
 /* Optional per-history records for the next gdpm_simulate on this context:
  * rec (device, n*4 int32: real photon interactions, electron steps, hard
  * electron events, banked secondaries) and recd (device, n*2 doubles:

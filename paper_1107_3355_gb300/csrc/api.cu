@@ -1089,6 +1089,72 @@ int gdpm_simulate(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_h
                          dose_out, sigma_out, stats_out, ctx->hrec, ctx->hrecd);
 }
 
+int gdpm_autotune(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_histories,
+                  int n_batches, double budget_ms, gdpm_tune_result* out) {
+    if (!ctx || !out || !(budget_ms > 0)) return GDPM_E_ARG;
+    int rc = validate_run(ctx, ph, tb, ctx->src, n_histories, n_batches);
+    if (rc) return rc;
+    GDPM_CUDA_TRY(cudaSetDevice(ctx->device));
+    const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
+    // candidates: batch mode x primaries per phase x phase pairs per host check
+    struct Cand { int mode; uint32_t chunk; int spec; };
+    std::vector<Cand> cands;
+    const bool can_conc = n_batches <= kMaxConcurrentBatches &&
+                          V * size_t(n_batches) * 8 <= ctx->concurrent_max_bytes;
+    const uint32_t chunks[3] = {1u << 20, 1u << 22, 1u << 23};
+    for (int mode = 2; mode >= 1; --mode) {
+        if (mode == 2 && !can_conc) continue;
+        const uint64_t per = mode == 2 ? n_histories : (n_histories + n_batches - 1) / n_batches;
+        uint32_t last = 0;
+        for (uint32_t c : chunks) {
+            const uint32_t cc = uint32_t(std::min<uint64_t>(c, per));
+            if (cc == last) continue;               // the same phases as the previous candidate
+            last = cc;
+            for (int spec : {1, 2, 4}) cands.push_back({mode, cc, spec});
+        }
+    }
+    const int saved_mode = ctx->batch_mode, saved_spec = ctx->speculative, saved_prof = ctx->profile;
+    const uint32_t saved_chunk = ctx->source_chunk;
+    ctx->profile = 0;
+    double best_ms = 1e300, spent = 0.0;
+    Cand best = cands.front();
+    int tried = 0;
+    for (const Cand& c : cands) {
+        ctx->batch_mode = c.mode;
+        ctx->source_chunk = c.chunk;
+        ctx->speculative = c.spec;
+        gdpm_stats st{};
+        const auto t0 = std::chrono::steady_clock::now();
+        rc = simulate_impl(ctx, ctx->run, ph, tb, ctx->src, ctx->request_id, n_histories, n_batches,
+                           nullptr, nullptr, &st, nullptr, nullptr);
+        const double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (rc) break;
+        ++tried;
+        spent += wall;
+        if (wall < best_ms) {
+            best_ms = wall;
+            best = c;
+        }
+        if (spent >= budget_ms) break;
+    }
+    ctx->profile = saved_prof;
+    if (rc) {
+        ctx->batch_mode = saved_mode;
+        ctx->source_chunk = saved_chunk;
+        ctx->speculative = saved_spec;
+        return rc;
+    }
+    ctx->batch_mode = best.mode;
+    ctx->source_chunk = best.chunk;
+    ctx->speculative = best.spec;
+    out->batch_mode = best.mode;
+    out->source_chunk = best.chunk;
+    out->speculative = best.spec;
+    out->candidates_tried = tried;
+    out->histories_per_s = double(n_histories) / (best_ms / 1e3);
+    return GDPM_OK;
+}
+
 int gdpm_simulate_beamlets(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb,
                            const uint64_t* n_histories, int n_batches, double* dose_out,
                            double* sigma_out, gdpm_stats* st) {

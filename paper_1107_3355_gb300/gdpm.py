@@ -47,7 +47,7 @@ EXPORTED = ["gdpm_context_create", "gdpm_context_destroy", "gdpm_set_param",
             "gdpm_set_history_records", "gdpm_request_submit", "gdpm_request_poll",
             "gdpm_strerror", "gdpm_debug_philox", "gdpm_debug_sample", "gdpm_tables_export",
             "gdpm_debug_sources", "gdpm_debug_beamlets", "gdpm_simulate_noalloc",
-            "gdpm_simulate_beamlets"]
+            "gdpm_simulate_beamlets", "gdpm_autotune"]
 
 
 class gdpm_material_desc(C.Structure):
@@ -142,6 +142,7 @@ def lib():
                 "gdpm_debug_beamlets": [vp, u64, u64, vp],
                 "gdpm_simulate_noalloc": [vp, vp, vp, u64, i, vp, vp, C.POINTER(gdpm_stats)],
                 "gdpm_simulate_beamlets": [vp, vp, vp, vp, i, vp, vp, C.POINTER(gdpm_stats)],
+                "gdpm_autotune": [vp, vp, vp, u64, i, d, C.POINTER(gdpm_tune_result)],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -280,6 +281,20 @@ def gdpm_simulate_beamlets(ctx, phantom, tables, n_histories, n_batches, dose_ou
                                         n_batches, _ptr(dose_out), _ptr(sigma_out), C.byref(st)),
            "gdpm_simulate_beamlets")
     return st.as_dict()
+
+
+class gdpm_tune_result(C.Structure):
+    _fields_ = [("batch_mode", C.c_int), ("source_chunk", C.c_uint32), ("speculative", C.c_int),
+                ("candidates_tried", C.c_int), ("histories_per_s", C.c_double)]
+
+
+def gdpm_autotune(ctx, phantom, tables, n_histories, n_batches, budget_ms=2000.0):
+    """Try launch configurations on this calculation, keep and set the fastest;
+    returns it as a dict."""
+    r = gdpm_tune_result()
+    _check(lib().gdpm_autotune(ctx, phantom, tables, n_histories, n_batches, budget_ms,
+                               C.byref(r)), "gdpm_autotune")
+    return {k: getattr(r, k) for k, _ in r._fields_}
 
 
 def gdpm_set_history_records(ctx, rec, recd, n):
