@@ -99,8 +99,15 @@ void runner_free(Runner& r) {
     Workspace& w = r.ws;
     Buffer* bs[] = {&w.edep, &w.edep2, &w.hi2, &w.lo2, &w.s1, &w.s2, &w.hi, &w.lo, &w.qph,
                     &w.qel0, &w.qel1, &w.ctl, &w.prefix, &w.counters, &w.ledger, &w.status,
-                    &w.edges, &w.beamlets, &w.bl_cdf, &w.stage};
+                    &w.edges, &w.beamlets, &w.bl_cdf, &w.bl_row, &w.bl_f, &w.al_cut,
+                    &w.al_alias, &w.chains, &w.pick, &w.sub_first, &w.sub_inv, &w.sub_nbig,
+                    &w.loop_k, &w.stage};
     for (Buffer* b : bs) release(*b);
+    if (r.loop_exec) cudaGraphExecDestroy(r.loop_exec);
+    if (r.loop_graph) cudaGraphDestroy(r.loop_graph);
+    r.loop_exec = nullptr;
+    r.loop_graph = nullptr;
+    r.loop_key.clear();
     if (w.pinned_host.p) cudaFreeHost(w.pinned_host.p);
     w.pinned_host.p = nullptr;
     for (cudaEvent_t e : r.prof_events) cudaEventDestroy(e);
@@ -455,6 +462,37 @@ static size_t bytes_needed(gdpm_ctx* ctx, const Runner& r, size_t V, uint64_t n_
 //   electron phase k consumes E[k] (+ electron primaries), banks photons into
 //   P[k+1] and electrons into E[k+2].
 // ctl row k: [0] pop counter of phase k, [1] count of P[k], [2] count of E[k].
+// The phase schedule of one run: queues, counter rows, sources (primaries
+// [first, first+n) in chunks of `chunk`), batch layout.  Both the host loop
+// and the device-driven loop hand it to the one phase kernel, which derives
+// phase k's arguments from it.
+static LoopArgs loop_args(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_source_state& src,
+                          uint64_t first, uint64_t n, uint32_t nb_small, uint32_t nb_rem, uint32_t chunk,
+                          uint32_t n_sub, uint32_t sub_batches, const uint32_t* sub_first) {
+    Workspace& ws = r.ws;
+    LoopArgs L{};
+    L.qph = make_queue(ws.qph, ws.cap_ph);
+    L.qe0 = make_queue(ws.qel0, ws.cap_el);
+    L.qe1 = make_queue(ws.qel1, ws.cap_el);
+    L.ctl = static_cast<uint32_t*>(ws.ctl.p);
+    L.status = P.status;
+    L.bin_prefix = static_cast<const uint32_t*>(ws.prefix.p);
+    L.sub_first = sub_first;
+    const bool metro = P.S.sampler == GDPM_SAMPLE_METROPOLIS && P.S.n_beamlets > 0 && n_sub == 0;
+    L.chains = metro ? static_cast<uint32_t*>(ws.chains.p) : nullptr;
+    L.pick = metro ? static_cast<uint32_t*>(ws.pick.p) : nullptr;
+    L.n_src = uint32_t(n);
+    L.first = uint32_t(first);
+    L.chunk = chunk;
+    L.nb_small = nb_small;
+    L.nb_rem = nb_rem;
+    L.n_sub = n_sub;
+    L.sub_batches = sub_batches;
+    L.src_particle = src.desc.particle;
+    L.max_phases = ctx->max_phases;
+    return L;
+}
+
 static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_source_state& src,
                       uint64_t first, uint64_t n, uint32_t nb_small, uint32_t nb_rem, uint32_t chunk,
                       int64_t& phases, int64_t& aux, uint32_t n_sub = 0, uint32_t sub_batches = 0,
@@ -532,6 +570,44 @@ static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_s
     return GDPM_OK;
 }
 
+// The same phases as run_phases, driven on the device: one launch of a
+// CUDA graph whose WHILE node repeats (photon phase, electron phase,
+// control) until no primaries or particles are left -- no host checks, no
+// per-phase launches.  The instantiated graph is kept on the runner and
+// rebuilt when anything it was built for changes.  The phase count is
+// read back into *k_host (pinned) when the stream reaches that point.
+static int run_phases_graph(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_source_state& src,
+                            uint64_t first, uint64_t n, uint32_t nb_small, uint32_t nb_rem,
+                            uint32_t chunk, uint32_t* k_host, uint32_t n_sub = 0,
+                            uint32_t sub_batches = 0, const uint32_t* sub_first = nullptr) {
+    Workspace& ws = r.ws;
+    cudaStream_t s = r.stream;
+    int rc;
+    if ((rc = ensure(ws.loop_k, 16))) return rc;
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, size_t(ctx->max_phases + 4) * 16, s));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.loop_k.p, 0, 16, s));
+    LoopArgs L = loop_args(ctx, r, P, src, first, n, nb_small, nb_rem, chunk, n_sub, sub_batches, sub_first);
+    L.k = static_cast<uint32_t*>(ws.loop_k.p);
+    const bool metro = L.pick != nullptr;
+    // the graph holds copies of P and L: rebuild when they differ
+    std::vector<unsigned char> key(sizeof(SimParams) + sizeof(LoopArgs) + 2 * sizeof(int));
+    std::memcpy(key.data(), &P, sizeof(SimParams));
+    std::memcpy(key.data() + sizeof(SimParams), &L, sizeof(LoopArgs));
+    const int extra[2] = {ctx->block_threads, ctx->blocks_per_sm};
+    std::memcpy(key.data() + sizeof(SimParams) + sizeof(LoopArgs), extra, sizeof(extra));
+    if (!r.loop_exec || key != r.loop_key) {
+        if (r.loop_exec) cudaGraphExecDestroy(r.loop_exec);
+        if (r.loop_graph) cudaGraphDestroy(r.loop_graph);
+        r.loop_exec = nullptr;
+        r.loop_graph = nullptr;
+        r.loop_key.clear();
+        if ((rc = build_loop_graph(ctx, P, L, metro, &r.loop_graph, &r.loop_exec))) return rc;
+        r.loop_key = key;
+    }
+    GDPM_CUDA_TRY(cudaGraphLaunch(r.loop_exec, s));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(k_host, ws.loop_k.p, 4, cudaMemcpyDeviceToHost, s));
+    return GDPM_OK;
+}
 
 // Point P's batch tally at buffer `which` (0 or 1).
 static void select_tally(Runner& r, SimParams& P, int which) {
@@ -632,6 +708,7 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
     r.prof_kind.clear();
     GDPM_CUDA_TRY(cudaEventRecord(r.ev0, s));
     int64_t phases = 0;
+    const uint32_t* graph_k = nullptr;   // device-driven loop: its phase count lands here
     int run_rc = GDPM_OK;
     if (conc) {
         // all batches side by side: particles carry their batch, each batch
@@ -640,7 +717,14 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
         P.edep = static_cast<double*>(ws.edep.p);
         P.edep_hi = static_cast<float*>(ws.edep.p);
         P.edep_lo = static_cast<float*>(ws.edep.p) + V * size_t(n_batches);
-        run_rc = run_phases(ctx, r, P, src, 0, n_hist, nb_small, nb_rem, chunk, phases, aux);
+        if (ctx->use_graph && !ctx->profile) {
+            uint32_t* kh = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ws.pinned_host.p) + 32);
+            run_rc = run_phases_graph(ctx, r, P, src, 0, n_hist, nb_small, nb_rem, chunk, kh);
+            graph_k = kh;
+            ++aux;                                  // the graph launch
+        } else {
+            run_rc = run_phases(ctx, r, P, src, 0, n_hist, nb_small, nb_rem, chunk, phases, aux);
+        }
         ++aux;
         if (run_rc == GDPM_OK) {
             const size_t pi = prof_begin(ctx, r, s, 2);
@@ -710,6 +794,7 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
     if (st) {
         std::memset(st, 0, sizeof(*st));
         fill_stats(hc, hl, st);
+        if (graph_k) phases = int64_t(*graph_k);
         st->phases = phases;
         st->launches = phases + aux + 2;    // + finalize and metric
         float ms = 0;
@@ -718,7 +803,7 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
     }
     prof_collect(r, st);
     if (*hs & ST_QUEUE_OVERFLOW) return GDPM_E_QUEUE_OVERFLOW;
-    if (*hs & ST_ITER_CAP) return GDPM_E_TIMEOUT;
+    if (*hs & (ST_ITER_CAP | ST_PHASE_CAP)) return GDPM_E_TIMEOUT;
     return GDPM_OK;
 }
 
@@ -922,6 +1007,10 @@ int gdpm_set_param(gdpm_ctx* ctx, int param, double v) {
     case GDPM_PARAM_REQUEST_ID:
         if (v < 0 || v > 4294967295.0) return GDPM_E_ARG;
         ctx->request_id = uint32_t(v);
+        return GDPM_OK;
+    case GDPM_PARAM_GRAPH:
+        if (v != 0 && v != 1) return GDPM_E_ARG;
+        ctx->use_graph = int(v);
         return GDPM_OK;
     case GDPM_PARAM_SPECULATIVE:
         if (v < 1 || v > 64) return GDPM_E_ARG;
@@ -1232,8 +1321,18 @@ int gdpm_simulate_beamlets(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb,
     r.prof_kind.clear();
     GDPM_CUDA_TRY(cudaEventRecord(r.ev0, s));
     int64_t phases = 0, aux = 0;
-    int run_rc = run_phases(ctx, r, P, src, 0, total, 0, 0, chunk, phases, aux, K, uint32_t(nb),
+    const uint32_t* graph_k = nullptr;
+    int run_rc;
+    if (ctx->use_graph && !ctx->profile) {
+        uint32_t* kh = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ws.pinned_host.p) + 32);
+        run_rc = run_phases_graph(ctx, r, P, src, 0, total, 0, 0, chunk, kh, K, uint32_t(nb),
+                                  static_cast<const uint32_t*>(ws.sub_first.p));
+        graph_k = kh;
+        ++aux;
+    } else {
+        run_rc = run_phases(ctx, r, P, src, 0, total, 0, 0, chunk, phases, aux, K, uint32_t(nb),
                             static_cast<const uint32_t*>(ws.sub_first.p));
+    }
     GDPM_CUDA_TRY(cudaEventRecord(r.ev1, s));
     if (run_rc != GDPM_OK) {
         cudaStreamSynchronize(s);
@@ -1279,6 +1378,7 @@ int gdpm_simulate_beamlets(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb,
     if (st) {
         std::memset(st, 0, sizeof(*st));
         fill_stats(hc, hl, st);
+        if (graph_k) phases = int64_t(*graph_k);
         st->phases = phases;
         st->launches = phases + aux;
         float ms = 0;
@@ -1287,7 +1387,7 @@ int gdpm_simulate_beamlets(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb,
     }
     prof_collect(r, st);
     if (*hs & ST_QUEUE_OVERFLOW) return GDPM_E_QUEUE_OVERFLOW;
-    if (*hs & ST_ITER_CAP) return GDPM_E_TIMEOUT;
+    if (*hs & (ST_ITER_CAP | ST_PHASE_CAP)) return GDPM_E_TIMEOUT;
     return GDPM_OK;
 }
 

@@ -21,6 +21,7 @@ constexpr float kTwoPi = 6.28318530717958647f;
 enum : uint32_t {
     ST_QUEUE_OVERFLOW = 1u,
     ST_ITER_CAP = 2u,
+    ST_PHASE_CAP = 4u,          // the device-driven phase loop reached its phase cap
     ST_BAD_MATERIAL = 4u,
 };
 

@@ -781,8 +781,7 @@ constexpr uint32_t kGrab = 32u;
 // secondaries of the last step, refill lanes whose particle ended.  Then
 // each lane takes one step of its own particle.
 template <int PT>
-__global__ void __launch_bounds__(256, PT == 0 ? GDPM_MIN_CTAS_PHOTON : GDPM_MIN_CTAS_ELECTRON)
-k_phase(const SimParams P, const PhaseArgs A) {
+__device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t n_in = A.in_count ? min(*A.in_count, A.in.capacity) : 0u;
     const uint32_t total = A.n_src + n_in;
@@ -910,6 +909,117 @@ k_phase(const SimParams P, const PhaseArgs A) {
     __syncthreads();
     for (int k = threadIdx.x; k < C_NCOUNT; k += blockDim.x)
         if (s_cnt[k]) atomicAdd(&P.counters[k], (unsigned long long)s_cnt[k]);
+}
+
+template <int PT>
+__global__ void __launch_bounds__(256, PT == 0 ? GDPM_MIN_CTAS_PHOTON : GDPM_MIN_CTAS_ELECTRON)
+k_phase(const SimParams P, const PhaseArgs A) {
+    phase_run<PT>(P, A);
+}
+
+
+// ---------------------------------------------------------------- device-driven phase loop
+// Phase k's arguments from k alone, as the host loop sets them: photon
+// phase k (even) reads photons P[k] and banks electrons into E[k+1];
+// electron phase k (odd) reads E[k] and banks photons into P[k+1] and
+// electrons into E[k+2].  Row k of ctl holds (pop head, P[k] count, E[k]
+// count, -).  The source particle's j-th phase takes primaries
+// [first + j*chunk, first + min((j+1)*chunk, n_src)).
+__device__ __forceinline__ PhaseArgs phase_args(const LoopArgs& L, uint32_t k) {
+    PhaseArgs A{};
+    A.nb_small = L.nb_small;
+    A.nb_rem = L.nb_rem;
+    A.bin_prefix = L.bin_prefix;
+    A.n_sub = L.n_sub;
+    A.sub_batches = L.sub_batches;
+    A.sub_first = L.sub_first;
+    A.bank_block = L.bank_block;
+    const bool ph = (k % 2u) == 0u;
+    const bool src_phase = ph == (L.src_particle == GDPM_PHOTON);
+    if (src_phase) {
+        const uint32_t j = L.src_particle == GDPM_PHOTON ? k / 2u : (k - 1u) / 2u;
+        const uint64_t off = uint64_t(j) * L.chunk;
+        if (off < L.n_src) {
+            A.n_src = uint32_t(min(uint64_t(L.chunk), uint64_t(L.n_src) - off));
+            A.src_first = L.first + uint32_t(off);
+            A.bl_pick = L.pick;
+        }
+    }
+    uint32_t* ctl = L.ctl;
+    A.head = ctl + size_t(k) * 4;
+    if (ph) {
+        A.in = L.qph;
+        A.in_count = k >= 1u ? ctl + size_t(k) * 4 + 1 : nullptr;
+        A.out_el = ((k + 1u) / 2u) % 2u ? L.qe1 : L.qe0;
+        A.out_el_count = ctl + size_t(k + 1) * 4 + 2;
+        A.out_ph = L.qph;
+        A.out_ph_count = ctl + size_t(k + 2) * 4 + 1;
+    } else {
+        A.in = (k / 2u) % 2u ? L.qe1 : L.qe0;
+        A.in_count = ctl + size_t(k) * 4 + 2;
+        A.out_ph = L.qph;
+        A.out_ph_count = ctl + size_t(k + 1) * 4 + 1;
+        A.out_el = ((k + 2u) / 2u) % 2u ? L.qe1 : L.qe0;
+        A.out_el_count = ctl + size_t(k + 2) * 4 + 2;
+    }
+    return A;
+}
+
+// One pass of the device-driven loop runs photon phase k and electron
+// phase k+1, k = *L.k (even); PT selects which of the two this launch is.
+// The phase's arguments are derived in shared memory from k.  (A kernel of
+// its own: the host loop's k_phase takes them as kernel parameters, which
+// keeps more registers for the transport loop.)
+template <int PT>
+__global__ void __launch_bounds__(256, PT == 0 ? GDPM_MIN_CTAS_PHOTON : GDPM_MIN_CTAS_ELECTRON)
+k_phase_loop(const SimParams P, const LoopArgs L) {
+    __shared__ PhaseArgs sA;
+    if (threadIdx.x == 0) sA = phase_args(L, *L.k + uint32_t(PT));
+    __syncthreads();
+    phase_run<PT>(P, sA);
+}
+
+// Metropolis picks for this pass's source phase (before it runs).
+__global__ void k_metropolis_loop(const SimParams P, const LoopArgs L) {
+    const uint32_t k = *L.k + (L.src_particle == GDPM_PHOTON ? 0u : 1u);
+    const PhaseArgs A = phase_args(L, k);
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t C = P.S.n_chains;
+    if (A.n_src == 0u || c >= C) return;
+    const uint32_t nf = uint32_t(P.S.n_beamlets);
+    const double* f = P.S.bl_f;
+    uint32_t I = L.chains[c];
+    double fI = f[I];
+    const uint64_t end = uint64_t(A.src_first) + A.n_src;
+    for (uint64_t h = uint64_t(A.src_first) + (uint64_t(c) + C - A.src_first % C) % C; h < end; h += C) {
+        const uint4 w = philox_block(uint32_t(h), 0u, 0u, 0u, P.key0, P.key1);
+        const uint32_t J = __umulhi(w.x, nf);
+        const double fJ = f[J];
+        const double u = (double(w.y) + 0.5) * 0x1p-32;
+        if (u * fI < fJ) {
+            I = J;
+            fI = fJ;
+        }
+        L.pick[h - A.src_first] = I;
+    }
+    L.chains[c] = I;
+}
+
+// After a pass: go on while primaries remain or the pass left particles for
+// the next one (photons P[k+2], electrons E[k+3]); stop at the phase cap
+// with a status bit.  One thread.
+__global__ void k_loop_ctl(const LoopArgs L, cudaGraphConditionalHandle h) {
+    const uint32_t k = *L.k, k2 = k + 2u;
+    const uint32_t j_next = k2 / 2u;        // index of the next pass's source phase
+    const bool src_left = uint64_t(j_next) * L.chunk < uint64_t(L.n_src);
+    const uint32_t pending = L.ctl[size_t(k2) * 4 + 1] + L.ctl[size_t(k2 + 1) * 4 + 2];
+    bool more = src_left || pending > 0u;
+    if (more && int(k2) + 3 >= L.max_phases) {
+        atomicOr(L.status, ST_PHASE_CAP);
+        more = false;
+    }
+    *L.k = k2;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------- checks
@@ -1093,6 +1203,83 @@ int launch_debug_sources(gdpm_ctx* ctx, const SimParams& P, const PhaseArgs& A, 
     const uint32_t grid = uint32_t(ctx->sm_count) * 2u;
     k_debug_sources<<<grid, 256, 0, ctx->stream>>>(P, A, n, out);
     GDPM_CUDA_TRY(cudaGetLastError());
+    return GDPM_OK;
+}
+
+// The device-driven phase loop: a graph holding one conditional WHILE node
+// whose body runs [Metropolis picks ->] photon phase -> electron phase ->
+// control kernel; the control kernel advances the phase index and ends the
+// loop when nothing is left (or at the phase cap).  The phase kernels use
+// the persistent grids of launch_phase; L.bank_block is set here.
+int build_loop_graph(gdpm_ctx* ctx, const SimParams& P, LoopArgs& L, bool metropolis,
+                     cudaGraph_t* graph, cudaGraphExec_t* exec) {
+    *graph = nullptr;
+    *exec = nullptr;
+    uint32_t grid[2];
+    size_t smem[2];
+    const void* fn[2] = {(const void*)k_phase_loop<0>, (const void*)k_phase_loop<1>};
+    for (int t = 0; t < 2; ++t) {
+        smem[t] = smem_of(P.T, t == 0 ? GDPM_PHOTON : GDPM_ELECTRON);
+        GDPM_CUDA_TRY(cudaFuncSetAttribute(fn[t], cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem[t])));
+        int bps = ctx->blocks_per_sm;
+        if (bps <= 0) {
+            GDPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn[t], ctx->block_threads, smem[t]));
+            if (bps < 1) return GDPM_E_ARG;
+        }
+        grid[t] = uint32_t(ctx->sm_count) * uint32_t(bps);
+    }
+    const uint64_t warps = uint64_t(std::max(grid[0], grid[1])) * uint64_t(ctx->block_threads / 32);
+    const uint64_t cap = std::min(L.qph.capacity, L.qe0.capacity);
+    const uint64_t bb = std::min<uint64_t>(32u, cap / (8u * warps));
+    L.bank_block = bb >= 8u ? uint32_t(bb) : 0u;
+
+    cudaGraph_t g = nullptr;
+    GDPM_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp{};
+    cudaGraphNode_t wn = nullptr;
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &cp);
+    }
+    cudaGraph_t body = e == cudaSuccess ? cp.conditional.phGraph_out[0] : nullptr;
+    SimParams Pc = P;
+    LoopArgs Lc = L;
+    void* phase_args_v[2] = {&Pc, &Lc};
+    void* metro_args_v[2] = {&Pc, &Lc};
+    void* ctl_args_v[2] = {&Lc, &h};
+    cudaGraphNode_t prev = nullptr;
+    auto add = [&](const void* f, dim3 gd, dim3 bd, size_t sm, void** args) {
+        if (e != cudaSuccess) return;
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void*>(f);
+        kp.gridDim = gd;
+        kp.blockDim = bd;
+        kp.sharedMemBytes = unsigned(sm);
+        kp.kernelParams = args;
+        cudaGraphNode_t n = nullptr;
+        e = cudaGraphAddKernelNode(&n, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        prev = n;
+    };
+    if (metropolis)
+        add((const void*)k_metropolis_loop, dim3((P.S.n_chains + 127) / 128), dim3(128), 0, metro_args_v);
+    add(fn[0], dim3(grid[0]), dim3(ctx->block_threads), smem[0], phase_args_v);
+    add(fn[1], dim3(grid[1]), dim3(ctx->block_threads), smem[1], phase_args_v);
+    add((const void*)k_loop_ctl, dim3(1), dim3(1), 0, ctl_args_v);
+    cudaGraphExec_t x = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        last_cuda_error() = e;
+        cudaGetLastError();
+        return GDPM_E_CUDA;
+    }
+    *graph = g;
+    *exec = x;
     return GDPM_OK;
 }
 

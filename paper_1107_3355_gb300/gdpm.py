@@ -39,6 +39,7 @@ GDPM_PARAM_METRIC_MIN_DENSITY = 14
 GDPM_PARAM_BATCH_MODE = 15
 GDPM_PARAM_CONCURRENT_MAX_HIST = 16
 GDPM_PARAM_CONCURRENT_MAX_MB = 17
+GDPM_PARAM_GRAPH = 18
 MAX_EL, MAX_MAT, MAX_BINS = 16, 8, 256
 
 EXPORTED = ["gdpm_context_create", "gdpm_context_destroy", "gdpm_set_param",
