@@ -454,14 +454,14 @@ def main():
 
     # roofline of the dominant kernel kind, from its live event time
     kinds = ["photon phase", "electron phase", "batch fold"]
-    kms = agg.get("kernel_ms", [0, 0, 0])
+    kms = agg.get("kernel_ms", [0, 0, 0, 0])
     dom = max(range(3), key=lambda i: kms[i])
     if dom == 0:
         ops = agg["ph_flights"] * OPS["ph_flights"] + agg["compton"] * OPS["compton"]
     else:
         ops = (agg["el_steps"] * OPS["el_steps"] + agg["crossings"] * OPS["crossings"] +
                agg["moller"] * OPS["moller"] + agg["brems"] * OPS["brems"])
-    launches_dom = max(1, agg.get("kernel_launches", [1, 1, 1])[dom])
+    launches_dom = max(1, agg.get("kernel_launches", [1, 1, 1, 1])[dom])
     achieved = ops / (kms[dom] / 1e3) / 1e12
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clk.get("sm_mhz") or 2070.0

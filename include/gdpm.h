@@ -129,9 +129,10 @@ typedef struct {
     double transport_ms;           /* device time of the transport + fold loop */
     int64_t crossings;             /* voxel boundaries crossed by electrons */
     /* with GDPM_PARAM_PROFILE: summed device time and launch count per kernel
-     * kind: [0] photon phase, [1] electron phase, [2] batch fold */
-    double kernel_ms[3];
-    int64_t kernel_launches[3];
+     * kind: [0] photon phase, [1] electron phase, [2] batch fold,
+     * [3] primaries (source kernel and Metropolis picks) */
+    double kernel_ms[4];
+    int64_t kernel_launches[4];
 } gdpm_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -354,7 +355,7 @@ int gdpm_debug_beamlets(gdpm_ctx *ctx, uint64_t first, uint64_t n, int32_t *out)
  *
  * All work buffers (batch tally, batch sums, particle queues, counters,
  * source arrays, Woodcock majorant) come from one file-scope device array of
- * GDPM_NOALLOC_SCRATCH_BYTES (about 3.9 MB).  Every GPU that loads this
+ * GDPM_NOALLOC_SCRATCH_BYTES (about 4.0 MB).  Every GPU that loads this
  * library holds that array until the process exits.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) for that
  * device; make that first call before any stream capture begins.
@@ -381,7 +382,7 @@ int gdpm_debug_beamlets(gdpm_ctx *ctx, uint64_t first, uint64_t n, int32_t *out)
 #define GDPM_NOALLOC_MAX_PREFIX 65536
 #define GDPM_NOALLOC_MAX_BEAMLETS 1024
 #define GDPM_NOALLOC_MAX_CHAINS 65536
-#define GDPM_NOALLOC_SCRATCH_BYTES 4024320
+#define GDPM_NOALLOC_SCRATCH_BYTES 4130816
 int gdpm_simulate_noalloc(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
                           int n_batches, double *dose_out, double *sigma_out,
                           gdpm_stats *stats_out);

@@ -98,7 +98,7 @@ void runner_free(Runner& r) {
     if (r.side) cudaStreamSynchronize(r.side);
     Workspace& w = r.ws;
     Buffer* bs[] = {&w.edep, &w.edep2, &w.hi2, &w.lo2, &w.s1, &w.s2, &w.hi, &w.lo, &w.qph,
-                    &w.qel0, &w.qel1, &w.ctl, &w.prefix, &w.counters, &w.ledger, &w.status,
+                    &w.qel0, &w.qel1, &w.qsrc, &w.ctl, &w.prefix, &w.counters, &w.ledger, &w.status,
                     &w.edges, &w.beamlets, &w.bl_cdf, &w.bl_row, &w.bl_f, &w.al_cut,
                     &w.al_alias, &w.chains, &w.pick, &w.sub_first, &w.sub_inv, &w.sub_nbig,
                     &w.loop_k, &w.stage};
@@ -151,7 +151,7 @@ static void prof_collect(Runner& r, gdpm_stats* st) {
             continue;
         }
         const int k = r.prof_kind[i];
-        if (st && k >= 0 && k < 3) {
+        if (st && k >= 0 && k < 4) {
             st->kernel_ms[k] += ms;
             st->kernel_launches[k] += 1;
         }
@@ -248,6 +248,8 @@ void beamlet_tables_host(const std::vector<double>& rows17, BeamletHost& out, bo
         out.cut.assign(n, 1.0);
         out.alias.resize(n);
         for (int k = 0; k < n; ++k) out.alias[k] = k;
+        out.cdf_up.assign(n, 1.0f);
+        out.cut_t.assign(n, uint64_t(1) << 32);
         return;
     }
     out.cdf[n - 1] = 1.0;
@@ -271,6 +273,15 @@ void beamlet_tables_host(const std::vector<double>& rows17, BeamletHost& out, bo
         out.alias[l] = g;
         q[g] = (q[g] + q[l]) - 1.0;
         (q[g] < 1.0 ? small : large).push_back(g);
+    }
+    out.cdf_up.resize(n);
+    out.cut_t.resize(n);
+    for (int k = 0; k < n; ++k) {
+        float c = float(out.cdf[k]);
+        if (double(c) < out.cdf[k]) c = std::nextafter(c, 2.0f);
+        out.cdf_up[k] = c;
+        // (x + 1/2) 2^-32 < cut  <=>  x < ceil(cut 2^32 - 1/2); all exact in FP64
+        out.cut_t[k] = uint64_t(std::ceil(std::ldexp(out.cut[k], 32) - 0.5));
     }
 }
 
@@ -311,22 +322,22 @@ static int source_upload(Runner& r, const gdpm_source_state& s, DevSource& d, bo
     if (!bh.f.empty()) {
         const size_t nbl = bh.f.size();
         Workspace& w = r.ws;
-        if ((rc = ensure(w.beamlets, nbl * 64)) || (rc = ensure(w.bl_cdf, nbl * 8)) ||
+        if ((rc = ensure(w.beamlets, nbl * 64)) || (rc = ensure(w.bl_cdf, nbl * 4)) ||
             (rc = ensure(w.bl_row, nbl * 4)) || (rc = ensure(w.bl_f, nbl * 8)) ||
             (rc = ensure(w.al_cut, nbl * 8)) || (rc = ensure(w.al_alias, nbl * 4)))
             return rc;
         GDPM_CUDA_TRY(cudaMemcpyAsync(w.beamlets.p, bh.rows.data(), nbl * 64, cudaMemcpyHostToDevice, r.stream));
-        GDPM_CUDA_TRY(cudaMemcpyAsync(w.bl_cdf.p, bh.cdf.data(), nbl * 8, cudaMemcpyHostToDevice, r.stream));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(w.bl_cdf.p, bh.cdf_up.data(), nbl * 4, cudaMemcpyHostToDevice, r.stream));
         GDPM_CUDA_TRY(cudaMemcpyAsync(w.bl_row.p, bh.row.data(), nbl * 4, cudaMemcpyHostToDevice, r.stream));
         GDPM_CUDA_TRY(cudaMemcpyAsync(w.bl_f.p, bh.f.data(), nbl * 8, cudaMemcpyHostToDevice, r.stream));
-        GDPM_CUDA_TRY(cudaMemcpyAsync(w.al_cut.p, bh.cut.data(), nbl * 8, cudaMemcpyHostToDevice, r.stream));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(w.al_cut.p, bh.cut_t.data(), nbl * 8, cudaMemcpyHostToDevice, r.stream));
         GDPM_CUDA_TRY(cudaMemcpyAsync(w.al_alias.p, bh.alias.data(), nbl * 4, cudaMemcpyHostToDevice, r.stream));
         d.n_beamlets = int(nbl);
         d.beamlets = static_cast<const float*>(w.beamlets.p);
-        d.bl_cdf = static_cast<const double*>(w.bl_cdf.p);
+        d.bl_cdf = static_cast<const float*>(w.bl_cdf.p);
         d.bl_row = static_cast<const int*>(w.bl_row.p);
         d.bl_f = static_cast<const double*>(w.bl_f.p);
-        d.al_cut = static_cast<const double*>(w.al_cut.p);
+        d.al_cut = static_cast<const uint64_t*>(w.al_cut.p);
         d.al_alias = static_cast<const int*>(w.al_alias.p);
     }
     // the host vectors above are staged by the copies; make the copies
@@ -409,8 +420,8 @@ static bool side_by_side(gdpm_ctx* ctx, size_t V, uint64_t n_hist, int n_batches
 }
 
 // Work buffers for a phantom of V voxels and queues of `cap` particles.
-static int prepare_workspace(gdpm_ctx* ctx, Runner& r, size_t V, uint32_t cap, int n_batches, int n_bins,
-                             bool concurrent) {
+static int prepare_workspace(gdpm_ctx* ctx, Runner& r, size_t V, uint32_t cap, uint32_t chunk,
+                             int n_batches, int n_bins, bool concurrent) {
     Workspace& ws = r.ws;
     int rc;
     if ((rc = ensure(ws.s1, V * 8)) || (rc = ensure(ws.s2, V * 8))) return rc;
@@ -427,6 +438,9 @@ static int prepare_workspace(gdpm_ctx* ctx, Runner& r, size_t V, uint32_t cap, i
     const size_t qb = size_t(cap) * kQueueWords * 4;
     if ((rc = ensure(ws.qph, qb)) || (rc = ensure(ws.qel0, qb)) || (rc = ensure(ws.qel1, qb))) return rc;
     ws.cap_ph = ws.cap_el = cap;
+    // primaries of one phase: at most a chunk
+    if ((rc = ensure(ws.qsrc, size_t(chunk) * kQueueWords * 4))) return rc;
+    ws.cap_src = chunk;
     if ((rc = ensure(ws.ctl, size_t(ctx->max_phases + 4) * 16)) ||
         (rc = ensure(ws.prefix, size_t(n_batches) * (n_bins + 1) * 4)) ||
         (rc = ensure(ws.counters, C_NCOUNT * 8)) || (rc = ensure(ws.ledger, L_NLEDGER * 8)) ||
@@ -445,13 +459,15 @@ static int prepare_workspace(gdpm_ctx* ctx, Runner& r, size_t V, uint32_t cap, i
 static size_t bytes_needed(gdpm_ctx* ctx, const Runner& r, size_t V, uint64_t n_hist, int n_batches,
                            bool with_result) {
     const bool conc = side_by_side(ctx, V, n_hist, n_batches);
-    const uint32_t cap = capacity_of(ctx, chunk_of(ctx, conc ? n_hist : n_hist / n_batches + 1, 1, conc));
+    const uint32_t chunk = chunk_of(ctx, conc ? n_hist : n_hist / n_batches + 1, 1, conc);
+    const uint32_t cap = capacity_of(ctx, chunk);
     auto grow = [](const Buffer& b, size_t want) { return b.bytes >= want ? size_t(0) : want; };
     const Workspace& w = r.ws;
     size_t n = grow(w.s1, V * 8) + grow(w.s2, V * 8);
     n += conc ? grow(w.edep, V * size_t(n_batches) * 8) : grow(w.edep, V * 8) + grow(w.edep2, V * 8);
     const size_t qb = size_t(cap) * kQueueWords * 4;
     n += grow(w.qph, qb) + grow(w.qel0, qb) + grow(w.qel1, qb);
+    n += grow(w.qsrc, size_t(chunk) * kQueueWords * 4);
     if (with_result) n += V * 16;
     return n;
 }
@@ -474,9 +490,11 @@ static LoopArgs loop_args(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gd
     L.qph = make_queue(ws.qph, ws.cap_ph);
     L.qe0 = make_queue(ws.qel0, ws.cap_el);
     L.qe1 = make_queue(ws.qel1, ws.cap_el);
+    L.qsrc = make_queue(ws.qsrc, ws.cap_src);
     L.ctl = static_cast<uint32_t*>(ws.ctl.p);
     L.status = P.status;
     L.bin_prefix = static_cast<const uint32_t*>(ws.prefix.p);
+    L.prefix_n = ws.prefix_n;
     L.sub_first = sub_first;
     const bool metro = P.S.sampler == GDPM_SAMPLE_METROPOLIS && P.S.n_beamlets > 0 && n_sub == 0;
     L.chains = metro ? static_cast<uint32_t*>(ws.chains.p) : nullptr;
@@ -518,12 +536,14 @@ static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_s
         A.sub_batches = sub_batches;
         A.sub_first = sub_first;
         A.bin_prefix = static_cast<const uint32_t*>(ws.prefix.p);
+        A.prefix_n = ws.prefix_n;
         if (ph == photon_src && left > 0) {
             A.n_src = uint32_t(std::min<uint64_t>(left, chunk));
             A.src_first = uint32_t(next);
             next += A.n_src;
             left -= A.n_src;
-            if (P.S.sampler == GDPM_SAMPLE_METROPOLIS && P.S.n_beamlets > 0) {
+            const size_t ps = prof_begin(ctx, r, s, 3);
+            if (P.S.sampler == GDPM_SAMPLE_METROPOLIS && P.S.n_beamlets > 0 && n_sub == 0) {
                 // this phase's beamlets: advance the chains (Algorithm A1)
                 uint32_t* pick = static_cast<uint32_t*>(ws.pick.p);
                 const int rc = launch_metropolis(s, P, A.src_first, A.n_src,
@@ -532,6 +552,11 @@ static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_s
                 A.bl_pick = pick;
                 ++aux;
             }
+            // this phase's primaries, made before it runs
+            A.src = make_queue(ws.qsrc, ws.cap_src);
+            if (int rc = launch_sources(ctx, s, P, A)) return rc;
+            prof_end(ctx, r, s, ps);
+            ++aux;
         }
         A.head = ctl + size_t(k) * 4 + 0;
         if (ph) {
@@ -661,7 +686,7 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
     uint32_t chunk = conc ? chunk_of(ctx, n_hist, 1, true) : chunk_of(ctx, n_hist, n_batches, false);
     const uint32_t cap = capacity_of(ctx, chunk);
     const int n_bins = int(src.weights.size());
-    if ((rc = prepare_workspace(ctx, r, V, cap, n_batches, n_bins, conc))) return rc;
+    if ((rc = prepare_workspace(ctx, r, V, cap, chunk, n_batches, n_bins, conc))) return rc;
     Workspace& ws = r.ws;
     SimParams P = base_params(ctx, ph, tb, request_id);
     if ((rc = get_majorant(ctx, s, ph, tb, &P.maj))) return rc;
@@ -672,6 +697,7 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
         allot_prefix(src.weights, nb, &prefix[size_t(b) * (n_bins + 1)]);
     }
     GDPM_CUDA_TRY(cudaMemcpyAsync(ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, s));
+    ws.prefix_n = uint32_t(prefix.size());
     if ((rc = source_upload(r, src, P.S))) return rc;
     int64_t aux = 0;          // launches besides the transport phases
     if (P.S.sampler == GDPM_SAMPLE_METROPOLIS && P.S.n_beamlets > 0) {
@@ -1274,7 +1300,7 @@ int gdpm_simulate_beamlets(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb,
     const uint32_t chunk = chunk_of(ctx, total, 1, true);
     const uint32_t cap = capacity_of(ctx, chunk);
     const int n_bins = int(src.weights.size());
-    if ((rc = prepare_workspace(ctx, r, V, cap, int(slots), n_bins, true))) return rc;
+    if ((rc = prepare_workspace(ctx, r, V, cap, chunk, int(slots), n_bins, true))) return rc;
     Workspace& ws = r.ws;
     SimParams P = base_params(ctx, ph, tb, ctx->request_id);
     if ((rc = get_majorant(ctx, s, ph, tb, &P.maj))) return rc;
@@ -1296,6 +1322,7 @@ int gdpm_simulate_beamlets(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb,
         (rc = ensure(ws.sub_nbig, nbig.size() * 4)))
         return rc;
     GDPM_CUDA_TRY(cudaMemcpyAsync(ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, s));
+    ws.prefix_n = uint32_t(prefix.size());
     GDPM_CUDA_TRY(cudaMemcpyAsync(ws.sub_first.p, first.data(), first.size() * 4, cudaMemcpyHostToDevice, s));
     GDPM_CUDA_TRY(cudaMemcpyAsync(ws.sub_inv.p, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, s));
     GDPM_CUDA_TRY(cudaMemcpyAsync(ws.sub_nbig.p, nbig.data(), nbig.size() * 4, cudaMemcpyHostToDevice, s));

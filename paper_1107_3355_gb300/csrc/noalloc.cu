@@ -49,7 +49,8 @@ constexpr size_t kOffCut = kOffF + al(size_t(kNaMaxBeamlets) * 8);
 constexpr size_t kOffAlias = kOffCut + al(size_t(kNaMaxBeamlets) * 8);
 constexpr size_t kOffChains = kOffAlias + al(size_t(kNaMaxBeamlets) * 4);
 constexpr size_t kOffPick = kOffChains + al(size_t(kNaMaxChains) * 4);
-constexpr size_t kScratchBytes = kOffPick + al(size_t(kNaChunk) * 4);
+constexpr size_t kOffSrc = kOffPick + al(size_t(kNaChunk) * 4);
+constexpr size_t kScratchBytes = kOffSrc + al(size_t(kNaChunk) * kQueueWords * 4);
 static_assert(kScratchBytes == GDPM_NOALLOC_SCRATCH_BYTES, "header and layout disagree");
 
 // The scratch.  In host code `g_scratch` only names a host-side stand-in; its
@@ -178,23 +179,24 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     float* maj = reinterpret_cast<float*>(base + kOffMaj);
     float* edges = reinterpret_cast<float*>(base + kOffEdges);
     float* bl = reinterpret_cast<float*>(base + kOffBeamlets);
-    double* cdf = reinterpret_cast<double*>(base + kOffCdf);
+    float* cdf = reinterpret_cast<float*>(base + kOffCdf);
     int* bl_row = reinterpret_cast<int*>(base + kOffRow);
     double* bl_f = reinterpret_cast<double*>(base + kOffF);
-    double* al_cut = reinterpret_cast<double*>(base + kOffCut);
+    uint64_t* al_cut = reinterpret_cast<uint64_t*>(base + kOffCut);
     int* al_alias = reinterpret_cast<int*>(base + kOffAlias);
     uint32_t* chains = reinterpret_cast<uint32_t*>(base + kOffChains);
     uint32_t* pick = reinterpret_cast<uint32_t*>(base + kOffPick);
+    const Queue qsrc = queue_at(base + kOffSrc, kNaChunk);
 
     // source arrays and majorant into the scratch
     std::vector<float> ef(src.edges.begin(), src.edges.end());
     GDPM_CUDA_TRY(cudaMemcpyAsync(edges, ef.data(), ef.size() * 4, cudaMemcpyHostToDevice, s));
     if (n_bl > 0) {
         GDPM_CUDA_TRY(cudaMemcpyAsync(bl, bh.rows.data(), size_t(n_bl) * 64, cudaMemcpyHostToDevice, s));
-        GDPM_CUDA_TRY(cudaMemcpyAsync(cdf, bh.cdf.data(), size_t(n_bl) * 8, cudaMemcpyHostToDevice, s));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(cdf, bh.cdf_up.data(), size_t(n_bl) * 4, cudaMemcpyHostToDevice, s));
         GDPM_CUDA_TRY(cudaMemcpyAsync(bl_row, bh.row.data(), size_t(n_bl) * 4, cudaMemcpyHostToDevice, s));
         GDPM_CUDA_TRY(cudaMemcpyAsync(bl_f, bh.f.data(), size_t(n_bl) * 8, cudaMemcpyHostToDevice, s));
-        GDPM_CUDA_TRY(cudaMemcpyAsync(al_cut, bh.cut.data(), size_t(n_bl) * 8, cudaMemcpyHostToDevice, s));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(al_cut, bh.cut_t.data(), size_t(n_bl) * 8, cudaMemcpyHostToDevice, s));
         GDPM_CUDA_TRY(cudaMemcpyAsync(al_alias, bh.alias.data(), size_t(n_bl) * 4, cudaMemcpyHostToDevice, s));
     }
     if ((rc = launch_majorant_into(s, ph, tb, maj))) return rc;
@@ -285,6 +287,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
             A.nb_small = uint32_t(n_hist / n_batches);
             A.nb_rem = uint32_t(n_hist % n_batches);
             A.bin_prefix = prefix_d;
+            A.prefix_n = uint32_t(prefix.size());
             if (ph_phase == photon_src && left > 0) {
                 A.n_src = uint32_t(std::min<uint64_t>(left, chunk));
                 A.src_first = uint32_t(first + next);
@@ -295,6 +298,9 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
                     A.bl_pick = pick;
                     ++aux;
                 }
+                A.src = qsrc;
+                if ((run_rc = launch_sources(ctx, s, P, A))) break;
+                ++aux;
             }
             A.head = ctl + size_t(k) * 4;
             if (ph_phase) {

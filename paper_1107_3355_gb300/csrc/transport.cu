@@ -200,20 +200,20 @@ __device__ bool enter_box(const SimParams& P, Part& p) {
 // the phase; the alias method reads the Philox block at (h, 0, 0, 0); the
 // cumulative search uses the primary's own uniform rw.
 __device__ __forceinline__ int pick_beamlet(const DevSource& S, const PhaseArgs& A, uint32_t idx,
-                                            uint32_t h, float rw, uint32_t k0, uint32_t k1) {
+                                            uint32_t h, float rw, uint32_t k0, uint32_t k1,
+                                            const float* cdf) {
     if (S.sampler == GDPM_SAMPLE_METROPOLIS) return int(A.bl_pick[idx]);
     if (S.sampler == GDPM_SAMPLE_ALIAS) {
         const uint4 w = philox_block(h, 0u, 0u, 0u, k0, k1);
         const int J = int(__umulhi(w.x, uint32_t(S.n_beamlets)));
-        const double u = (double(w.y) + 0.5) * 0x1p-32;
-        return u < S.al_cut[J] ? J : S.al_alias[J];
+        return uint64_t(w.y) < S.al_cut[J] ? J : S.al_alias[J];   // u = (w.y + 1/2) 2^-32 < cut
     }
-    // the I with P(I) <= r < P(I+1)
-    const double rr = double(rw);
+    // the I with P(I) <= r < P(I+1) (rounded-up FP32 table: the same decisions
+    // as comparing double(r) with the FP64 cumulative weights)
     int l = 0, hi = S.n_beamlets - 1;
     while (l < hi) {
         const int mid = (l + hi) >> 1;
-        if (rr < S.bl_cdf[mid]) hi = mid; else l = mid + 1;
+        if (rw < cdf[mid]) hi = mid; else l = mid + 1;
     }
     return l;
 }
@@ -222,8 +222,11 @@ __device__ __forceinline__ int pick_beamlet(const DevSource& S, const PhaseArgs&
 // spectrum interval allotment (uniform inside the interval), position and
 // direction from the source geometry.  Draw 0 of the primary's stream:
 // (u-position, v-position, energy, beamlet).
+// prefix_tab / cdf_tab: copies of A.bin_prefix and S.bl_cdf (e.g. in shared
+// memory), or null to read the originals.
 __device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t idx, Part& p,
-                             Acc& acc) {
+                             Acc& acc, const uint32_t* prefix_tab = nullptr,
+                             const float* cdf_tab = nullptr) {
     const DevSource& S = P.S;
     const uint32_t h = A.src_first + idx;
     // a dose-matrix run: sub-problem k holds histories [sub_first[k],
@@ -254,7 +257,7 @@ __device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t id
         local = (hl - split) - (b - nb_rem) * nb_small;
     }
     const uint32_t slot = A.n_sub ? k * A.sub_batches + b : b;
-    const uint32_t* prefix = A.bin_prefix + size_t(slot) * (S.n_bins + 1);
+    const uint32_t* prefix = (prefix_tab ? prefix_tab : A.bin_prefix) + size_t(slot) * (S.n_bins + 1);
     p.hist = h;
     p.pidlo = 1u; p.pidhi = 0u; p.ctr = 0u;
     p.flags = (slot << kBatchShift) & kBatchMask;
@@ -276,7 +279,8 @@ __device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t id
             a0 = -S.half_u; a1 = S.half_u; b0 = -S.half_v; b1 = S.half_v;
         } else {
             // a dose-matrix sub-problem is its own beamlet; otherwise sample one
-            const int kb = A.n_sub ? int(k) : pick_beamlet(S, A, idx, h, r.w, P.key0, P.key1);
+            const int kb = A.n_sub ? int(k)
+                                   : pick_beamlet(S, A, idx, h, r.w, P.key0, P.key1, cdf_tab ? cdf_tab : S.bl_cdf);
             const float* row = S.beamlets + size_t(kb) * 16;
             src = row; cen = row + 3; au = row + 6; av = row + 9;
             a0 = row[12]; a1 = row[13]; b0 = row[14]; b1 = row[15];
@@ -855,14 +859,15 @@ __device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A
                 st_base += k;
                 st_left -= k;
             }
-            bool from_src = false, from_queue = false, missed = false;
+            bool from_queue = false;
             if (need) {
                 const uint32_t r = __popc(nm & lanemask_lt());
                 const uint32_t idx = r < left0 ? base0 + r : nb + (r - left0);
                 if (idx < A.n_src) {
-                    from_src = true;
-                    active = make_primary(P, A, idx, p, acc);
-                    missed = !active;
+                    // made by k_sources; a primary that missed the phantom
+                    // left its slot empty (E < 0) and is accounted there
+                    queue_load(A.src, idx, p);
+                    active = p.E >= 0.f;
                 } else if (idx < total) {
                     queue_load(A.in, idx - A.n_src, p);
                     // a slot reserved but never written holds E < 0
@@ -872,8 +877,7 @@ __device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A
                     exhausted = true;
                 }
             }
-            wc.w1 += __popc(__ballot_sync(kFull, from_src)) << 16;
-            wc.w2 += __popc(__ballot_sync(kFull, from_queue)) + (__popc(__ballot_sync(kFull, missed)) << 16);
+            wc.w2 += __popc(__ballot_sync(kFull, from_queue));
         }
         if (__all_sync(kFull, exhausted)) break;
         if (it >= P.max_iters) {
@@ -918,6 +922,78 @@ k_phase(const SimParams P, const PhaseArgs A) {
 }
 
 
+// ---------------------------------------------------------------- sources
+// The primaries of one source phase (Sec. 2.3), made with every lane busy
+// before the phase runs: primary idx goes to slot idx of A.src.  One that
+// misses the phantom leaves its slot empty (E < 0) and is accounted here:
+// source and escaped energy, a created and a terminated particle.
+// The spectrum prefix counts of the batches and the cumulative beamlet
+// weights are searched for every primary: a CTA copies them to shared
+// memory when they fit (n_prefix, n_cdf of them; see sources_smem).
+template <int PT>
+__device__ __forceinline__ void make_sources(const SimParams& P, const PhaseArgs& A, uint32_t n_prefix,
+                                             uint32_t n_cdf) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* s_cdf = reinterpret_cast<float*>(smem);
+    uint32_t* s_prefix = reinterpret_cast<uint32_t*>(smem + size_t(n_cdf) * 4);
+    for (uint32_t i = threadIdx.x; i < n_cdf; i += blockDim.x) s_cdf[i] = P.S.bl_cdf[i];
+    for (uint32_t i = threadIdx.x; i < n_prefix; i += blockDim.x) s_prefix[i] = A.bin_prefix[i];
+    __syncthreads();
+    const uint32_t* ptab = n_prefix ? s_prefix : nullptr;
+    const float* ctab = n_cdf ? s_cdf : nullptr;
+    Acc acc{0.0, 0.0, 0.0};
+    uint32_t made = 0u, missed = 0u;
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < A.n_src;
+         idx += gridDim.x * blockDim.x) {
+        Part p{};
+        if (make_primary(P, A, idx, p, acc, ptab, ctab)) {
+            queue_store(A.src, idx, p);
+        } else {
+            A.src.E[idx] = -1.f;
+            ++missed;
+        }
+        ++made;
+    }
+    made = __reduce_add_sync(kFull, made);
+    missed = __reduce_add_sync(kFull, missed);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.src += __shfl_down_sync(kFull, acc.src, o);
+        acc.esc += __shfl_down_sync(kFull, acc.esc, o);
+    }
+    if (lane_id() == 0) {
+        if (acc.src != 0.0) atomicAdd(&P.ledger[L_SOURCE], acc.src);
+        if (acc.esc != 0.0) atomicAdd(&P.ledger[L_ESCAPED], acc.esc);
+        if (made) {
+            atomicAdd(&P.counters[C_PRIMARY], (unsigned long long)made);
+            atomicAdd(&P.counters[PT == 0 ? C_PH_CREATED : C_EL_CREATED], (unsigned long long)made);
+        }
+        if (missed) atomicAdd(&P.counters[PT == 0 ? C_PH_TERMINATED : C_EL_TERMINATED], (unsigned long long)missed);
+    }
+}
+
+template <int PT>
+__global__ void __launch_bounds__(256) k_sources(const SimParams P, const PhaseArgs A, uint32_t n_prefix,
+                                                 uint32_t n_cdf) {
+    make_sources<PT>(P, A, n_prefix, n_cdf);
+}
+
+// Cumulative-weight entries the sources search (the cumulative sampler of a
+// sampled fluence map; none otherwise).
+inline uint32_t cdf_entries(const SimParams& P, const PhaseArgs& A) {
+    return (P.S.geometry == GDPM_GEO_BEAMLETS && P.S.sampler == GDPM_SAMPLE_CDF && A.n_sub == 0)
+               ? uint32_t(P.S.n_beamlets) : 0u;
+}
+
+// Entries of the prefix and cumulative-weight tables a source CTA stages in
+// shared memory (0: read from global memory), within a 40 KB budget.
+__host__ __device__ inline void sources_smem(uint32_t prefix_entries, uint32_t cdf_entries,
+                                             uint32_t& n_prefix, uint32_t& n_cdf) {
+    const size_t budget = 40u << 10;
+    n_cdf = size_t(cdf_entries) * 4 <= budget ? cdf_entries : 0u;
+    n_prefix = size_t(n_cdf) * 4 + size_t(prefix_entries) * 4 <= budget ? prefix_entries : 0u;
+}
+
 // ---------------------------------------------------------------- device-driven phase loop
 // Phase k's arguments from k alone, as the host loop sets them: photon
 // phase k (even) reads photons P[k] and banks electrons into E[k+1];
@@ -930,10 +1006,12 @@ __device__ __forceinline__ PhaseArgs phase_args(const LoopArgs& L, uint32_t k) {
     A.nb_small = L.nb_small;
     A.nb_rem = L.nb_rem;
     A.bin_prefix = L.bin_prefix;
+    A.prefix_n = L.prefix_n;
     A.n_sub = L.n_sub;
     A.sub_batches = L.sub_batches;
     A.sub_first = L.sub_first;
     A.bank_block = L.bank_block;
+    A.src = L.qsrc;
     const bool ph = (k % 2u) == 0u;
     const bool src_phase = ph == (L.src_particle == GDPM_PHOTON);
     if (src_phase) {
@@ -977,6 +1055,14 @@ k_phase_loop(const SimParams P, const LoopArgs L) {
     if (threadIdx.x == 0) sA = phase_args(L, *L.k + uint32_t(PT));
     __syncthreads();
     phase_run<PT>(P, sA);
+}
+
+// Primaries of this pass's source phase (before it runs).
+template <int PT>
+__global__ void __launch_bounds__(256) k_sources_loop(const SimParams P, const LoopArgs L, uint32_t n_prefix,
+                                                      uint32_t n_cdf) {
+    const PhaseArgs A = phase_args(L, *L.k + uint32_t(PT));
+    if (A.n_src) make_sources<PT>(P, A, n_prefix, n_cdf);
 }
 
 // Metropolis picks for this pass's source phase (before it runs).
@@ -1117,7 +1203,7 @@ __global__ void k_debug_beamlets(const SimParams P, uint32_t first, uint32_t n,
         const float4 r = draw(p, P.key0, P.key1);
         PhaseArgs A{};
         A.bl_pick = pick;
-        out[s] = P.S.bl_row[pick_beamlet(P.S, A, s, first + s, r.w, P.key0, P.key1)];
+        out[s] = P.S.bl_row[pick_beamlet(P.S, A, s, first + s, r.w, P.key0, P.key1, P.S.bl_cdf)];
     }
 }
 
@@ -1251,6 +1337,14 @@ int build_loop_graph(gdpm_ctx* ctx, const SimParams& P, LoopArgs& L, bool metrop
     LoopArgs Lc = L;
     void* phase_args_v[2] = {&Pc, &Lc};
     void* metro_args_v[2] = {&Pc, &Lc};
+    uint32_t np, nc;
+    {
+        PhaseArgs probe{};
+        probe.n_sub = L.n_sub;
+        sources_smem(L.prefix_n, cdf_entries(P, probe), np, nc);
+    }
+    const size_t src_sm = size_t(nc) * 4 + size_t(np) * 4;
+    void* src_args_v[4] = {&Pc, &Lc, &np, &nc};
     void* ctl_args_v[2] = {&Lc, &h};
     cudaGraphNode_t prev = nullptr;
     auto add = [&](const void* f, dim3 gd, dim3 bd, size_t sm, void** args) {
@@ -1267,6 +1361,12 @@ int build_loop_graph(gdpm_ctx* ctx, const SimParams& P, LoopArgs& L, bool metrop
     };
     if (metropolis)
         add((const void*)k_metropolis_loop, dim3((P.S.n_chains + 127) / 128), dim3(128), 0, metro_args_v);
+    {
+        const uint32_t sg = std::max(1u, std::min((L.chunk + 255u) / 256u, uint32_t(ctx->sm_count) * 8u));
+        const void* sf = L.src_particle == GDPM_PHOTON ? (const void*)k_sources_loop<0> : (const void*)k_sources_loop<1>;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(sf, cudaFuncAttributeMaxDynamicSharedMemorySize, int(src_sm));
+        add(sf, dim3(sg), dim3(256), src_sm, src_args_v);
+    }
     add(fn[0], dim3(grid[0]), dim3(ctx->block_threads), smem[0], phase_args_v);
     add(fn[1], dim3(grid[1]), dim3(ctx->block_threads), smem[1], phase_args_v);
     add((const void*)k_loop_ctl, dim3(1), dim3(1), 0, ctl_args_v);
@@ -1280,6 +1380,22 @@ int build_loop_graph(gdpm_ctx* ctx, const SimParams& P, LoopArgs& L, bool metrop
     }
     *graph = g;
     *exec = x;
+    return GDPM_OK;
+}
+
+int launch_sources(gdpm_ctx* ctx, cudaStream_t st, const SimParams& P, const PhaseArgs& A) {
+    const uint32_t grid = std::max(1u, std::min((A.n_src + 255u) / 256u, uint32_t(ctx->sm_count) * 8u));
+    uint32_t np, nc;
+    sources_smem(A.prefix_n, cdf_entries(P, A), np, nc);
+    const size_t sm = size_t(nc) * 4 + size_t(np) * 4;
+    if (P.S.particle == GDPM_PHOTON) {
+        GDPM_CUDA_TRY(cudaFuncSetAttribute(k_sources<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+        k_sources<0><<<grid, 256, sm, st>>>(P, A, np, nc);
+    } else {
+        GDPM_CUDA_TRY(cudaFuncSetAttribute(k_sources<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+        k_sources<1><<<grid, 256, sm, st>>>(P, A, np, nc);
+    }
+    GDPM_CUDA_TRY(cudaGetLastError());
     return GDPM_OK;
 }
 

@@ -82,7 +82,7 @@ class gdpm_stats(C.Structure):
                 [("pushes", C.c_int64 * 2), ("pops", C.c_int64 * 2), ("phases", C.c_int64),
                  ("launches", C.c_int64), ("dmax", C.c_double), ("sigma_over_dmax", C.c_double),
                  ("transport_ms", C.c_double), ("crossings", C.c_int64),
-                 ("kernel_ms", C.c_double * 3), ("kernel_launches", C.c_int64 * 3)])
+                 ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64 * 4)])
 
     def as_dict(self):
         d = {n: getattr(self, n) for n in _STAT_D1 + _STAT_I}
