@@ -412,8 +412,10 @@ struct ElSmem {
 // Straight segment of mass thickness `mass` through the voxel grid (3-D
 // DDA), depositing dpm MeV per g/cm2 in each voxel; with defer_last the
 // final piece is left to the caller.  True if the particle left the phantom.
+// rho_cur is the density of the particle's current voxel, known on entry
+// (no load before the first segment) and kept up to date on exit.
 __device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& dep, bool defer_last,
-                     uint32_t& crossings) {
+                     uint32_t& crossings, float& rho_cur) {
     if (!(mass > 0.f)) return false;
     const float iu = p.u != 0.f ? 1.f / p.u : 0.f;
     const float iv = p.v != 0.f ? 1.f / p.v : 0.f;
@@ -431,7 +433,7 @@ __device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& 
         else if (ty <= tz) { tb = ty; ab = 1; }
         else { tb = tz; ab = 2; }
         tb = fmaxf(tb, 0.f);
-        const float rho = __ldg(&P.rho[vox]);
+        const float rho = rho_cur;
         if (rho * tb >= left) {
             const float t = left / rho;
             p.x = fmaf(t, p.u, p.x);
@@ -467,6 +469,7 @@ __device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& 
             const uint32_t plane = uint32_t(P.nx) * uint32_t(P.ny);
             vox = sz > 0 ? vox + plane : vox - plane;
         }
+        rho_cur = __ldg(&P.rho[vox]);
     }
     atomicOr(P.status, ST_ITER_CAP);
     return true;
@@ -492,7 +495,10 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
         const float4 r = draw(p, P.key0, P.key1);
         ev.b += EV_STEP;
         hist_count(P, p.hist, 1);
-        const int m = __ldg(&P.mat[vox_of(P, p.ix, p.iy, p.iz)]);
+        // material and density of the start voxel, loaded together
+        const uint32_t vox0 = vox_of(P, p.ix, p.iy, p.iz);
+        const int m = __ldg(&P.mat[vox0]);
+        float rho_cur = __ldg(&P.rho[vox0]);
         int i;
         float f;
         grid_pos(T, p.E, i, f);
@@ -546,7 +552,7 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
         bool out = false;
 #pragma unroll 1
         for (int leg = 0; leg < 2; ++leg) {
-            out = walk(P, p, leg ? (1.f - r.y) * xs : r.y * xs, dpm, dep, leg == 1, ev.n);
+            out = walk(P, p, leg ? (1.f - r.y) * xs : r.y * xs, dpm, dep, leg == 1, ev.n, rho_cur);
             if (out || leg == 1) break;
             rotate(p.u, p.v, p.w, mu, cp, sp);
         }
