@@ -168,11 +168,12 @@ enum {
     GDPM_PARAM_CONCURRENT_MAX_HIST = 16, /* auto: side by side when histories per batch <= this
                                             (default 4e9, no limit) ... */
     GDPM_PARAM_CONCURRENT_MAX_MB = 17,   /* ... and the per-batch grids fit in this (default 16384) */
-    GDPM_PARAM_GRAPH = 18            /* 1 (default): batches side by side run their phases as one
+    GDPM_PARAM_GRAPH = 18            /* 1: batches side by side run their phases as one
                                         CUDA graph launch, a conditional WHILE node that repeats
                                         photon phase, electron phase and a control kernel on the
                                         device until nothing is left (no host checks); 0: the host
-                                        loop.  Profiling (GDPM_PARAM_PROFILE) uses the host loop. */
+                                        loop (default).  Profiling (GDPM_PARAM_PROFILE) uses the
+                                        host loop. */
 };
 
 /* ------------------------------------------------------------------ inputs */
