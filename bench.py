@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="throughput", choices=["throughput", "serve", "beamlets"])
     ap.add_argument("--matrix-beamlets", type=int, default=400)
+    ap.add_argument("--matrix-batches", type=int, default=2)
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-arc-histories", type=float, default=5e8)
@@ -267,13 +268,15 @@ def beamlet_matrix_bench(args):
     import torch
     from paper_1107_3355_gb300 import gdpm as G
 
-    prob = W.beamlet_matrix_problem(n_beamlets=args.matrix_beamlets, n_batches=1)
+    nb = args.matrix_batches
+    prob = W.beamlet_matrix_problem(n_beamlets=args.matrix_beamlets, n_batches=nb)
     K, V, total = len(prob.sub_histories), prob.phantom.n_voxels, prob.n_histories
     eng = G.Engine(prob, params={G.GDPM_PARAM_PROFILE: 1})
     dose = torch.empty((K, V), dtype=torch.float64, device="cuda")
+    sigma = torch.empty((K, V), dtype=torch.float64, device="cuda") if nb >= 2 else None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
-        G.gdpm_simulate_beamlets(eng.ctx, eng.phantom, eng.tables, prob.sub_histories, 1, dose)
+        G.gdpm_simulate_beamlets(eng.ctx, eng.phantom, eng.tables, prob.sub_histories, nb, dose, sigma)
     clocks = Clocks(0)
     torch.cuda.synchronize()
     clocks.start()
@@ -284,7 +287,7 @@ def beamlet_matrix_bench(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st = G.gdpm_simulate_beamlets(eng.ctx, eng.phantom, eng.tables, prob.sub_histories, 1, dose)
+        st = G.gdpm_simulate_beamlets(eng.ctx, eng.phantom, eng.tables, prob.sub_histories, nb, dose, sigma)
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
@@ -308,7 +311,8 @@ def beamlet_matrix_bench(args):
             "ms_per_step": float(np.median(ms)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "slab128_beamlet_matrix", "beamlets": K, "histories": total,
-                       "tally": "one FP64 grid per beamlet (%.1f GB)" % (K * V * 8 / 1e9),
+                       "batches": nb, "outputs": "dose and sigma per beamlet" if nb >= 2 else "dose per beamlet",
+                       "tally": "%d FP64 grids per beamlet (%.1f GB)" % (nb, nb * K * V * 8 / 1e9),
                        "l2": "flushed between steps (256 MB write)"},
             "one_beamlet_at_a_time": {"value": serial, "unit": "histories/s",
                                       "calls": K, "batches_per_call": 2},
