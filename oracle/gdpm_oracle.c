@@ -22,6 +22,8 @@
  *   - Sec. 2.3.2: the spectrum split into equal energy intervals, histories
  *     of a batch allotted to intervals by spectrum weight, energy uniform
  *     inside an interval.
+ *   - Sec. 4 (physics variants): with ORC_SAUTER the photoelectron leaves at an
+ *     angle from Sauter's K-shell distribution instead of along the photon.
  *   - Sec. 3.1: absorption energies (electron 200 keV, photon 50 keV);
  *     sigma/Dmax over D > 0.5 Dmax.
  * The paper defers every physics formula to DPM and states none.  The
@@ -56,6 +58,7 @@
 
 enum { ORC_SAMPLE_CDF = 0, ORC_SAMPLE_ALIAS = 1, ORC_SAMPLE_METROPOLIS = 2 };
 
+#define ORC_SAUTER 8               /* photoelectron direction from Sauter's distribution */
 #define ORC_NO_ANNIHILATION 1
 #define ORC_COMPTON_ONLY 2
 #define ORC_NO_HARD 4
@@ -536,6 +539,40 @@ static void rotate(double u[3], double cost, double phi)
     for (int a = 0; a < 3; a++) u[a] = n[a] / l;
 }
 
+/* READING (physics variant): Sauter's K-shell photoelectron distribution in
+ * mu = cos(theta) for a photoelectron of kinetic energy T (binding energy
+ * neglected, as for the photoelectric product above), gamma = 1 + T/mc2,
+ * beta = sqrt(1 - 1/gamma^2):
+ *   p(mu) ~ (1 - mu^2) / (1 - beta mu)^4 * [1 + b (1 - beta mu)],
+ *   b = gamma (gamma - 1) (gamma - 2) / 2.
+ * Sampling: propose mu from q(mu) ~ 1/(1 - beta mu)^2 on [-1, 1] by inverting
+ * its distribution, 1/(1 - beta mu) = 1/(1 + beta) + xi 2 beta/(1 - beta^2),
+ * and accept with (1 - mu^2)(1 - beta^2)/(1 - beta mu)^2 * g(mu)/g_max, where
+ * g = 1 + b (1 - beta mu) and g_max its largest value on [-1, 1] (both
+ * factors are at most 1).  Draws per trial: (proposal, accept, phi, -). */
+static void sample_sauter(orc_sim *S, orc_particle *p, double T, double *mu, double *phi)
+{
+    double g = 1.0 + T / MC2;
+    double beta = sqrt(fmax(0.0, 1.0 - 1.0 / (g * g)));
+    double b = 0.5 * g * (g - 1.0) * (g - 2.0);
+    double gmax = b >= 0 ? 1.0 + b * (1.0 + beta) : 1.0 + b * (1.0 - beta);
+    double c[4];
+    *mu = 0.0;
+    *phi = 0.0;
+    for (int it = 0; it < 4096; it++) {
+        draw4(S, p, c);
+        double x = 1.0 / (1.0 + beta) + c[0] * 2.0 * beta / (1.0 - beta * beta);
+        double m = (1.0 - 1.0 / x) / beta;
+        if (m > 1.0) m = 1.0;
+        if (m < -1.0) m = -1.0;
+        double d = 1.0 - beta * m;
+        double w = (1.0 - m * m) * (1.0 - beta * beta) / (d * d) * (1.0 + b * d) / gmax;
+        *mu = m;
+        *phi = 2.0 * PI * c[2];
+        if (c[1] < w) break;
+    }
+}
+
 /* Move a primary from outside onto the phantom surface.  Returns 0 if the
  * ray misses.  The entry coordinate is set exactly on the face. */
 static int enter_box(const orc_problem *P, double x[3], const double u[3])
@@ -685,7 +722,13 @@ static void photon_track(orc_sim *S, orc_particle *p)
             compton(S, p, &alive);
         } else if (r < muc + mupe) {
             S->res->photoelectric++;
-            bank(S, p, PT_ELECTRON, p->E, p->x, p->u, p->iv);
+            double d[3] = {p->u[0], p->u[1], p->u[2]};
+            if (P->flags & ORC_SAUTER) {
+                double mu, phi;
+                sample_sauter(S, p, p->E, &mu, &phi);
+                rotate(d, mu, phi);
+            }
+            bank(S, p, PT_ELECTRON, p->E, p->x, d, p->iv);
             S->res->ph_terminated++;
             alive = 0;
         } else {
@@ -1272,7 +1315,7 @@ int orc_table_lookup(const orc_problem *P, int m, int which, const double *x, do
 
 /* Draw n samples from one of the interaction samplers, each sample from its
  * own Philox stream (history = sample index, particle id 1). */
-enum { OS_KN = 0, OS_MOLLER, OS_BREMS, OS_SR, OS_ISO };
+enum { OS_KN = 0, OS_MOLLER, OS_BREMS, OS_SR, OS_ISO, OS_SAUTER };
 int orc_sample(int which, double a, double b, long long n, unsigned long long seed,
                double *out1, double *out2)
 {
@@ -1323,6 +1366,11 @@ int orc_sample(int which, double a, double b, long long n, unsigned long long se
             double v[4];
             draw4(&S, &p, v);
             out1[s] = b * pow(a / b, v[2]);
+        } else if (which == OS_SAUTER) {
+            double mu, phi;
+            sample_sauter(&S, &p, a, &mu, &phi);
+            out1[s] = mu;
+            if (out2) out2[s] = phi;
         } else if (which == OS_SR) {
             double u[4];
             draw4(&S, &p, u);

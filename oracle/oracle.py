@@ -30,7 +30,7 @@ HD_ESCAPED, HD_EL_MASSPATH, HD_ND = 0, 1, 2
 # orc_table_lookup ids
 OT_MU_C, OT_MU_PE, OT_MU_PAIR, OT_SIG_M, OT_SIG_B, OT_RANGE, OT_RANGE_INV, OT_MUMAX = range(8)
 # orc_sample ids
-OS_KN, OS_MOLLER, OS_BREMS, OS_SR, OS_ISO = range(5)
+OS_KN, OS_MOLLER, OS_BREMS, OS_SR, OS_ISO, OS_SAUTER = range(6)
 
 
 class OrcMaterial(C.Structure):

@@ -37,7 +37,8 @@ import numpy as np
 # ---------------------------------------------------------------------------
 
 _ATOMIC_WEIGHT = {1: 1.008, 6: 12.011, 7: 14.007, 8: 15.999, 11: 22.990,
-                  12: 24.305, 15: 30.974, 16: 32.06, 18: 39.948, 20: 40.078}
+                  12: 24.305, 15: 30.974, 16: 32.06, 17: 35.45, 18: 39.948, 19: 39.098,
+                  20: 40.078}
 
 
 @dataclasses.dataclass(frozen=True)
@@ -57,6 +58,10 @@ def _mat(name, rho, I_eV, zw):
 WATER = _mat("water", 1.0, 75.0, [(1, 0.111894), (8, 0.888106)])
 # Lung read as low-density water (same composition, 0.26 g/cm3).
 LUNG = _mat("lung", 0.26, 75.0, [(1, 0.111894), (8, 0.888106)])
+# ICRU Report 44 lung tissue (composition by mass), inflated to 0.26 g/cm3
+LUNG_ICRU = _mat("lung_icru", 0.26, 75.3, [(1, 0.103), (6, 0.105), (7, 0.031), (8, 0.749),
+                                           (11, 0.002), (15, 0.002), (16, 0.003), (17, 0.003),
+                                           (19, 0.002)])
 # Cortical bone, ICRU-44-like composition.
 BONE = _mat("bone", 1.85, 106.4, [(1, 0.034), (6, 0.155), (7, 0.042), (8, 0.435),
                                   (11, 0.001), (12, 0.002), (15, 0.103), (16, 0.003),
@@ -379,6 +384,7 @@ def ct_imrt_problem(n_histories=250_000_000, n_batches=100, shape=(256, 256, 128
 FLAG_NO_ANNIHILATION = 1     # positrons end without annihilation photons (paper Sec. 4)
 FLAG_COMPTON_ONLY = 2        # photoelectric and pair cross sections set to zero
 FLAG_NO_HARD = 4             # no hard Moller / bremsstrahlung events for electrons
+FLAG_SAUTER = 8              # photoelectrons leave at Sauter's K-shell angle (physics variant)
 
 
 @dataclasses.dataclass
