@@ -82,6 +82,8 @@ enum { GDPM_SAMPLE_CDF = 0, GDPM_SAMPLE_ALIAS = 1, GDPM_SAMPLE_METROPOLIS = 2 };
 /* Table/transport flags (gdpm_tables_build). */
 #define GDPM_FLAG_COMPTON_ONLY 2   /* zero photoelectric and pair cross sections */
 #define GDPM_FLAG_NO_HARD 4        /* no hard Moller/bremsstrahlung events */
+#define GDPM_FLAG_SAUTER 8         /* photoelectrons leave at an angle from Sauter's K-shell
+                                      distribution (physics variant; default: along the photon) */
 
 /* Source description (Sec. 2.3): particle, energy spectrum, geometry.
  *   GDPM_GEO_PENCIL: all primaries start at `origin` along `direction`.
@@ -195,7 +197,7 @@ int gdpm_phantom_destroy(gdpm_phantom *ph);
  * screening parameter.  The absorption energies are also the hard-event
  * thresholds (W_cc = eabs_electron, W_cb = eabs_photon).  `ms_loss` is the
  * CSDA energy fraction that limits one multiple-scattering step; `flags`
- * takes GDPM_FLAG_COMPTON_ONLY / GDPM_FLAG_NO_HARD.
+ * takes GDPM_FLAG_COMPTON_ONLY / GDPM_FLAG_NO_HARD / GDPM_FLAG_SAUTER.
  * Errors: GDPM_E_ARG (n_mats outside 1..8, n_energy < 16, bad energies). */
 int gdpm_tables_build(gdpm_ctx *ctx, const gdpm_material_desc *mats, int n_mats,
                       double e_min, double e_max, int n_energy, double eabs_photon,
@@ -317,6 +319,7 @@ int gdpm_debug_philox(gdpm_ctx *ctx, const uint32_t *ctr, uint32_t k0, uint32_t 
  *   kind 2 bremsstrahlung at T = a, W_cb = b: out1 = k
  *   kind 3 screened Rutherford with screening a: out1 = mu
  *   kind 4 isotropic: out1 = cos(theta), out2 = phi
+ *   kind 5 Sauter photoelectron of kinetic energy a: out1 = cos(theta), out2 = phi
  * out1/out2: device arrays of n doubles (out2 may be NULL). */
 int gdpm_debug_sample(gdpm_ctx *ctx, int kind, double a, double b, uint64_t n,
                       uint64_t seed, double *out1, double *out2);

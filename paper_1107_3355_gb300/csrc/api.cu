@@ -1133,7 +1133,7 @@ int gdpm_tables_build(gdpm_ctx* ctx, const gdpm_material_desc* mats, int n_mats,
     if (!(eabs_photon >= e_min) || !(eabs_electron >= e_min / 0.5) || eabs_electron >= e_max ||
         eabs_photon >= e_max || !(ms_loss > 0 && ms_loss < 0.9))
         return GDPM_E_ARG;
-    if (flags & ~(GDPM_FLAG_COMPTON_ONLY | GDPM_FLAG_NO_HARD)) return GDPM_E_ARG;
+    if (flags & ~(GDPM_FLAG_COMPTON_ONLY | GDPM_FLAG_NO_HARD | GDPM_FLAG_SAUTER)) return GDPM_E_ARG;
     for (int m = 0; m < n_mats; ++m) {
         const gdpm_material_desc& d = mats[m];
         if (d.n_elements < 1 || d.n_elements > GDPM_MAX_ELEMENTS || !(d.mean_excitation_MeV > 0))
@@ -1429,8 +1429,9 @@ int gdpm_debug_philox(gdpm_ctx* ctx, const uint32_t* ctr, uint32_t k0, uint32_t 
 
 int gdpm_debug_sample(gdpm_ctx* ctx, int kind, double a, double b, uint64_t n, uint64_t seed,
                       double* out1, double* out2) {
-    if (!ctx || !out1 || kind < 0 || kind > 4 || !is_device_ptr(out1) || (out2 && !is_device_ptr(out2)))
+    if (!ctx || !out1 || kind < 0 || kind > 5 || !is_device_ptr(out1) || (out2 && !is_device_ptr(out2)))
         return GDPM_E_ARG;
+    if (kind == 5 && !(a > 0)) return GDPM_E_ARG;
     if (kind == 1 && !(a > 2 * b && b > 0)) return GDPM_E_ARG;
     if (kind == 2 && !(a > b && b > 0)) return GDPM_E_ARG;
     if (kind == 0 && !(a > 0)) return GDPM_E_ARG;

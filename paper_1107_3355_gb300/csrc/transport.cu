@@ -143,6 +143,33 @@ __device__ __forceinline__ void sample_moller(Part& p, const SimParams& P, float
     }
 }
 
+// Sauter's K-shell photoelectron distribution (physics variant) in
+// mu = cos(theta), for kinetic energy T: p(mu) ~ (1-mu^2)/(1-beta mu)^4
+// [1 + b (1 - beta mu)], b = gamma(gamma-1)(gamma-2)/2.  Proposal
+// q(mu) ~ 1/(1 - beta mu)^2 by inversion, 1/(1 - beta mu) = 1/(1+beta) +
+// xi 2beta/(1-beta^2); accepted with (1-mu^2)(1-beta^2)/(1-beta mu)^2 times
+// g/g_max.  Draws per trial: (proposal, accept, phi, -).
+__device__ __forceinline__ void sample_sauter(Part& p, const SimParams& P, float T, float& mu,
+                                              float& rphi) {
+    const float g = 1.f + T * (1.f / kMC2f);
+    const float beta = sqrtf(fmaxf(0.f, 1.f - 1.f / (g * g)));
+    const float b = 0.5f * g * (g - 1.f) * (g - 2.f);
+    const float gmax = b >= 0.f ? 1.f + b * (1.f + beta) : 1.f + b * (1.f - beta);
+    const float ib = 1.f / (1.f + beta), sc = 2.f * beta / (1.f - beta * beta);
+    mu = 0.f;
+    rphi = 0.f;
+    for (int it = 0; it < 4096; ++it) {
+        const float4 c = draw(p, P.key0, P.key1);
+        const float x = ib + c.x * sc;
+        const float m = fminf(fmaxf((1.f - 1.f / x) / beta, -1.f), 1.f);
+        const float d = 1.f - beta * m;
+        const float w = (1.f - m * m) * (1.f - beta * beta) / (d * d) * (1.f + b * d) / gmax;
+        mu = m;
+        rphi = c.z;
+        if (c.y < w) break;
+    }
+}
+
 // Screening parameter A for first moment G1 (table in ln G1; asymptote
 // 1/A = 3d(1 + 3d/2), d = 1 - G1, near isotropy).
 __device__ __forceinline__ float screening_A(const DevTables& T, const float* atab, float G1) {
@@ -383,12 +410,19 @@ __device__ void photon_step(const SimParams& P, const PhSmem& S, Part& p, bool& 
             p.E = Ep;
         }
     } else if (rr < lerpf(c0.y, c1.y, f)) {
-        // photoelectric: photon absorbed, photoelectron along the photon
+        // photoelectric: photon absorbed, photoelectron along the photon (or
+        // at Sauter's angle to it, physics variant)
         ev.a += EV_PHOTO;
         ev.b += EV_TERM;
         sec.E1 = p.E;
         sec.pos2 = false;
         active = false;
+        if (T.flags & GDPM_FLAG_SAUTER) {
+            float mu, rphi, cp, sp;
+            sample_sauter(p, P, p.E, mu, rphi);
+            cossin_2pi(rphi, cp, sp);
+            rotate(sec.dx, sec.dy, sec.dz, mu, cp, sp);
+        }
     } else {
         // pair: electron takes r.w of the kinetic energy, positron the rest
         ev.a += EV_PAIR;
@@ -1152,6 +1186,11 @@ __global__ void k_debug_sample(int kind, float a, float b, uint64_t n, uint32_t 
         } else if (kind == 3) {
             const float4 r = draw(p, k0, k1);
             o1 = 1.f - 2.f * a * r.z / (1.f - r.z + a);
+        } else if (kind == 5) {
+            float mu, rphi;
+            sample_sauter(p, P, a, mu, rphi);
+            o1 = mu;
+            o2 = kTwoPi * rphi;
         } else {
             const float4 r = draw(p, k0, k1);
             o1 = 2.f * r.x - 1.f;

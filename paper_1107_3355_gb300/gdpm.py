@@ -22,7 +22,7 @@ GDPM_E_ARG, GDPM_E_NOMEM, GDPM_E_QUEUE_OVERFLOW, GDPM_E_TIMEOUT = -1, -2, -3, -4
 GDPM_E_CUDA, GDPM_E_STATE, GDPM_E_BUSY = -5, -6, -7
 GDPM_PHOTON, GDPM_ELECTRON = 0, 1
 GDPM_GEO_PENCIL, GDPM_GEO_POINT_FIELD, GDPM_GEO_BEAMLETS = 0, 1, 2
-GDPM_FLAG_COMPTON_ONLY, GDPM_FLAG_NO_HARD = 2, 4
+GDPM_FLAG_COMPTON_ONLY, GDPM_FLAG_NO_HARD, GDPM_FLAG_SAUTER = 2, 4, 8
 GDPM_PARAM_QUEUE_CAPACITY = 1
 GDPM_PARAM_BLOCK_THREADS = 2
 GDPM_PARAM_BLOCKS_PER_SM = 3
@@ -392,7 +392,8 @@ class Engine:
         self.tables = gdpm_tables_build(self.ctx, ph.materials, prob.e_min, prob.e_max,
                                         prob.n_energy, prob.eabs_photon, prob.eabs_electron,
                                         prob.ms_loss_fraction,
-                                        prob.flags & (GDPM_FLAG_COMPTON_ONLY | GDPM_FLAG_NO_HARD))
+                                        prob.flags & (GDPM_FLAG_COMPTON_ONLY | GDPM_FLAG_NO_HARD |
+                                                      GDPM_FLAG_SAUTER))
         src = prob.source
         if prob.flags & W.FLAG_NO_ANNIHILATION and src.annihilation:
             import dataclasses

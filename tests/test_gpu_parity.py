@@ -132,7 +132,8 @@ def test_tables_match_oracle():
 # --------------------------------------------------------------------- samplers
 
 @pytest.mark.parametrize("kind,a,b", [(0, 0.1, 0), (0, 1.0, 0), (0, 6.0, 0), (1, 1.0, 0.2),
-                                      (1, 15.0, 0.2), (2, 5.0, 0.05), (3, 0.01, 0), (4, 0, 0)])
+                                      (1, 15.0, 0.2), (2, 5.0, 0.05), (3, 0.01, 0), (4, 0, 0),
+                                      (5, 0.02, 0), (5, 0.6, 0), (5, 3.0, 0)])
 def test_samplers_elementwise(kind, a, b):
     """Same Philox streams: the GPU sampler (FP32) reproduces the oracle's
     (FP64) sample by sample, except where a rejection test flips."""
@@ -142,7 +143,8 @@ def test_samplers_elementwise(kind, a, b):
         o1, o2 = cuda_f64(n), cuda_f64(n)
         G.gdpm_debug_sample(ctx, kind, a, b, n, 777, o1, o2)
         g1 = o1.cpu().numpy()
-        oracle_kind = {0: O.OS_KN, 1: O.OS_MOLLER, 2: O.OS_BREMS, 3: O.OS_SR, 4: O.OS_ISO}[kind]
+        oracle_kind = {0: O.OS_KN, 1: O.OS_MOLLER, 2: O.OS_BREMS, 3: O.OS_SR, 4: O.OS_ISO,
+                       5: O.OS_SAUTER}[kind]
         r1, _ = O.sample(oracle_kind, a, b, n, seed=777)
         # inputs differ by < 2^-23 (23-bit vs 32-bit uniforms) plus FP32 rounding
         match = np.abs(g1 - r1) <= 2e-5 + 1e-4 * np.abs(r1)
@@ -375,3 +377,38 @@ def test_ct_imrt_beamlets_same_seed(sampler):
     r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
     print("ct imrt t-test", r)
     assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97
+
+
+# --------------------------------------------------------------------- physics variants
+
+def test_sauter_variant_same_seed():
+    """Low-energy photons with transported photoelectrons: with the Sauter
+    variant on both sides the runs agree history by history."""
+    ph = W.homogeneous_phantom((16, 16, 16), (0.2, 0.2, 0.2), W.WATER, 1.0)
+    prob = W.Problem(ph, W.pencil_source(ph, 0.08), 50_000, 10, eabs_photon=0.005,
+                     eabs_electron=0.01, e_min=0.002, e_max=0.1, flags=W.FLAG_SAUTER)
+    d_o, s_o, led_o, rec_o, _ = O.run(prob, per_history=True)
+    d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
+    check_ledger(st, prob.n_histories, 1e-5)
+    assert st["photoelectric"] == pytest.approx(led_o["photoelectric"], rel=1e-3)
+    same = np.all(rec_o == rec_g, axis=1)
+    print("sauter identical records: %.5f" % same.mean())
+    assert same.mean() > 0.99
+    r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
+    assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97, r
+
+
+def test_icru_lung_slab_same_seed():
+    ph = W.slab_phantom((32, 32, 64), (0.5, 0.5, 0.5),
+                        layers=((3.0, W.WATER, 1.0), (10.0, W.LUNG_ICRU, 0.26),
+                                (12.0, W.BONE, 1.85), (1e30, W.WATER, 1.0)))
+    prob = W.Problem(ph, W.field_source(ph, W.kramers_spectrum()), 30_000, 10,
+                     eabs_photon=0.05, eabs_electron=0.2, e_min=0.005, e_max=6.5)
+    d_o, s_o, _, rec_o, _ = O.run(prob, per_history=True)
+    d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
+    check_ledger(st, prob.n_histories, 1e-5)
+    same = np.all(rec_o == rec_g, axis=1)
+    print("icru lung identical records: %.5f" % same.mean())
+    assert same.mean() > 0.99
+    r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
+    assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97, r
