@@ -223,6 +223,27 @@ int gdpm_source_set(gdpm_ctx *ctx, const gdpm_source_desc *src);
 int gdpm_simulate(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
                   int n_batches, double *dose_out, double *sigma_out, gdpm_stats *stats_out);
 
+/* Checkpoint / resume.  The state of a run is the per-voxel sums over its
+ * finished batches, sum1 = sum_b x_b and sum2 = sum_b x_b^2 with x_b the
+ * energy per history of batch b (Sec. 2.2.1), plus the index of the next
+ * batch.  gdpm_simulate_part runs batches [first_batch, first_batch +
+ * n_part) of the n_histories / n_batches calculation (at most 128 at a time)
+ * and ADDS their x_b and x_b^2 into sum1, sum2 (nx*ny*nz doubles each, host
+ * or device, caller-owned; zero them before the first part).  Histories
+ * keep their ids in the whole calculation, so the parts can run in any
+ * grouping, in separate processes, and the sums equal those of one
+ * uninterrupted run up to the order of FP64 additions.  gdpm_finalize turns
+ * the sums of all n_batches batches into dose and sigma (as gdpm_simulate,
+ * MeV/g per history; host or device outputs, either may be NULL) and
+ * reports Dmax and sigma/Dmax in stats_out.
+ * Errors: as gdpm_simulate; GDPM_E_ARG for a batch range outside
+ * [0, n_batches) or n_part > 128. */
+int gdpm_simulate_part(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
+                       int n_batches, int first_batch, int n_part, double *sum1, double *sum2,
+                       gdpm_stats *stats_out);
+int gdpm_finalize(gdpm_ctx *ctx, gdpm_phantom *ph, int n_batches, const double *sum1,
+                  const double *sum2, double *dose_out, double *sigma_out, gdpm_stats *stats_out);
+
 /* Beamlet dose matrix: every row k of the current source's fluence map
  * (GDPM_GEO_BEAMLETS; its weight is ignored) is a calculation of its own --
  * the beamlet's rectangle as the field of a point source, n_histories[k]

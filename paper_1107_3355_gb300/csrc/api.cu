@@ -515,6 +515,7 @@ static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_s
                       uint64_t first, uint64_t n, uint32_t nb_small, uint32_t nb_rem, uint32_t chunk,
                       int64_t& phases, int64_t& aux, uint32_t n_sub = 0, uint32_t sub_batches = 0,
                       const uint32_t* sub_first = nullptr) {
+    Range range("transport phases");
     Workspace& ws = r.ws;
     cudaStream_t s = r.stream;
     uint32_t* ctl = static_cast<uint32_t*>(ws.ctl.p);
@@ -677,6 +678,7 @@ static void fill_stats(const unsigned long long* c, const double* l, gdpm_stats*
 int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
                   const gdpm_source_state& src, uint32_t request_id, uint64_t n_hist, int n_batches,
                   double* dose_out, double* sigma_out, gdpm_stats* st, int32_t* hrec, double* hrecd) {
+    Range range("gdpm_simulate");
     int rc = validate_run(ctx, ph, tb, src, n_hist, n_batches);
     if (rc) return rc;
     cudaStream_t s = r.stream;
@@ -874,6 +876,7 @@ static void serve_worker(gdpm_ctx* ctx, int slot_class) {
     r.serving = true;
     for (;;) {
         gdpm_request* q = nullptr;
+        bool refused = false;
         {
             std::unique_lock<std::mutex> lk(ctx->mu);
             for (;;) {
@@ -894,6 +897,14 @@ static void serve_worker(gdpm_ctx* ctx, int slot_class) {
                 const size_t need = bytes_needed(ctx, r, V, front->desc.n_histories, front->desc.n_batches, true);
                 size_t free_b = 0, total_b = 0;
                 if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) cudaGetLastError();
+                if (total_b > 0 && need + ctx->serve_reserve > total_b) {
+                    // larger than the device can ever hold with the reserve: refuse
+                    ctx->pending.erase(it);
+                    q = front;
+                    refused = true;
+                    ++ctx->running;
+                    break;
+                }
                 if (ctx->running > 0 && free_b < need + ctx->serve_reserve) {
                     // not admitted yet: wait for a running request to finish
                     ctx->cv.wait_for(lk, std::chrono::milliseconds(2));
@@ -906,7 +917,7 @@ static void serve_worker(gdpm_ctx* ctx, int slot_class) {
             }
             if (ctx->stop) break;
         }
-        int rc = init_rc;
+        int rc = refused ? GDPM_E_NOMEM : init_rc;
         if (rc == GDPM_OK) {
             const gdpm_phantom* ph = q->desc.phantom;
             const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
@@ -1204,6 +1215,167 @@ int gdpm_simulate(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_h
                          dose_out, sigma_out, stats_out, ctx->hrec, ctx->hrecd);
 }
 
+int gdpm_simulate_part(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_histories,
+                       int n_batches, int first_batch, int n_part, double* sum1, double* sum2,
+                       gdpm_stats* st) {
+    if (!ctx || !sum1 || !sum2) return GDPM_E_ARG;
+    Range range("gdpm_simulate_part");
+    const gdpm_source_state& src = ctx->src;
+    int rc = validate_run(ctx, ph, tb, src, n_histories, n_batches);
+    if (rc) return rc;
+    if (first_batch < 0 || n_part < 1 || first_batch + n_part > n_batches || n_part > kMaxConcurrentBatches)
+        return GDPM_E_ARG;
+    GDPM_CUDA_TRY(cudaSetDevice(ctx->device));
+    Runner& r = ctx->run;
+    cudaStream_t s = r.stream;
+    const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
+    const uint32_t nb_small = uint32_t(n_histories / n_batches), nb_rem = uint32_t(n_histories % n_batches);
+    // batch b holds histories [h(b), h(b+1)), h(b) = b nb_small + min(b, nb_rem)
+    auto hb = [&](uint64_t b) { return b * nb_small + std::min<uint64_t>(b, nb_rem); };
+    const uint64_t h0 = hb(uint64_t(first_batch)), h1 = hb(uint64_t(first_batch + n_part));
+    const uint32_t chunk = chunk_of(ctx, h1 - h0, 1, true);
+    const uint32_t cap = capacity_of(ctx, chunk);
+    const int n_bins = int(src.weights.size());
+    if ((rc = prepare_workspace(ctx, r, V, cap, chunk, n_part, n_bins, true))) return rc;
+    Workspace& ws = r.ws;
+    SimParams P = base_params(ctx, ph, tb, ctx->request_id);
+    if ((rc = get_majorant(ctx, s, ph, tb, &P.maj))) return rc;
+    // spectrum allotment of every batch of the whole calculation (the
+    // primaries find theirs by their global history id)
+    std::vector<uint32_t> prefix(size_t(n_batches) * (n_bins + 1));
+    for (int b = 0; b < n_batches; ++b)
+        allot_prefix(src.weights, hb(b + 1) - hb(b), &prefix[size_t(b) * (n_bins + 1)]);
+    if ((rc = ensure(ws.prefix, prefix.size() * 4))) return rc;
+    GDPM_CUDA_TRY(cudaMemcpyAsync(ws.prefix.p, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, s));
+    ws.prefix_n = uint32_t(prefix.size());
+    if ((rc = source_upload(r, src, P.S))) return rc;
+    int64_t aux = 0;
+    if (P.S.sampler == GDPM_SAMPLE_METROPOLIS && P.S.n_beamlets > 0) {
+        // the chains run from their start through the histories before h0
+        if ((rc = ensure(ws.chains, size_t(P.S.n_chains) * 4)) ||
+            (rc = ensure(ws.pick, std::max<size_t>(size_t(chunk), h0) * 4)))
+            return rc;
+        uint32_t* chains = static_cast<uint32_t*>(ws.chains.p);
+        if ((rc = launch_metropolis_init(s, P, chains))) return rc;
+        if (h0 > 0 && (rc = launch_metropolis(s, P, 0, uint32_t(h0), chains, static_cast<uint32_t*>(ws.pick.p))))
+            return rc;
+        aux += 2;
+    }
+    P.counters = static_cast<unsigned long long*>(ws.counters.p);
+    P.ledger = static_cast<double*>(ws.ledger.p);
+    P.status = static_cast<uint32_t*>(ws.status.p);
+    // the part's grids hold batches first_batch.. as slots 0..n_part-1
+    const uintptr_t shift = uintptr_t(first_batch) * V;
+    P.batch_stride = V;
+    P.edep = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(ws.edep.p) - shift * 8);
+    P.edep_hi = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(ws.edep.p) - shift * 4);
+    P.edep_lo = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(ws.edep.p) + (V * size_t(n_part) - shift) * 4);
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep.p, 0, V * size_t(n_part) * 8, s));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.counters.p, 0, C_NCOUNT * 8, s));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.ledger.p, 0, L_NLEDGER * 8, s));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.status.p, 0, 16, s));
+    // the caller's sums, on the device for the fold
+    const bool dev = is_device_ptr(sum1) && is_device_ptr(sum2);
+    double *d1 = sum1, *d2 = sum2;
+    if (!dev) {
+        if ((rc = ensure(ws.stage, V * 16))) return rc;
+        d1 = static_cast<double*>(ws.stage.p);
+        d2 = d1 + V;
+        GDPM_CUDA_TRY(cudaMemcpyAsync(d1, sum1, V * 8, cudaMemcpyDefault, s));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(d2, sum2, V * 8, cudaMemcpyDefault, s));
+    }
+    r.prof_kind.clear();
+    GDPM_CUDA_TRY(cudaEventRecord(r.ev0, s));
+    int64_t phases = 0;
+    int run_rc = run_phases(ctx, r, P, src, h0, h1 - h0, nb_small, nb_rem, chunk, phases, aux);
+    if (run_rc == GDPM_OK) {
+        SimParams Pf = P;
+        Pf.edep = static_cast<double*>(ws.edep.p);
+        Pf.edep_hi = static_cast<float*>(ws.edep.p);
+        Pf.edep_lo = static_cast<float*>(ws.edep.p) + V * size_t(n_part);
+        const int n_big = int(std::min<int64_t>(std::max<int64_t>(int64_t(nb_rem) - first_batch, 0), n_part));
+        run_rc = launch_fold_batches(ctx, s, Pf, V, n_part, nb_small, uint32_t(n_big), d1, d2);
+        ++aux;
+    }
+    GDPM_CUDA_TRY(cudaEventRecord(r.ev1, s));
+    if (run_rc != GDPM_OK) {
+        cudaStreamSynchronize(s);
+        r.prof_kind.clear();
+        return run_rc;
+    }
+    if (!dev) {
+        GDPM_CUDA_TRY(cudaMemcpyAsync(sum1, d1, V * 8, cudaMemcpyDefault, s));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(sum2, d2, V * 8, cudaMemcpyDefault, s));
+    }
+    unsigned char* hp = static_cast<unsigned char*>(ws.pinned_host.p);
+    unsigned long long* hc = reinterpret_cast<unsigned long long*>(hp + 64);
+    double* hl = reinterpret_cast<double*>(hp + 64 + C_NCOUNT * 8);
+    uint32_t* hs = reinterpret_cast<uint32_t*>(hp + 64 + C_NCOUNT * 8 + L_NLEDGER * 8);
+    GDPM_CUDA_TRY(cudaMemcpyAsync(hc, ws.counters.p, C_NCOUNT * 8, cudaMemcpyDeviceToHost, s));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(hl, ws.ledger.p, L_NLEDGER * 8, cudaMemcpyDeviceToHost, s));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(hs, ws.status.p, 4, cudaMemcpyDeviceToHost, s));
+    GDPM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        fill_stats(hc, hl, st);
+        st->phases = phases;
+        st->launches = phases + aux;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r.ev0, r.ev1);
+        st->transport_ms = ms;
+    }
+    prof_collect(r, st);
+    if (*hs & ST_QUEUE_OVERFLOW) return GDPM_E_QUEUE_OVERFLOW;
+    if (*hs & (ST_ITER_CAP | ST_PHASE_CAP)) return GDPM_E_TIMEOUT;
+    return GDPM_OK;
+}
+
+int gdpm_finalize(gdpm_ctx* ctx, gdpm_phantom* ph, int n_batches, const double* sum1, const double* sum2,
+                  double* dose_out, double* sigma_out, gdpm_stats* st) {
+    if (!ctx || !ph || !sum1 || !sum2 || n_batches < 2) return GDPM_E_ARG;
+    GDPM_CUDA_TRY(cudaSetDevice(ctx->device));
+    Runner& r = ctx->run;
+    cudaStream_t s = r.stream;
+    const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
+    Workspace& ws = r.ws;
+    int rc;
+    if ((rc = ensure(ws.s1, V * 8)) || (rc = ensure(ws.s2, V * 8)) || (rc = ensure(ws.stage, V * 16)) ||
+        (rc = ensure(ws.ledger, L_NLEDGER * 8)))
+        return rc;
+    if (!ws.pinned_host.p) {
+        void* h = nullptr;
+        GDPM_CUDA_TRY(cudaMallocHost(&h, 4096));
+        ws.pinned_host.p = h;
+        ws.pinned_host.bytes = 4096;
+    }
+    GDPM_CUDA_TRY(cudaMemcpyAsync(ws.s1.p, sum1, V * 8, cudaMemcpyDefault, s));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(ws.s2.p, sum2, V * 8, cudaMemcpyDefault, s));
+    GDPM_CUDA_TRY(cudaMemsetAsync(ws.ledger.p, 0, L_NLEDGER * 8, s));
+    SimParams P{};
+    P.dx = ph->dx; P.dy = ph->dy; P.dz = ph->dz;
+    P.rho = static_cast<const float*>(ph->rho.p);
+    P.ledger = static_cast<double*>(ws.ledger.p);
+    double* dd = static_cast<double*>(ws.stage.p);
+    double* ds = dd + V;
+    if ((rc = launch_finalize_into(ctx, s, P, V, n_batches, static_cast<const double*>(ws.s1.p),
+                                   static_cast<const double*>(ws.s2.p), dd, ds)))
+        return rc;
+    if (dose_out) GDPM_CUDA_TRY(cudaMemcpyAsync(dose_out, dd, V * 8, cudaMemcpyDefault, s));
+    if (sigma_out) GDPM_CUDA_TRY(cudaMemcpyAsync(sigma_out, ds, V * 8, cudaMemcpyDefault, s));
+    double* hl = reinterpret_cast<double*>(static_cast<unsigned char*>(ws.pinned_host.p) + 64 + C_NCOUNT * 8);
+    GDPM_CUDA_TRY(cudaMemcpyAsync(hl, ws.ledger.p, L_NLEDGER * 8, cudaMemcpyDeviceToHost, s));
+    GDPM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        double dmax;
+        std::memcpy(&dmax, &hl[L_DMAX], 8);
+        st->dmax = dmax;
+        st->sigma_over_dmax = (hl[L_SIGCNT] > 0 && dmax > 0) ? hl[L_SIGSUM] / hl[L_SIGCNT] / dmax : 0.0;
+        st->launches = 2;
+    }
+    return GDPM_OK;
+}
+
 int gdpm_autotune(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_histories,
                   int n_batches, double budget_ms, gdpm_tune_result* out) {
     if (!ctx || !out || !(budget_ms > 0)) return GDPM_E_ARG;
@@ -1277,6 +1449,7 @@ int gdpm_simulate_beamlets(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb,
     const gdpm_source_state& src = ctx->src;
     if (!src.set) return GDPM_E_STATE;
     if (src.desc.geometry != GDPM_GEO_BEAMLETS) return GDPM_E_ARG;
+    Range range("gdpm_simulate_beamlets");
     const uint32_t K = uint32_t(src.beamlets.size() / 17);
     const int nb = n_batches;
     if (nb < 1 || (nb < 2 && sigma_out) || size_t(K) * nb > size_t(kMaxSlots)) return GDPM_E_ARG;

@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(256) k_fold(SimParams P, size_t V, double inv_
 }
 
 // All batches at once (batches run side by side, one tally grid each):
-// s1 = sum_b E_b/n_b, s2 = sum_b (E_b/n_b)^2 per voxel.
+// s1 += sum_b E_b/n_b, s2 += sum_b (E_b/n_b)^2 per voxel (the sums of a run
+// in parts accumulate).
 __global__ void __launch_bounds__(256) k_fold_batches(SimParams P, size_t V, int nbatch,
                                                       double inv_big, double inv_small, int n_big,
                                                       double* __restrict__ s1, double* __restrict__ s2) {
@@ -149,8 +150,8 @@ __global__ void __launch_bounds__(256) k_fold_batches(SimParams P, size_t V, int
             acc1 += x;
             acc2 = fma(x, x, acc2);
         }
-        s1[v] = acc1;
-        s2[v] = acc2;
+        s1[v] += acc1;
+        s2[v] += acc2;
     }
     const double t = block_sum(dep, s_red);
     if (threadIdx.x == 0 && t != 0.0) atomicAdd(&P.ledger[L_DEPOSITED], t);

@@ -48,7 +48,7 @@ EXPORTED = ["gdpm_context_create", "gdpm_context_destroy", "gdpm_set_param",
             "gdpm_set_history_records", "gdpm_request_submit", "gdpm_request_poll",
             "gdpm_strerror", "gdpm_debug_philox", "gdpm_debug_sample", "gdpm_tables_export",
             "gdpm_debug_sources", "gdpm_debug_beamlets", "gdpm_simulate_noalloc",
-            "gdpm_simulate_beamlets", "gdpm_autotune"]
+            "gdpm_simulate_beamlets", "gdpm_autotune", "gdpm_simulate_part", "gdpm_finalize"]
 
 
 class gdpm_material_desc(C.Structure):
@@ -144,6 +144,8 @@ def lib():
                 "gdpm_simulate_noalloc": [vp, vp, vp, u64, i, vp, vp, C.POINTER(gdpm_stats)],
                 "gdpm_simulate_beamlets": [vp, vp, vp, vp, i, vp, vp, C.POINTER(gdpm_stats)],
                 "gdpm_autotune": [vp, vp, vp, u64, i, d, C.POINTER(gdpm_tune_result)],
+                "gdpm_simulate_part": [vp, vp, vp, u64, i, i, i, vp, vp, C.POINTER(gdpm_stats)],
+                "gdpm_finalize": [vp, vp, i, vp, vp, vp, vp, C.POINTER(gdpm_stats)],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -296,6 +298,25 @@ def gdpm_autotune(ctx, phantom, tables, n_histories, n_batches, budget_ms=2000.0
     _check(lib().gdpm_autotune(ctx, phantom, tables, n_histories, n_batches, budget_ms,
                                C.byref(r)), "gdpm_autotune")
     return {k: getattr(r, k) for k, _ in r._fields_}
+
+
+def gdpm_simulate_part(ctx, phantom, tables, n_histories, n_batches, first_batch, n_part,
+                       sum1, sum2):
+    """Run batches [first_batch, first_batch+n_part) and add their per-batch
+    x_b, x_b^2 into sum1, sum2 (checkpointable run state)."""
+    st = gdpm_stats()
+    _check(lib().gdpm_simulate_part(ctx, phantom, tables, n_histories, n_batches, first_batch,
+                                    n_part, _ptr(sum1), _ptr(sum2), C.byref(st)),
+           "gdpm_simulate_part")
+    return st.as_dict()
+
+
+def gdpm_finalize(ctx, phantom, n_batches, sum1, sum2, dose_out=None, sigma_out=None):
+    """Dose and sigma from the sums of all n_batches batches."""
+    st = gdpm_stats()
+    _check(lib().gdpm_finalize(ctx, phantom, n_batches, _ptr(sum1), _ptr(sum2), _ptr(dose_out),
+                               _ptr(sigma_out), C.byref(st)), "gdpm_finalize")
+    return st.as_dict()
 
 
 def gdpm_set_history_records(ctx, rec, recd, n):

@@ -79,3 +79,24 @@ def test_many_requests_complete_with_few_slots():
             G.gdpm_request_poll(eng.ctx, ids[0])          # already released
     finally:
         eng.close()
+
+
+def test_request_that_can_never_fit_is_refused():
+    """Admission: a request whose workspace plus the reserve exceeds the
+    device's memory is refused with GDPM_E_NOMEM instead of waiting."""
+    prob = W.tiny_problem(n_histories=20_000, n_batches=10)
+    eng = G.Engine(prob)
+    V = prob.phantom.n_voxels
+    try:
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_SERVE_RESERVE_MB, 1e7)   # 10 TB kept free
+        rid = G.gdpm_request_submit(eng.ctx, eng.phantom, eng.tables, prob.source, 20_000, 10)
+        with pytest.raises(G.GdpmError) as e:
+            wait(eng.ctx, rid, V)
+        assert e.value.code == G.GDPM_E_NOMEM
+        # the context still serves once the reserve is sane again
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_SERVE_RESERVE_MB, 1024)
+        rid = G.gdpm_request_submit(eng.ctx, eng.phantom, eng.tables, prob.source, 20_000, 10)
+        d, _, st = wait(eng.ctx, rid, V)
+        assert st["n_primary"] == 20_000 and d.max() > 0
+    finally:
+        eng.close()
