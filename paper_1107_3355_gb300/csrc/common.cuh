@@ -1,15 +1,12 @@
 // Device-side building blocks of the GB300 gDPM engine: random numbers,
 // geometry helpers and the data layouts shared by the transport kernels.
 #pragma once
-#include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "gdpm.h"
 
 namespace gdpm {
-
-namespace cg = cooperative_groups;
 
 constexpr int kMaxMat = GDPM_MAX_MATERIALS;
 constexpr int kMaxBins = GDPM_MAX_BINS;
@@ -196,29 +193,6 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
-}
-
-// Reserve one slot per calling thread on a queue tail with one atomic per
-// group of converged threads.
-__device__ __forceinline__ uint32_t reserve_slot(uint32_t* tail) {
-    cg::coalesced_group g = cg::coalesced_threads();
-    uint32_t base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(tail, g.size());
-    base = g.shfl(base, 0);
-    return base + g.thread_rank();
-}
-
-// Add a per-thread count n, one shared atomic per group of converged threads.
-__device__ __forceinline__ void count_n(uint32_t* s_counts, int slot, uint32_t n) {
-    const uint32_t mask = __activemask();
-    const uint32_t tot = __reduce_add_sync(mask, n);
-    if (int(lane_id()) == __ffs(mask) - 1 && tot) atomicAdd(&s_counts[slot], tot);
-}
-
-// Count an event once per calling thread, one shared atomic per group.
-__device__ __forceinline__ void count_event(uint32_t* s_counts, int slot) {
-    cg::coalesced_group g = cg::coalesced_threads();
-    if (g.thread_rank() == 0) atomicAdd(&s_counts[slot], g.size());
 }
 
 }  // namespace gdpm

@@ -3,6 +3,7 @@
 // Woodcock majorant.  These kernels stream voxel arrays and are bound by
 // HBM bandwidth: coalesced grid-stride loops sized to the SM count.
 #include <algorithm>
+#include <cstring>
 
 #include "internal.h"
 
