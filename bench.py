@@ -454,6 +454,7 @@ def main():
         G.gdpm_phantom_destroy(ph)
         G.gdpm_tables_destroy(tb)
         e2e_s += time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, world, dev)          # the slowest rank's end-to-end time
     e2e_value = world * args.e2e_steps * n_hist / e2e_s if args.e2e_steps > 0 else None
 
     # roofline of the dominant kernel kind, from its live event time
