@@ -472,6 +472,25 @@ def main():
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peak = props.multi_processor_count * LANES_PER_SM * sm_mhz * 1e6 / 1e12
 
+    # the resources behind the roofline, measured on this GPU after the timed
+    # region: FP32 FMA and MUFU issue, and scattered FP64 atomics into a
+    # buffer the size of one dose grid (the tally's target)
+    probe = torch.zeros(V, dtype=torch.float64, device=dev)
+    ffma, _, _ = G.gdpm_microbench(ctx, "ffma", probe, 1, int(1e11))
+    mufu, _, _ = G.gdpm_microbench(ctx, "mufu_lg2", probe, 1, int(2e10))
+    red64, _, _ = G.gdpm_microbench(ctx, "red_f64", probe, V, int(2e9))
+    del probe
+    # tally atomics of the electron phase: one per voxel crossed, the ends of
+    # the two hinge legs of each step, and one at each track's end
+    tally_n = agg["crossings"] + 2 * agg["el_steps"] + agg["el_terminated"]
+    tally_rate = tally_n / (kms[1] / 1e3) if kms[1] > 0 else 0.0
+    resources = {"ffma_Tops": ffma / 1e12, "mufu_lg2_Tops": mufu / 1e12,
+                 "red_f64_Gops": red64 / 1e9,
+                 "tally_atomics_Gops": tally_rate / 1e9,
+                 "tally_frac_of_red_f64": tally_rate / red64 if red64 > 0 else None,
+                 "note": "measured by gdpm_microbench after the timed region; tally atomics "
+                         "counted as crossings + 2 x electron steps + electron terminations"}
+
     sig = last["sigma_over_dmax"]
     n_to_1pct = n_hist * (sig / 0.01) ** 2 if sig > 0 else float("nan")
     t_to_1pct = n_to_1pct / (value / world) if value > 0 else float("nan")
@@ -489,6 +508,7 @@ def main():
                          "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                          "traffic": None,
                          "note": "ALU lane-operations/s vs SMs x 128 lanes x sampled SM clock"},
+            "resources": resources,
             "kernel_ms_per_step": [k / args.steps for k in kms],
             "events_per_history": {k: agg[k] / (args.steps * n_hist) for k in
                                    ("ph_flights", "compton", "el_steps", "crossings", "moller",

@@ -345,6 +345,36 @@ int gdpm_debug_philox(gdpm_ctx *ctx, const uint32_t *ctr, uint32_t k0, uint32_t 
 int gdpm_debug_sample(gdpm_ctx *ctx, int kind, double a, double b, uint64_t n,
                       uint64_t seed, double *out1, double *out2);
 
+/* Rate of one hardware resource that the transport kernels use, measured by
+ * a persistent grid (SM count x resident blocks of 256 threads) that does
+ * nothing else.  The dose tally of Sec. 2.2.2 is a scattered atomic add into
+ * the batch grid; the flights and deflections spend FP32, MUFU and (ledger,
+ * fold) FP64 issue slots.
+ *   GDPM_MB_RED_F64   FP64 atomic add of 1.0 into n_slots doubles of buf,
+ *                     uniform random slots, old value unused
+ *   GDPM_MB_RED_F32   the same with FP32 (n_slots floats)
+ *   GDPM_MB_ATOM_F32  FP32 atomic add whose returned old value is used, as
+ *                     in the compensated FP32 pair tally
+ *   GDPM_MB_FFMA      FP32 fused multiply-adds, 8 chains per thread
+ *   GDPM_MB_DFMA      FP64 fused multiply-adds
+ *   GDPM_MB_MUFU_LG2  MUFU base-2 logarithms
+ * buf: caller-owned device array (n_slots doubles or floats for the atomic
+ * kinds; at least one float for the others, used as a sink).  One untimed
+ * launch warms up, then the array is cleared and one launch of about n_ops
+ * operations is timed with events on the context's stream, so after an
+ * atomic kind the array's elements sum to *ops_done.
+ * Out: *ops_done = operations the timed launch did (n_ops rounded up to whole
+ * threads), *ms = its device time.  Errors: GDPM_E_ARG (bad kind, NULL or
+ * host buf, n_slots outside [1, 2^32), n_ops 0), GDPM_E_CUDA. */
+#define GDPM_MB_RED_F64 0
+#define GDPM_MB_RED_F32 1
+#define GDPM_MB_ATOM_F32 2
+#define GDPM_MB_FFMA 3
+#define GDPM_MB_DFMA 4
+#define GDPM_MB_MUFU_LG2 5
+int gdpm_microbench(gdpm_ctx *ctx, int kind, void *buf, uint64_t n_slots, uint64_t n_ops,
+                    double *ops_done, double *ms);
+
 /* Copy one FP32 table to a device buffer of doubles:
  *   0 mu_compton [m][i], 1 mu_compton + mu_photo, 2 total mu (cm2/g; the
  *   cumulative forms the transport stores and samples from), 3 CSDA range

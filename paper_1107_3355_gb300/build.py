@@ -27,7 +27,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
 EXTRA = {
     "transport.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
 }
-SOURCES = ["api.cu", "tables.cu", "transport.cu", "stats.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "tables.cu", "transport.cu", "stats.cu", "noalloc.cu", "peaks.cu"]
 
 
 def nvcc() -> str:

@@ -40,6 +40,7 @@ GDPM_PARAM_BATCH_MODE = 15
 GDPM_PARAM_CONCURRENT_MAX_HIST = 16
 GDPM_PARAM_CONCURRENT_MAX_MB = 17
 GDPM_PARAM_GRAPH = 18
+MICROBENCH = {"red_f64": 0, "red_f32": 1, "atom_f32": 2, "ffma": 3, "dfma": 4, "mufu_lg2": 5}
 MAX_EL, MAX_MAT, MAX_BINS = 16, 8, 256
 
 EXPORTED = ["gdpm_context_create", "gdpm_context_destroy", "gdpm_set_param",
@@ -48,7 +49,8 @@ EXPORTED = ["gdpm_context_create", "gdpm_context_destroy", "gdpm_set_param",
             "gdpm_set_history_records", "gdpm_request_submit", "gdpm_request_poll",
             "gdpm_strerror", "gdpm_debug_philox", "gdpm_debug_sample", "gdpm_tables_export",
             "gdpm_debug_sources", "gdpm_debug_beamlets", "gdpm_simulate_noalloc",
-            "gdpm_simulate_beamlets", "gdpm_autotune", "gdpm_simulate_part", "gdpm_finalize"]
+            "gdpm_simulate_beamlets", "gdpm_autotune", "gdpm_simulate_part", "gdpm_finalize",
+            "gdpm_microbench"]
 
 
 class gdpm_material_desc(C.Structure):
@@ -146,6 +148,7 @@ def lib():
                 "gdpm_autotune": [vp, vp, vp, u64, i, d, C.POINTER(gdpm_tune_result)],
                 "gdpm_simulate_part": [vp, vp, vp, u64, i, i, i, vp, vp, C.POINTER(gdpm_stats)],
                 "gdpm_finalize": [vp, vp, i, vp, vp, vp, vp, C.POINTER(gdpm_stats)],
+                "gdpm_microbench": [vp, i, vp, u64, u64, C.POINTER(d), C.POINTER(d)],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -349,6 +352,17 @@ def gdpm_request_poll(ctx, req_id, dose_out=None, sigma_out=None):
 
 def gdpm_debug_philox(ctx, ctr, k0, k1, out, n):
     _check(lib().gdpm_debug_philox(ctx, _ptr(ctr), k0, k1, _ptr(out), n), "gdpm_debug_philox")
+
+
+def gdpm_microbench(ctx, kind, buf, n_slots, n_ops):
+    """Rate of one resource (MICROBENCH name or code) in operations per
+    second; buf is a device tensor of n_slots cells.  Returns
+    (ops/s, ops done, ms)."""
+    kind = MICROBENCH.get(kind, kind)
+    ops, ms = C.c_double(), C.c_double()
+    _check(lib().gdpm_microbench(ctx, kind, _ptr(buf), n_slots, n_ops, C.byref(ops), C.byref(ms)),
+           "gdpm_microbench")
+    return ops.value / (ms.value * 1e-3), ops.value, ms.value
 
 
 def gdpm_debug_sample(ctx, kind, a, b, n, seed, out1, out2=None):
