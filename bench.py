@@ -480,16 +480,16 @@ def main():
     mufu, _, _ = G.gdpm_microbench(ctx, "mufu_lg2", probe, 1, int(2e10))
     red64, _, _ = G.gdpm_microbench(ctx, "red_f64", probe, V, int(2e9))
     del probe
-    # tally atomics of the electron phase: one per voxel crossed, the ends of
-    # the two hinge legs of each step, and one at each track's end
-    tally_n = agg["crossings"] + 2 * agg["el_steps"] + agg["el_terminated"]
+    # tally atomics of the electron phase: a track tallies once per voxel it
+    # leaves and once where it stops (at most crossings + terminations)
+    tally_n = agg["crossings"] + agg["el_terminated"]
     tally_rate = tally_n / (kms[1] / 1e3) if kms[1] > 0 else 0.0
     resources = {"ffma_Tops": ffma / 1e12, "mufu_lg2_Tops": mufu / 1e12,
                  "red_f64_Gops": red64 / 1e9,
                  "tally_atomics_Gops": tally_rate / 1e9,
                  "tally_frac_of_red_f64": tally_rate / red64 if red64 > 0 else None,
                  "note": "measured by gdpm_microbench after the timed region; tally atomics "
-                         "counted as crossings + 2 x electron steps + electron terminations"}
+                         "counted as voxel crossings + electron terminations (an upper bound)"}
 
     sig = last["sigma_over_dmax"]
     n_to_1pct = n_hist * (sig / 0.01) ** 2 if sig > 0 else float("nan")

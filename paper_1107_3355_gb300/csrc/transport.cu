@@ -448,8 +448,12 @@ struct ElSmem {
 // final piece is left to the caller.  True if the particle left the phantom.
 // rho_cur is the density of the particle's current voxel, known on entry
 // (no load before the first segment) and kept up to date on exit.
+// pend is energy already owed to the current voxel but not yet tallied: it
+// goes out with the first piece tallied on leaving the voxel, so a track
+// issues one atomic per voxel it visits rather than one per piece.  dep
+// counts this step's energy (tallied or added to pend).
 __device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& dep, bool defer_last,
-                     uint32_t& crossings, float& rho_cur) {
+                     uint32_t& crossings, float& rho_cur, float& pend) {
     if (!(mass > 0.f)) return false;
     const float iu = p.u != 0.f ? 1.f / p.u : 0.f;
     const float iv = p.v != 0.f ? 1.f / p.v : 0.f;
@@ -474,7 +478,7 @@ __device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& 
             p.y = fmaf(t, p.v, p.y);
             p.z = fmaf(t, p.w, p.z);
             if (!defer_last) {
-                tally(P, p.flags, vox, dpm * left);
+                pend += dpm * left;
                 dep += dpm * left;
             }
             return false;
@@ -483,10 +487,10 @@ __device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& 
         p.y = fmaf(tb, p.v, p.y);
         p.z = fmaf(tb, p.w, p.z);
         const float piece = rho * tb;
-        if (piece > 0.f) {
-            tally(P, p.flags, vox, dpm * piece);
-            dep += dpm * piece;
-        }
+        const float e = dpm * piece;
+        if (e + pend > 0.f) tally(P, p.flags, vox, e + pend);
+        dep += e;
+        pend = 0.f;
         left -= piece;
         ++crossings;
         if (ab == 0) {
@@ -522,7 +526,7 @@ __device__ void electron_escape(const SimParams& P, Part& p, float energy, Acc& 
 // One condensed-history step of an electron or positron (Sec. 2.1), or its
 // absorption.
 __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool& active, Acc& acc,
-                              Ev& ev, Sec& sec) {
+                              Ev& ev, Sec& sec, float& pend) {
     const DevTables& T = P.T;
     bool absorb = p.E < T.eabs_el;
     if (!absorb) {
@@ -586,7 +590,8 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
         bool out = false;
 #pragma unroll 1
         for (int leg = 0; leg < 2; ++leg) {
-            out = walk(P, p, leg ? (1.f - r.y) * xs : r.y * xs, dpm, dep, leg == 1, ev.n, rho_cur);
+            out = walk(P, p, leg ? (1.f - r.y) * xs : r.y * xs, dpm, dep, leg == 1, ev.n, rho_cur,
+                       pend);
             if (out || leg == 1) break;
             rotate(p.u, p.v, p.w, mu, cp, sp);
         }
@@ -596,7 +601,8 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
             active = false;
             return;
         }
-        tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), dT - dep);
+        // the step's remainder stays owed to the voxel the step ends in
+        pend += dT - dep;
         p.E = Tend;
         if (lim == 0) {
             absorb = true;
@@ -648,7 +654,8 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
         // end of track: residual energy deposited here; a positron then
         // annihilates into two back-to-back 0.511 MeV photons (isotropic),
         // or its rest energy is discarded (Sec. 2.1, Sec. 4)
-        tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), p.E);
+        tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), p.E + pend);
+        pend = 0.f;
         ev.b += EV_TERM;
         active = false;
         if (p.flags & kPositron) {
@@ -868,6 +875,7 @@ __device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A
     WarpCnt wc{0u, 0u, 0u};
     Slots sl[2] = {{0u, 0u}, {0u, 0u}};
     bool active = false, exhausted = false;
+    float pend = 0.f;   // electron energy owed to its current voxel (see walk)
     // the warp's block of work indices [st_base, st_base + st_left); near
     // the end of the phase (less than two per lane of the grid left) the
     // warp takes exactly what it needs, so no warp sits on spare work
@@ -927,9 +935,11 @@ __device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A
         // ---- each lane on its own: one step
         if (active) {
             if (PT == 0) photon_step(P, ps, p, active, acc, ev, sec);
-            else electron_step(P, es, p, active, acc, ev, sec);
+            else electron_step(P, es, p, active, acc, ev, sec, pend);
         }
     }
+    // only a phase stopped by its iteration cap leaves a track unfinished
+    if (PT == 1 && pend != 0.f) tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), pend);
     flush_events<PT>(ev, s_cnt);
     flush_warp_counts<PT>(wc, s_cnt);
     // reserved queue slots never written: mark them empty for the consumer
