@@ -72,3 +72,12 @@ def test_single_rank_defaults(monkeypatch):
     assert bench.rank_env() == (1, 0, 0)
     assert bench.max_over_ranks(12.5, 1) == 12.5
     assert bench.whole_job_rate(1, 2, 100, 1000.0) == pytest.approx(200.0)
+
+
+def test_parallel_oracle_baseline_runs_disjoint_processes():
+    """The CPU baseline's multi-process timing: spawned single-thread oracle
+    processes started together, one rate per step."""
+    import bench
+    rates = bench.oracle_rate_parallel("water32_1MeV_pencil", 300, 2, steps=2)
+    assert len(rates) == 2 and all(r > 0 for r in rates)
+    assert bench.host_cores() >= 1
