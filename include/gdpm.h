@@ -44,6 +44,7 @@ extern "C" {
 #define GDPM_E_CUDA (-5)           /* a CUDA runtime call failed */
 #define GDPM_E_STATE (-6)          /* call not valid in the current state */
 #define GDPM_E_BUSY (-7)           /* request not admitted (memory or slots) */
+#define GDPM_E_BOUNDS (-8)         /* checked build only: an index was out of range */
 
 typedef struct gdpm_ctx gdpm_ctx;
 typedef struct gdpm_phantom gdpm_phantom;

@@ -376,6 +376,9 @@ static SimParams base_params(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, u
     P.key1 = uint32_t(ctx->seed >> 32) ^ request_id;
     P.tally_mode = ctx->tally_mode;
     P.max_iters = 1u << 22;   // per-warp iterations in one phase; far above real use
+    P.tally_lo = 0;
+    P.tally_hi = uint64_t(ph->nx) * ph->ny * ph->nz;   // one grid; widened by batched runs
+    P.n_records = 0;
     return P;
 }
 
@@ -713,6 +716,7 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
     P.status = static_cast<uint32_t*>(ws.status.p);
     P.hrec = hrec;
     P.hrecd = hrecd;
+    P.n_records = hrec ? ctx->hrec_n : 0;
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.s1.p, 0, V * 8, s));
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.s2.p, 0, V * 8, s));
     if (conc) {
@@ -742,6 +746,7 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
         // all batches side by side: particles carry their batch, each batch
         // has its own grid; one fold at the end
         P.batch_stride = V;
+        P.tally_hi = V * uint64_t(n_batches);
         P.edep = static_cast<double*>(ws.edep.p);
         P.edep_hi = static_cast<float*>(ws.edep.p);
         P.edep_lo = static_cast<float*>(ws.edep.p) + V * size_t(n_batches);
@@ -830,6 +835,7 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
         st->transport_ms = ms;
     }
     prof_collect(r, st);
+    if (*hs & ST_BOUNDS) return GDPM_E_BOUNDS;
     if (*hs & ST_QUEUE_OVERFLOW) return GDPM_E_QUEUE_OVERFLOW;
     if (*hs & (ST_ITER_CAP | ST_PHASE_CAP)) return GDPM_E_TIMEOUT;
     return GDPM_OK;
@@ -963,6 +969,7 @@ const char* gdpm_strerror(int code) {
     case GDPM_E_CUDA: return cudaGetErrorString(last_cuda_error());
     case GDPM_E_STATE: return "call not valid in the current state";
     case GDPM_E_BUSY: return "request not admitted";
+    case GDPM_E_BOUNDS: return "checked build: an index was out of range";
     }
     return "unknown status";
 }
@@ -1267,6 +1274,8 @@ int gdpm_simulate_part(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_
     // the part's grids hold batches first_batch.. as slots 0..n_part-1
     const uintptr_t shift = uintptr_t(first_batch) * V;
     P.batch_stride = V;
+    P.tally_lo = uint64_t(first_batch) * V;
+    P.tally_hi = uint64_t(first_batch + n_part) * V;
     P.edep = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(ws.edep.p) - shift * 8);
     P.edep_hi = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(ws.edep.p) - shift * 4);
     P.edep_lo = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(ws.edep.p) + (V * size_t(n_part) - shift) * 4);
@@ -1325,6 +1334,7 @@ int gdpm_simulate_part(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_
         st->transport_ms = ms;
     }
     prof_collect(r, st);
+    if (*hs & ST_BOUNDS) return GDPM_E_BOUNDS;
     if (*hs & ST_QUEUE_OVERFLOW) return GDPM_E_QUEUE_OVERFLOW;
     if (*hs & (ST_ITER_CAP | ST_PHASE_CAP)) return GDPM_E_TIMEOUT;
     return GDPM_OK;
@@ -1504,12 +1514,14 @@ int gdpm_simulate_beamlets(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb,
     P.ledger = static_cast<double*>(ws.ledger.p);
     P.status = static_cast<uint32_t*>(ws.status.p);
     P.batch_stride = V;
+    P.tally_hi = V * uint64_t(slots);
     P.edep = static_cast<double*>(ws.edep.p);
     P.edep_hi = static_cast<float*>(ws.edep.p);
     P.edep_lo = static_cast<float*>(ws.edep.p) + V * size_t(slots);
     if (ctx->hrec) {
         if (ctx->hrec_n < total) return GDPM_E_ARG;
         P.hrec = ctx->hrec;
+        P.n_records = ctx->hrec_n;
         P.hrecd = ctx->hrecd;
         GDPM_CUDA_TRY(cudaMemsetAsync(ctx->hrec, 0, total * 16, s));
         GDPM_CUDA_TRY(cudaMemsetAsync(ctx->hrecd, 0, total * 16, s));
@@ -1586,6 +1598,7 @@ int gdpm_simulate_beamlets(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb,
         st->transport_ms = ms;
     }
     prof_collect(r, st);
+    if (*hs & ST_BOUNDS) return GDPM_E_BOUNDS;
     if (*hs & ST_QUEUE_OVERFLOW) return GDPM_E_QUEUE_OVERFLOW;
     if (*hs & (ST_ITER_CAP | ST_PHASE_CAP)) return GDPM_E_TIMEOUT;
     return GDPM_OK;

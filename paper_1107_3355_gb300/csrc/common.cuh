@@ -19,8 +19,30 @@ enum : uint32_t {
     ST_QUEUE_OVERFLOW = 1u,
     ST_ITER_CAP = 2u,
     ST_PHASE_CAP = 4u,          // the device-driven phase loop reached its phase cap
-    ST_BAD_MATERIAL = 4u,
+    ST_BOUNDS = 8u,             // checked build: an index was out of range (class below)
+    ST_B_VOXEL = 1u << 8,       //   phantom voxel
+    ST_B_TALLY = 1u << 9,       //   tally cell
+    ST_B_TABLE = 1u << 10,      //   material / beamlet table row
+    ST_B_QUEUE = 1u << 11,      //   queue slot
+    ST_B_RECORD = 1u << 12,     //   per-history record
 };
+
+// Checked build (compiled with GDPM_CHECKED=1): an index is tested against
+// its range before use.  One out of range sets ST_BOUNDS and its class bit
+// and is replaced by 0, so the access stays in bounds and the call returns
+// GDPM_E_BOUNDS.  In the normal build the check and its range expression
+// vanish.
+#ifndef GDPM_CHECKED
+#define GDPM_CHECKED 0
+#endif
+#if GDPM_CHECKED
+__device__ __noinline__ inline void bounds_fail(uint32_t* status, uint32_t cls) {
+    atomicOr(status, ST_BOUNDS | cls);
+}
+#define GDPM_IDX(status, i, n, cls) ((i) < (n) ? (i) : (bounds_fail((status), (cls)), decltype(i)(0)))
+#else
+#define GDPM_IDX(status, i, n, cls) (i)
+#endif
 
 // ---------------------------------------------------------------- counters
 // Slots of the device counter array (uint64).  Names follow gdpm_stats.

@@ -230,6 +230,9 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     P.key1 = uint32_t(ctx->seed >> 32) ^ ctx->request_id;
     P.tally_mode = ctx->tally_mode;
     P.max_iters = 1u << 22;
+    P.tally_lo = 0;
+    P.tally_hi = V;
+    P.n_records = 0;
     P.edep = edep;
     P.edep_hi = reinterpret_cast<float*>(edep);            // FP32 pair mode: two V-float halves
     P.edep_lo = reinterpret_cast<float*>(edep) + V;
@@ -384,6 +387,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
         cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
         st->transport_ms = ms;
     }
+    if (hs & ST_BOUNDS) return GDPM_E_BOUNDS;
     if (hs & ST_QUEUE_OVERFLOW) return GDPM_E_QUEUE_OVERFLOW;
     if (hs & ST_ITER_CAP) return GDPM_E_TIMEOUT;
     return GDPM_OK;

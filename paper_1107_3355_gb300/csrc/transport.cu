@@ -73,7 +73,13 @@ struct Sec {
 
 // Deposit e MeV in voxel vox of the tally of the batch in `flags`.
 __device__ __forceinline__ void tally(const SimParams& P, uint32_t flags, uint32_t vox0, float e) {
-    const size_t vox = size_t(vox0) + size_t((flags & kBatchMask) >> kBatchShift) * P.batch_stride;
+    size_t vox = size_t(vox0) + size_t((flags & kBatchMask) >> kBatchShift) * P.batch_stride;
+#if GDPM_CHECKED
+    if (vox < P.tally_lo || vox >= P.tally_hi) {
+        bounds_fail(P.status, ST_B_TALLY);
+        vox = P.tally_lo;
+    }
+#endif
     if (P.tally_mode == 0) {
         atomicAdd(&P.edep[vox], double(e));
     } else {
@@ -92,11 +98,16 @@ __device__ __forceinline__ uint32_t vox_of(const SimParams& P, int ix, int iy, i
 }
 
 __device__ __forceinline__ void hist_count(const SimParams& P, uint32_t hist, int k) {
-    if (P.hrec) atomicAdd(&P.hrec[size_t(hist) * 4 + k], 1);
+    if (P.hrec) atomicAdd(&P.hrec[size_t(GDPM_IDX(P.status, hist, P.n_records, ST_B_RECORD)) * 4 + k], 1);
 }
 __device__ __forceinline__ void hist_add(const SimParams& P, uint32_t hist, int k, double v) {
-    if (P.hrec) atomicAdd(&P.hrecd[size_t(hist) * 2 + k], v);
+    if (P.hrec) atomicAdd(&P.hrecd[size_t(GDPM_IDX(P.status, hist, P.n_records, ST_B_RECORD)) * 2 + k], v);
 }
+#if GDPM_CHECKED
+__device__ __forceinline__ uint32_t n_voxels(const SimParams& P) {
+    return uint32_t(P.nx) * uint32_t(P.ny) * uint32_t(P.nz);
+}
+#endif
 
 // ---------------------------------------------------------------- samplers
 // Klein-Nishina in eps = E'/E by the two-branch mixture method: with weight
@@ -308,7 +319,7 @@ __device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t id
             // a dose-matrix sub-problem is its own beamlet; otherwise sample one
             const int kb = A.n_sub ? int(k)
                                    : pick_beamlet(S, A, idx, h, r.w, P.key0, P.key1, cdf_tab ? cdf_tab : S.bl_cdf);
-            const float* row = S.beamlets + size_t(kb) * 16;
+            const float* row = S.beamlets + size_t(GDPM_IDX(P.status, kb, S.n_beamlets, ST_B_TABLE)) * 16;
             src = row; cen = row + 3; au = row + 6; av = row + 9;
             a0 = row[12]; a1 = row[13]; b0 = row[14]; b1 = row[15];
         }
@@ -373,8 +384,8 @@ __device__ void photon_step(const SimParams& P, const PhSmem& S, Part& p, bool& 
         }
         ++ev.n;
         voxel_of(P, p);
-        vox = vox_of(P, p.ix, p.iy, p.iz);
-        const int m = __ldg(&P.mat[vox]);
+        vox = GDPM_IDX(P.status, vox_of(P, p.ix, p.iy, p.iz), n_voxels(P), ST_B_VOXEL);
+        const int m = GDPM_IDX(P.status, int(__ldg(&P.mat[vox])), T.n_mat, ST_B_TABLE);
         const float rho = __ldg(&P.rho[vox]);
         mi = m * T.n_e + i;
         mt = lerpf(S.tot[mi], S.tot[mi + 1], f);
@@ -507,6 +518,7 @@ __device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& 
             const uint32_t plane = uint32_t(P.nx) * uint32_t(P.ny);
             vox = sz > 0 ? vox + plane : vox - plane;
         }
+        vox = GDPM_IDX(P.status, vox, n_voxels(P), ST_B_VOXEL);
         rho_cur = __ldg(&P.rho[vox]);
     }
     atomicOr(P.status, ST_ITER_CAP);
@@ -534,8 +546,8 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
         ev.b += EV_STEP;
         hist_count(P, p.hist, 1);
         // material and density of the start voxel, loaded together
-        const uint32_t vox0 = vox_of(P, p.ix, p.iy, p.iz);
-        const int m = __ldg(&P.mat[vox0]);
+        const uint32_t vox0 = GDPM_IDX(P.status, vox_of(P, p.ix, p.iy, p.iz), n_voxels(P), ST_B_VOXEL);
+        const int m = GDPM_IDX(P.status, int(__ldg(&P.mat[vox0])), T.n_mat, ST_B_TABLE);
         float rho_cur = __ldg(&P.rho[vox0]);
         int i;
         float f;
@@ -914,10 +926,10 @@ __device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A
                 if (idx < A.n_src) {
                     // made by k_sources; a primary that missed the phantom
                     // left its slot empty (E < 0) and is accounted there
-                    queue_load(A.src, idx, p);
+                    queue_load(A.src, GDPM_IDX(P.status, idx, A.src.capacity, ST_B_QUEUE), p);
                     active = p.E >= 0.f;
                 } else if (idx < total) {
-                    queue_load(A.in, idx - A.n_src, p);
+                    queue_load(A.in, GDPM_IDX(P.status, idx - A.n_src, A.in.capacity, ST_B_QUEUE), p);
                     // a slot reserved but never written holds E < 0
                     from_queue = p.E >= 0.f;
                     active = from_queue;
@@ -997,9 +1009,9 @@ __device__ __forceinline__ void make_sources(const SimParams& P, const PhaseArgs
          idx += gridDim.x * blockDim.x) {
         Part p{};
         if (make_primary(P, A, idx, p, acc, ptab, ctab)) {
-            queue_store(A.src, idx, p);
+            queue_store(A.src, GDPM_IDX(P.status, idx, A.src.capacity, ST_B_QUEUE), p);
         } else {
-            A.src.E[idx] = -1.f;
+            A.src.E[GDPM_IDX(P.status, idx, A.src.capacity, ST_B_QUEUE)] = -1.f;
             ++missed;
         }
         ++made;

@@ -19,7 +19,7 @@ from . import workloads as W
 
 GDPM_OK = 0
 GDPM_E_ARG, GDPM_E_NOMEM, GDPM_E_QUEUE_OVERFLOW, GDPM_E_TIMEOUT = -1, -2, -3, -4
-GDPM_E_CUDA, GDPM_E_STATE, GDPM_E_BUSY = -5, -6, -7
+GDPM_E_CUDA, GDPM_E_STATE, GDPM_E_BUSY, GDPM_E_BOUNDS = -5, -6, -7, -8
 GDPM_PHOTON, GDPM_ELECTRON = 0, 1
 GDPM_GEO_PENCIL, GDPM_GEO_POINT_FIELD, GDPM_GEO_BEAMLETS = 0, 1, 2
 GDPM_FLAG_COMPTON_ONLY, GDPM_FLAG_NO_HARD, GDPM_FLAG_SAUTER = 2, 4, 8
@@ -110,16 +110,23 @@ class GdpmError(RuntimeError):
         self.code = code
 
 
+def checked_build() -> bool:
+    """True when GDPM_CHECKED=1 in the environment: this process loads the
+    bounds-checked library (libgdpm_checked.so) instead of libgdpm.so."""
+    return os.environ.get("GDPM_CHECKED", "0") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked_build() else _build.LIB
 
 
 def lib():
-    """Load libgdpm.so (building it with nvcc first if it is missing or stale)."""
+    """Load libgdpm.so, or libgdpm_checked.so under GDPM_CHECKED=1 (building
+    it with nvcc first if it is missing or stale)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(checked=checked_build())
             L = C.CDLL(path)
             vp, i, u64, d = C.c_void_p, C.c_int, C.c_uint64, C.c_double
             sig = {

@@ -37,9 +37,17 @@ def test_library_builds_and_exports_every_symbol():
     assert set(declared_functions()) <= exported
 
 
+def test_checked_build_exports_the_same_symbols():
+    path = B.build(checked=True)
+    assert path.endswith("libgdpm_checked.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    assert set(declared_functions()) <= set(re.findall(r"\bT (gdpm_\w+)", out))
+
+
 def test_strerror_needs_no_device():
     assert G.gdpm_strerror(G.GDPM_E_QUEUE_OVERFLOW) == "secondary particle queue overflow"
     assert G.gdpm_strerror(0) == "ok"
+    assert "out of range" in G.gdpm_strerror(G.GDPM_E_BOUNDS)
 
 
 def test_product_path_refuses_without_gpu():
