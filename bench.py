@@ -54,7 +54,7 @@ LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gdpm", choices=["gdpm", "reference"])
     ap.add_argument("--workload", default="slab128_6MV", choices=sorted(WORKLOADS))
@@ -76,7 +76,11 @@ def parse():
 
 # ---------------------------------------------------------------- clocks
 class Clocks:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of the SM clock and throttle reasons every 100 ms.
+    Start it before the warm-up (nvidia-smi takes a while to come up), mark
+    the timed region with begin()/end(); stop() keeps the samples whose
+    timestamps fall inside that region."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -84,20 +88,37 @@ class Clocks:
         self.index = index
         self.path = tempfile.mktemp(prefix="gdpm_clk_", suffix=".csv")
         self.proc = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        if self.t1 is None:
+            self.end()
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -110,6 +131,14 @@ class Clocks:
             if len(parts) >= 9:
                 rows.append(parts)
         os.unlink(self.path)
+        window = "timed region"
+        if self.t0 is not None:
+            inside = [r for r in rows if (self._stamp(r[0]) or 0.0) >= self.t0 - 0.05 and
+                      (self._stamp(r[0]) or 0.0) <= self.t1 + 0.05]
+            if inside:
+                rows = inside
+            else:
+                window = "no sample inside the timed region: all samples of the run"
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
 
@@ -125,7 +154,7 @@ class Clocks:
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "window": window}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -325,11 +354,12 @@ def beamlet_matrix_bench(args):
     dose = torch.empty((K, V), dtype=torch.float64, device="cuda")
     sigma = torch.empty((K, V), dtype=torch.float64, device="cuda") if nb >= 2 else None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clocks = Clocks(0)
+    clocks.start()
     for _ in range(args.warmup):
         G.gdpm_simulate_beamlets(eng.ctx, eng.phantom, eng.tables, prob.sub_histories, nb, dose, sigma)
-    clocks = Clocks(0)
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     stream = torch.cuda.current_stream()
     ms = []
     for k in range(args.steps):
@@ -341,6 +371,7 @@ def beamlet_matrix_bench(args):
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
+    clocks.end()
     clk = clocks.stop()
     batched = total / (float(np.median(ms)) / 1e3)
     # one beamlet at a time (dose of each beamlet alone, 2 batches: the
@@ -452,6 +483,8 @@ def main():
     dose = torch.empty(V, dtype=torch.float64, device=dev)
     sigma = torch.empty(V, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    clocks = Clocks(local)
+    clocks.start()
     for _ in range(args.warmup):
         eng.run(dose=dose, sigma=sigma)
 
@@ -461,9 +494,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    clocks = Clocks(local)
     barrier()
-    clocks.start()
+    clocks.begin()
     stream = torch.cuda.current_stream(dev)
     total_ms = 0.0
     agg = {}
@@ -483,6 +515,7 @@ def main():
                 agg[key] = agg.get(key, 0) + v
         last = st
     barrier()
+    clocks.end()
     clk = clocks.stop()
     t_max = max_over_ranks(total_ms, world, dev)
     value = whole_job_rate(world, args.steps, n_hist, t_max)

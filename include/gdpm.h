@@ -167,7 +167,9 @@ enum {
                                           (g/cm3, default 0.05: excludes air) */
     GDPM_PARAM_BATCH_MODE = 15,      /* 0 auto, 1 batches one after another, 2 all batches side
                                         by side (one tally grid per batch, n_batches <= 128,
-                                        phases of up to 8M primaries shared by all batches) */
+                                        phases shared by all batches: up to 32M primaries
+                                        where their queues fit in a quarter of the device's
+                                        memory, else 16M, 8M ...) */
     GDPM_PARAM_CONCURRENT_MAX_HIST = 16, /* auto: side by side when histories per batch <= this
                                             (default 4e9, no limit) ... */
     GDPM_PARAM_CONCURRENT_MAX_MB = 17,   /* ... and the per-batch grids fit in this (default 16384) */
@@ -277,8 +279,8 @@ typedef struct {
 /* Autotuner: run the calculation gdpm_simulate(ph, tb, n_histories,
  * n_batches) with the current source under each candidate launch
  * configuration -- batches side by side (when their grids fit) or one after
- * another, 1M / 4M / 8M primaries per phase, 1 / 2 / 4 phase pairs per host
- * check -- until the wall-clock budget is spent, keep the fastest, and set
+ * another, 1M / 4M primaries per phase or the side-by-side default (8M or
+ * more), 1 / 2 / 4 phase pairs per host check -- until the wall-clock budget is spent, keep the fastest, and set
  * it on the context (GDPM_PARAM_BATCH_MODE, _SOURCE_CHUNK, _SPECULATIVE).
  * Results do not depend on the configuration (per-history random streams),
  * only the time does.  `out` is a host struct.

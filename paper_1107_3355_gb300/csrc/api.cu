@@ -400,14 +400,15 @@ static int validate_run(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const 
     return GDPM_OK;
 }
 
-// Primaries per phase: up to 2^20, and no more than one batch (or run) holds.
-// Primaries per transport phase.  Batches side by side share their phases,
-// so those phases can be long (8M primaries): a phase ends with a tail in
-// which lanes run out of particles, and longer phases make the tail a
-// smaller share.  Batches one after another have one batch per phase.
+// Primaries per transport phase, and no more than one batch (or run) holds.
+// Batches side by side share their phases, so those phases can be long (up
+// to ctx->auto_chunk primaries, sized from the device's memory): a phase
+// ends with a tail in which lanes run out of particles, and longer phases
+// make the tail a smaller share.  Batches one after another have one batch
+// per phase, up to 2^20 primaries.
 static uint32_t chunk_of(gdpm_ctx* ctx, uint64_t n_per_run, int parts, bool concurrent) {
     const uint64_t per = (n_per_run + parts - 1) / parts;
-    const uint32_t chunk = ctx->source_chunk ? ctx->source_chunk : concurrent ? (1u << 23) : (1u << 20);
+    const uint32_t chunk = ctx->source_chunk ? ctx->source_chunk : concurrent ? ctx->auto_chunk : (1u << 20);
     return uint32_t(std::min<uint64_t>(chunk, per));
 }
 static uint32_t capacity_of(gdpm_ctx* ctx, uint32_t chunk) {
@@ -991,6 +992,15 @@ int gdpm_context_create(gdpm_ctx** out, int device, void* cuda_stream, uint64_t 
         return GDPM_E_CUDA;
     }
     c->sm_count = prop.multiProcessorCount;
+    // default phase length of side-by-side runs: the largest power of two up
+    // to 2^25 primaries whose queues (three of capacity_of(chunk) slots and
+    // the source queue) take at most a quarter of the device's memory
+    {
+        const double per_primary = (3.0 * 8.0 + 1.0) * kQueueWords * 4;
+        uint32_t ch = 1u << 25;
+        while (ch > (1u << 20) && per_primary * ch > 0.25 * double(prop.totalGlobalMem)) ch >>= 1;
+        c->auto_chunk = ch;
+    }
     const int rc = runner_init(c->run, static_cast<cudaStream_t>(cuda_stream), false);
     if (rc) {
         runner_free(c->run);
@@ -1398,7 +1408,7 @@ int gdpm_autotune(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_h
     std::vector<Cand> cands;
     const bool can_conc = n_batches <= kMaxConcurrentBatches &&
                           V * size_t(n_batches) * 8 <= ctx->concurrent_max_bytes;
-    const uint32_t chunks[3] = {1u << 20, 1u << 22, 1u << 23};
+    const uint32_t chunks[3] = {1u << 20, 1u << 22, std::max(1u << 23, ctx->auto_chunk)};
     for (int mode = 2; mode >= 1; --mode) {
         if (mode == 2 && !can_conc) continue;
         const uint64_t per = mode == 2 ? n_histories : (n_histories + n_batches - 1) / n_batches;
