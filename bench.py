@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "serve", "beamlets"])
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "serve", "beamlets",
+                                                             "resources"])
     ap.add_argument("--matrix-beamlets", type=int, default=400)
     ap.add_argument("--matrix-batches", type=int, default=2)
     ap.add_argument("--serve-requests", type=int, default=60)
@@ -425,8 +426,39 @@ def whole_job_rate(world, steps, n_hist, t_max_ms):
     return world * steps * n_hist / (t_max_ms / 1e3)
 
 
+def resources_bench(args):
+    """Rates of the resources behind the transport kernels (gdpm_microbench):
+    scattered atomic adds into arrays from 32K cells (contended) to 64M cells
+    (larger than L2), and FP32 FMA, FP64 FMA and MUFU issue.  Best of three
+    launches each; one JSON line."""
+    import torch
+    from paper_1107_3355_gb300 import gdpm as G
+    ctx = G.gdpm_context_create(0, torch.cuda.current_stream().cuda_stream, 1)
+    out = {}
+    try:
+        for kind in ("red_f64", "red_f32", "atom_f32"):
+            for n in (32768, 262144, 2097152, 8388608, 67108864):
+                dt = torch.float64 if kind == "red_f64" else torch.float32
+                buf = torch.zeros(n, dtype=dt, device="cuda")
+                out["%s_%dcells_per_s" % (kind, n)] = max(
+                    G.gdpm_microbench(ctx, kind, buf, n, int(2e9))[0] for _ in range(3))
+                del buf
+        sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+        for kind, n in (("ffma", 2e11), ("dfma", 2e9), ("mufu_lg2", 4e10)):
+            out[kind + "_per_s"] = max(G.gdpm_microbench(ctx, kind, sink, 1, int(n))[0] for _ in range(3))
+    finally:
+        G.gdpm_context_destroy(ctx)
+    props = torch.cuda.get_device_properties(0)
+    print(json.dumps({"mode": "resources", "sms": props.multi_processor_count,
+                      "lane_peak_at_2070MHz_per_s": props.multi_processor_count * LANES_PER_SM * 2.07e9,
+                      "rates": out}))
+
+
 def main():
     args = parse()
+    if args.mode == "resources":
+        resources_bench(args)
+        return
     if args.mode == "serve":
         serve_bench(args)
         return

@@ -132,27 +132,37 @@ __global__ void __launch_bounds__(256) k_fold(SimParams P, size_t V, double inv_
     if (threadIdx.x == 0 && t != 0.0) atomicAdd(&P.ledger[L_DEPOSITED], t);
 }
 
+// Sums of a voxel's batch tallies b in [b0, b1) of grids of V cells
+// starting at slot `first`: sum e and sum e^2, two FP64 operations per
+// tally.  GB300's FP64 rate (about 5e11 FMA/s), not HBM, bounds the fold,
+// so the batch weights are applied once per voxel, not per tally.
+__device__ __forceinline__ void batch_sums(const SimParams& P, size_t V, size_t first, size_t v,
+                                           int b0, int b1, double& se, double& sq) {
+    for (int b = b0; b < b1; ++b) {
+        const size_t k = (first + size_t(b)) * V + v;
+        const double e = P.tally_mode == 0 ? P.edep[k] : double(P.edep_hi[k]) + double(P.edep_lo[k]);
+        se += e;
+        sq = fma(e, e, sq);
+    }
+}
+
 // All batches at once (batches run side by side, one tally grid each):
 // s1 += sum_b E_b/n_b, s2 += sum_b (E_b/n_b)^2 per voxel (the sums of a run
-// in parts accumulate).
+// in parts accumulate).  The first n_big batches hold one history more.
 __global__ void __launch_bounds__(256) k_fold_batches(SimParams P, size_t V, int nbatch,
                                                       double inv_big, double inv_small, int n_big,
                                                       double* __restrict__ s1, double* __restrict__ s2) {
     __shared__ double s_red[32];
     double dep = 0.0;
+    const int nbig = min(n_big, nbatch);
     for (size_t v = blockIdx.x * size_t(blockDim.x) + threadIdx.x; v < V;
          v += size_t(gridDim.x) * blockDim.x) {
-        double acc1 = 0.0, acc2 = 0.0;
-        for (int b = 0; b < nbatch; ++b) {
-            const size_t k = size_t(b) * V + v;
-            const double e = P.tally_mode == 0 ? P.edep[k] : double(P.edep_hi[k]) + double(P.edep_lo[k]);
-            dep += e;
-            const double x = e * (b < n_big ? inv_big : inv_small);
-            acc1 += x;
-            acc2 = fma(x, x, acc2);
-        }
-        s1[v] += acc1;
-        s2[v] += acc2;
+        double eb = 0.0, qb = 0.0, es = 0.0, qs = 0.0;
+        batch_sums(P, V, 0, v, 0, nbig, eb, qb);
+        batch_sums(P, V, 0, v, nbig, nbatch, es, qs);
+        dep += eb + es;
+        s1[v] += fma(eb, inv_big, es * inv_small);
+        s2[v] += fma(qb, inv_big * inv_big, qs * (inv_small * inv_small));
     }
     const double t = block_sum(dep, s_red);
     if (threadIdx.x == 0 && t != 0.0) atomicAdd(&P.ledger[L_DEPOSITED], t);
@@ -173,17 +183,15 @@ __global__ void __launch_bounds__(256) k_fold_sub(SimParams P, size_t V, uint32_
     const double ib = inv_n[2 * k], is = inv_n[2 * k + 1];
     const uint32_t n_big = nbig[k];
     double dep = 0.0;
+    const int nbg = int(min(n_big, uint32_t(nb)));
     for (size_t v = blockIdx.x * size_t(blockDim.x) + threadIdx.x; v < V;
          v += size_t(gridDim.x) * blockDim.x) {
-        double a1 = 0.0, a2 = 0.0;
-        for (int b = 0; b < nb; ++b) {
-            const size_t i = (size_t(k) * nb + b) * V + v;
-            const double e = P.tally_mode == 0 ? P.edep[i] : double(P.edep_hi[i]) + double(P.edep_lo[i]);
-            dep += e;
-            const double x = e * (uint32_t(b) < n_big ? ib : is);
-            a1 += x;
-            a2 = fma(x, x, a2);
-        }
+        double eb = 0.0, qb = 0.0, es = 0.0, qs = 0.0;
+        batch_sums(P, V, size_t(k) * nb, v, 0, nbg, eb, qb);
+        batch_sums(P, V, size_t(k) * nb, v, nbg, nb, es, qs);
+        dep += eb + es;
+        const double a1 = fma(eb, ib, es * is);
+        const double a2 = fma(qb, ib * ib, qs * (is * is));
         const double mass = double(P.rho[v]) * dvol;
         double im = double(1.0f / float(mass));
         im = im * fma(-mass, im, 2.0);                       // Newton step for 1/mass
