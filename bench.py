@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--workload", default="slab128_6MV", choices=sorted(WORKLOADS))
     ap.add_argument("--histories", type=float, default=1e8)
     ap.add_argument("--batches", type=int, default=100)
+    ap.add_argument("--tally", default="fp64", choices=["fp64", "fp32pair"],
+                    help="dose tally: FP64 atomics, or FP32 hi/lo compensated pairs")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -472,7 +474,7 @@ def main():
               "phantom": {"slab128_6MV": "128^3 slab @0.25cm", "slab128_e20MeV": "128^3 slab @0.25cm",
                           "ct256_imrt7": "256x256x128 ellipsoid CT @0.25cm",
                           "water32_1MeV_pencil": "32^3 water @0.5cm"}[args.workload],
-              "l2": "flushed between steps (256 MB write)",
+              "l2": "flushed between steps (256 MB write)", "tally": args.tally,
               "parallelism": "replicas" if world > 1 else "single GPU"}
 
     if args.impl == "reference":
@@ -510,7 +512,8 @@ def main():
     dev = torch.device("cuda", local)
 
     prob = make(n_hist, args.batches).with_(request_id=rank)
-    eng = G.Engine(prob, device=local, params={G.GDPM_PARAM_PROFILE: 1})
+    eng = G.Engine(prob, device=local, params={G.GDPM_PARAM_PROFILE: 1,
+                                               G.GDPM_PARAM_TALLY_MODE: 1 if args.tally == "fp32pair" else 0})
     V = prob.phantom.n_voxels
     dose = torch.empty(V, dtype=torch.float64, device=dev)
     sigma = torch.empty(V, dtype=torch.float64, device=dev)

@@ -405,10 +405,14 @@ static int validate_run(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const 
 // to ctx->auto_chunk primaries, sized from the device's memory): a phase
 // ends with a tail in which lanes run out of particles, and longer phases
 // make the tail a smaller share.  Batches one after another have one batch
-// per phase, up to 2^20 primaries.
-static uint32_t chunk_of(gdpm_ctx* ctx, uint64_t n_per_run, int parts, bool concurrent) {
+// per phase, up to 2^20 primaries.  A served request keeps phases of at
+// most 2^23 primaries: a persistent phase holds its SMs until it drains, and
+// shorter phases let the small requests that arrive meanwhile get SMs sooner.
+static uint32_t chunk_of(gdpm_ctx* ctx, uint64_t n_per_run, int parts, bool concurrent,
+                         bool serving = false) {
     const uint64_t per = (n_per_run + parts - 1) / parts;
-    const uint32_t chunk = ctx->source_chunk ? ctx->source_chunk : concurrent ? ctx->auto_chunk : (1u << 20);
+    uint32_t chunk = ctx->source_chunk ? ctx->source_chunk : concurrent ? ctx->auto_chunk : (1u << 20);
+    if (serving && !ctx->source_chunk) chunk = std::min(chunk, 1u << 23);
     return uint32_t(std::min<uint64_t>(chunk, per));
 }
 static uint32_t capacity_of(gdpm_ctx* ctx, uint32_t chunk) {
@@ -463,7 +467,7 @@ static int prepare_workspace(gdpm_ctx* ctx, Runner& r, size_t V, uint32_t cap, u
 static size_t bytes_needed(gdpm_ctx* ctx, const Runner& r, size_t V, uint64_t n_hist, int n_batches,
                            bool with_result) {
     const bool conc = side_by_side(ctx, V, n_hist, n_batches);
-    const uint32_t chunk = chunk_of(ctx, conc ? n_hist : n_hist / n_batches + 1, 1, conc);
+    const uint32_t chunk = chunk_of(ctx, conc ? n_hist : n_hist / n_batches + 1, 1, conc, r.serving);
     const uint32_t cap = capacity_of(ctx, chunk);
     auto grow = [](const Buffer& b, size_t want) { return b.bytes >= want ? size_t(0) : want; };
     const Workspace& w = r.ws;
@@ -689,7 +693,8 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
     const size_t V = size_t(ph->nx) * ph->ny * ph->nz;
     const bool conc = side_by_side(ctx, V, n_hist, n_batches);
     const uint32_t nb_small = uint32_t(n_hist / n_batches), nb_rem = uint32_t(n_hist % n_batches);
-    uint32_t chunk = conc ? chunk_of(ctx, n_hist, 1, true) : chunk_of(ctx, n_hist, n_batches, false);
+    uint32_t chunk = conc ? chunk_of(ctx, n_hist, 1, true, r.serving)
+                          : chunk_of(ctx, n_hist, n_batches, false, r.serving);
     const uint32_t cap = capacity_of(ctx, chunk);
     const int n_bins = int(src.weights.size());
     if ((rc = prepare_workspace(ctx, r, V, cap, chunk, n_batches, n_bins, conc))) return rc;
