@@ -487,6 +487,7 @@ def main():
         per = max(2000, int(3.0 * n1 / dt1))
         vals = oracle_rate_parallel(args.workload, per, procs, args.steps)
         v = statistics.median(vals)
+        config = dict(config, parallelism="%d single-thread CPU processes" % procs, tally="fp64 (oracle)")
         sample = per * procs
         line = {"impl": "reference", "metric": "histories/s", "value": v, "unit": "histories/s",
                 "n_gpus": 0, "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * sample / v,
