@@ -50,6 +50,35 @@ OPS = {
 }
 LANES_PER_SM = 128
 
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+# DRAM bytes (read + write) of the phase kernels in one step of slab128_6MV
+# at 1e8 histories and 100 batches, from one ncu capture of that step
+# (profiles/dram_k_phase_slab128_6MV_1e8hist.md).  They hold while the
+# kernel sources hash to TRAFFIC_SOURCES_SHA1; otherwise traffic is null.
+TRAFFIC_SOURCES = ("transport.cu", "common.cuh", "internal.h")
+TRAFFIC_SOURCES_SHA1 = "c3e3bb40140323f19d97b4cfe518da3374abc746"
+TRAFFIC = {"workload": "slab128_6MV", "histories": 100_000_000, "batches": 100,
+           "photon phase": (7, 1.74e10), "electron phase": (7, 1.01e10)}   # (launches, bytes)
+
+
+def measured_traffic(args, kernel):
+    """Average DRAM bytes per launch of the named kernel from the ncu
+    capture, or None when this run is not the captured configuration or the
+    kernels changed."""
+    import hashlib
+    run = (args.workload, int(args.histories), args.batches, args.tally)
+    if run != (TRAFFIC["workload"], TRAFFIC["histories"], TRAFFIC["batches"], "fp64") or kernel not in TRAFFIC:
+        return None
+    h = hashlib.sha1()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(HERE, "paper_1107_3355_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != TRAFFIC_SOURCES_SHA1:
+        return None
+    launches, nbytes = TRAFFIC[kernel]
+    return nbytes / launches
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -629,7 +658,8 @@ def main():
             "gpu_launches": int(agg.get("launches", 0)),
             "roofline": {"bound": "alu", "kernel": kinds[dom], "achieved": achieved,
                          "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                         "traffic": None,
+                         "traffic": measured_traffic(args, kinds[dom]),
+                         "traffic_unit": "DRAM bytes per launch (ncu)",
                          "note": "ALU lane-operations/s vs SMs x 128 lanes x sampled SM clock"},
             "resources": resources,
             "kernel_ms_per_step": [k / args.steps for k in kms],
