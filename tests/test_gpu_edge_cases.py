@@ -1,0 +1,98 @@
+"""Degenerate and limiting cases of the transport, against the oracle.
+
+Beams that never reach the phantom, sources below the absorption energies,
+a one-voxel phantom, an air-filled phantom, a phantom at the largest
+extent per axis, one history per batch, and a ragged history count.  Same
+seed on both sides, so each history's event record must agree (Sec. 2.2.1
+transport; records differ only where FP32 and FP64 arithmetic part ways),
+and the energy ledger must balance.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1107_3355_gb300 import gdpm as G
+from paper_1107_3355_gb300 import workloads as W
+from tests.test_gpu_parity import check_ledger, run_gpu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def problem(phantom, source, n=20_000, nb=10, eabs_photon=0.01, eabs_electron=0.2, e_max=1.5):
+    return W.Problem(phantom, source, n, nb, eabs_photon=eabs_photon, eabs_electron=eabs_electron,
+                     e_min=0.005, e_max=e_max)
+
+
+def same_seed(prob, min_identical=0.99):
+    d_o, s_o, led_o, rec_o, _ = O.run(prob, per_history=True)
+    d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
+    check_ledger(st, prob.n_histories, 1e-5)
+    same = np.all(rec_o == rec_g, axis=1).mean()
+    assert same >= min_identical, same
+    assert st["source_energy"] == pytest.approx(led_o["source_energy"], rel=1e-6)
+    return d_o, d_g, st, led_o
+
+
+def test_beam_that_misses_the_phantom():
+    ph = W.homogeneous_phantom((16, 16, 16), (0.5, 0.5, 0.5), W.WATER, 1.0)
+    src = W.Source(W.PHOTON, W.mono_spectrum(1.0), "pencil", (-5.0, 4.0, 0.0), (0.0, 0.0, 1.0))
+    d_o, d_g, st, led_o = same_seed(problem(ph, src))
+    assert np.all(d_g == 0.0) and np.all(d_o == 0.0)
+    assert st["deposited"] == 0.0
+    assert st["escaped"] == pytest.approx(st["source_energy"], rel=1e-12)
+    assert st["compton"] == 0 and st["el_steps"] == 0
+
+
+@pytest.mark.parametrize("particle,energy", [(W.PHOTON, 0.008), (W.ELECTRON, 0.1)])
+def test_source_below_its_absorption_energy(particle, energy):
+    """Every primary is absorbed where it enters: all energy in the entry
+    voxel of the pencil (central voxel of the z=0 face)."""
+    ph = W.homogeneous_phantom((16, 16, 16), (0.5, 0.5, 0.5), W.WATER, 1.0)
+    src = W.Source(particle, W.mono_spectrum(energy), "pencil", (4.25, 4.25, 0.0), (0.0, 0.0, 1.0))
+    d_o, d_g, st, _ = same_seed(problem(ph, src))
+    entry = 8 + 16 * 8                     # ix = iy = 8, iz = 0
+    assert np.count_nonzero(d_g) == 1 and d_g[entry] > 0
+    assert d_g[entry] == pytest.approx(d_o[entry], rel=1e-6)
+    assert st["deposited"] == pytest.approx(st["source_energy"], rel=1e-6)
+
+
+def test_one_voxel_phantom():
+    ph = W.homogeneous_phantom((1, 1, 1), (1.0, 1.0, 1.0), W.WATER, 1.0)
+    src = W.Source(W.PHOTON, W.mono_spectrum(1.0), "pencil", (0.5, 0.5, 0.0), (0.0, 0.0, 1.0))
+    d_o, d_g, st, led_o = same_seed(problem(ph, src, n=50_000))
+    assert 0 < st["deposited"] < st["source_energy"]
+    assert st["deposited"] == pytest.approx(led_o["deposited"], rel=0.02)
+
+
+def test_air_filled_phantom():
+    ph = W.homogeneous_phantom((32, 32, 32), (0.5, 0.5, 0.5), W.AIR, 0.0012)
+    src = W.pencil_source(ph, 1.0)
+    d_o, d_g, st, led_o = same_seed(problem(ph, src, n=50_000))
+    assert st["escaped"] > 0.99 * st["source_energy"]
+    assert st["compton"] == pytest.approx(led_o["compton"], abs=10)
+
+
+def test_largest_extent_along_an_axis():
+    """nx = 1024 voxels (the per-axis limit), a beam along +x through all of
+    them; 1025 is refused."""
+    ph = W.homogeneous_phantom((1024, 2, 2), (0.1, 0.5, 0.5), W.WATER, 1.0)
+    src = W.Source(W.PHOTON, W.mono_spectrum(1.0), "pencil", (0.0, 0.5, 0.5), (1.0, 0.0, 0.0))
+    d_o, d_g, st, led_o = same_seed(problem(ph, src, n=20_000))
+    along_x = d_g.reshape(2, 2, 1024).sum(axis=(0, 1))
+    assert along_x[:100].sum() > 0 and along_x[512:].sum() > 0    # dose past the middle
+    ctx = G.gdpm_context_create(0)
+    try:
+        big = W.homogeneous_phantom((1025, 1, 1), (0.1, 0.1, 0.1), W.WATER, 1.0)
+        with pytest.raises(G.GdpmError) as e:
+            G.gdpm_phantom_create(ctx, big.shape, big.voxel, big.mat, big.rho)
+        assert e.value.code == G.GDPM_E_ARG
+    finally:
+        G.gdpm_context_destroy(ctx)
+
+
+@pytest.mark.parametrize("n,nb", [(10, 10), (10_007, 10), (2, 2)])
+def test_few_and_ragged_histories_per_batch(n, nb):
+    prob = W.tiny_problem(n_histories=n, n_batches=nb)
+    d_o, d_g, st, _ = same_seed(prob, min_identical=0.95)
+    assert st["n_primary"] == n
