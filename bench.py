@@ -33,7 +33,24 @@ WORKLOADS = {
     "ct256_imrt7": lambda n, nb: W.ct_imrt_problem(n_histories=n, n_batches=nb),
     "slab128_e20MeV": lambda n, nb: W.slab_electron_problem(n_histories=n, n_batches=nb),
     "water32_1MeV_pencil": lambda n, nb: W.tiny_problem(n_histories=n, n_batches=nb),
+    # the phantom cases of Sec. 3.1 (Tables 1 and 2), the paper's own geometry
+    "paper_slab_e20_lung": lambda n, nb: W.paper_slab_problem("lung", W.ELECTRON, n, nb),
+    "paper_slab_e20_bone": lambda n, nb: W.paper_slab_problem("bone", W.ELECTRON, n, nb),
+    "paper_slab_6MV_lung": lambda n, nb: W.paper_slab_problem("lung", W.PHOTON, n, nb),
+    "paper_slab_6MV_bone": lambda n, nb: W.paper_slab_problem("bone", W.PHOTON, n, nb),
 }
+# histories and batches of a step when not given: the paper's for its cases
+DEFAULT_SIZE = {"paper_slab_e20_lung": (2.5e6, 10), "paper_slab_e20_bone": (2.5e6, 10),
+                "paper_slab_6MV_lung": (2.5e8, 10), "paper_slab_6MV_bone": (2.5e8, 10)}
+# The paper's GPU throughput on its Table 2 cases (histories / T_GPU, Tesla
+# C2050, transfers included): the published numbers these workloads compare to.
+PAPER_RATE = {"paper_slab_e20_lung": 2.5e6 / 1.70, "paper_slab_e20_bone": 2.5e6 / 1.65,
+              "paper_slab_6MV_lung": 2.5e8 / 16.1, "paper_slab_6MV_bone": 2.5e8 / 20.5}
+PHANTOM_DESC = {"slab128_6MV": "128^3 slab @0.25cm", "slab128_e20MeV": "128^3 slab @0.25cm",
+                "ct256_imrt7": "256x256x128 ellipsoid CT @0.25cm",
+                "water32_1MeV_pencil": "32^3 water @0.5cm"}
+for _k in DEFAULT_SIZE:
+    PHANTOM_DESC[_k] = "61x61x150 slab @0.5x0.5x0.2cm (Sec. 3.1), %s middle" % _k.rsplit("_", 1)[1]
 
 # Algorithmic ALU operations per unit of work (FP32 arithmetic, integer
 # arithmetic of the Philox rounds and index math, and special-function calls,
@@ -87,8 +104,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gdpm", choices=["gdpm", "reference"])
     ap.add_argument("--workload", default="slab128_6MV", choices=sorted(WORKLOADS))
-    ap.add_argument("--histories", type=float, default=1e8)
-    ap.add_argument("--batches", type=int, default=100)
+    ap.add_argument("--histories", type=float, default=None,
+                    help="histories per step (default 1e8; the paper's count for its cases)")
+    ap.add_argument("--batches", type=int, default=None,
+                    help="batches (default 100; 10 for the paper's cases)")
     ap.add_argument("--tally", default="fp64", choices=["fp64", "fp32pair"],
                     help="dose tally: FP64 atomics, or FP32 hi/lo compensated pairs")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -103,7 +122,13 @@ def parse():
     ap.add_argument("--serve-arc-histories", type=float, default=5e8)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-seed", type=int, default=3)
-    return ap.parse_args()
+    args = ap.parse_args()
+    h, nb = DEFAULT_SIZE.get(args.workload, (1e8, 100))
+    if args.histories is None:
+        args.histories = h
+    if args.batches is None:
+        args.batches = nb
+    return args
 
 
 # ---------------------------------------------------------------- clocks
@@ -500,9 +525,7 @@ def main():
     n_hist = int(args.histories)
     make = WORKLOADS[args.workload]
     config = {"workload": args.workload, "histories_per_step": n_hist, "batches": args.batches,
-              "phantom": {"slab128_6MV": "128^3 slab @0.25cm", "slab128_e20MeV": "128^3 slab @0.25cm",
-                          "ct256_imrt7": "256x256x128 ellipsoid CT @0.25cm",
-                          "water32_1MeV_pencil": "32^3 water @0.5cm"}[args.workload],
+              "phantom": PHANTOM_DESC[args.workload],
               "l2": "flushed between steps (256 MB write)", "tally": args.tally,
               "parallelism": "replicas" if world > 1 else "single GPU"}
 
@@ -649,7 +672,11 @@ def main():
 
     line = {"metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": (value / PAPER_RATE[args.workload]
+                            if args.workload in PAPER_RATE and n_hist == int(DEFAULT_SIZE[args.workload][0])
+                            and args.batches == DEFAULT_SIZE[args.workload][1] else None),
+            "dtype": "f32",
             "data": "synthetic", "config": config,
             "time_to_1pct_s": t_to_1pct,
             "sigma_over_dmax": sig, "histories_for_1pct": n_to_1pct,

@@ -439,6 +439,29 @@ def slab_photon_problem(n_histories=100_000_000, seed=12345, n_batches=100,
                    eabs_photon=0.05, eabs_electron=0.2, e_min=0.005, e_max=6.5, seed=seed)
 
 
+def paper_slab_problem(middle="lung", particle=PHOTON, n_histories=None, n_batches=10,
+                       seed=12345) -> Problem:
+    """The phantom cases of Sec. 3.1 (Table 1): a 30.5 x 30.5 x 30.0 cm slab of
+    0.5 x 0.5 x 0.2 cm voxels (61 x 61 x 150), 5 cm water, 5 cm lung or bone,
+    20 cm water along z; a point source at SSD 90 cm whose 10 x 10 cm field at
+    SAD 100 cm is 9 x 9 cm on the surface; 20 MeV electrons or the 6 MV-like
+    spectrum; absorption energies 200 keV (electrons) and 50 keV (photons);
+    10 batches.  Histories default to the paper's: 2.5e6 electrons, 2.5e8
+    photons.  Lung and bone take this module's densities (0.26, 1.85 g/cm3);
+    the paper does not state them."""
+    mid = {"lung": (LUNG, 0.26), "bone": (BONE, 1.85)}[middle]
+    ph = slab_phantom((61, 61, 150), (0.5, 0.5, 0.2),
+                      layers=((5.0, WATER, 1.0), (10.0, mid[0], mid[1]), (1e30, WATER, 1.0)))
+    if n_histories is None:
+        n_histories = 2_500_000 if particle == ELECTRON else 250_000_000
+    if particle == ELECTRON:
+        src, e_max = field_source(ph, mono_spectrum(20.0), ELECTRON, ssd=90.0, field=(9.0, 9.0)), 21.0
+    else:
+        src, e_max = field_source(ph, kramers_spectrum(), PHOTON, ssd=90.0, field=(9.0, 9.0)), 6.5
+    return Problem(ph, src, n_histories, n_batches, eabs_photon=0.05, eabs_electron=0.2,
+                   e_min=0.005, e_max=e_max, seed=seed)
+
+
 def beamlet_matrix_problem(n_beamlets=400, seed=7, n_batches=1, hist_range=(1e5, 5e6),
                            shape=(128, 128, 128), voxel=(0.25, 0.25, 0.25)) -> Problem:
     """Beamlet dose matrix on the 128^3 slab: n_beamlets square beamlets of
