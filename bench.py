@@ -38,19 +38,26 @@ WORKLOADS = {
     "paper_slab_e20_bone": lambda n, nb: W.paper_slab_problem("bone", W.ELECTRON, n, nb),
     "paper_slab_6MV_lung": lambda n, nb: W.paper_slab_problem("lung", W.PHOTON, n, nb),
     "paper_slab_6MV_bone": lambda n, nb: W.paper_slab_problem("bone", W.PHOTON, n, nb),
+    # the comparison case of Sec. 4: 64^3 water, 15 MeV beams, annihilation off
+    "water64_e15": lambda n, nb: W.water64_problem(W.ELECTRON, n, nb),
+    "water64_g15": lambda n, nb: W.water64_problem(W.PHOTON, n, nb),
 }
 # histories and batches of a step when not given: the paper's for its cases
 DEFAULT_SIZE = {"paper_slab_e20_lung": (2.5e6, 10), "paper_slab_e20_bone": (2.5e6, 10),
-                "paper_slab_6MV_lung": (2.5e8, 10), "paper_slab_6MV_bone": (2.5e8, 10)}
-# The paper's GPU throughput on its Table 2 cases (histories / T_GPU, Tesla
-# C2050, transfers included): the published numbers these workloads compare to.
+                "paper_slab_6MV_lung": (2.5e8, 10), "paper_slab_6MV_bone": (2.5e8, 10),
+                "water64_e15": (1e6, 10), "water64_g15": (4e6, 10)}
+# The paper's GPU throughput on its Table 2 cases and its Sec. 4 comparison
+# case (histories / T_GPU, Tesla C2050, transfers included): the published
+# numbers these workloads compare to.
 PAPER_RATE = {"paper_slab_e20_lung": 2.5e6 / 1.70, "paper_slab_e20_bone": 2.5e6 / 1.65,
-              "paper_slab_6MV_lung": 2.5e8 / 16.1, "paper_slab_6MV_bone": 2.5e8 / 20.5}
+              "paper_slab_6MV_lung": 2.5e8 / 16.1, "paper_slab_6MV_bone": 2.5e8 / 20.5,
+              "water64_e15": 1e6 / 0.47, "water64_g15": 4e6 / 0.90}
 PHANTOM_DESC = {"slab128_6MV": "128^3 slab @0.25cm", "slab128_e20MeV": "128^3 slab @0.25cm",
                 "ct256_imrt7": "256x256x128 ellipsoid CT @0.25cm",
                 "water32_1MeV_pencil": "32^3 water @0.5cm"}
 for _k in DEFAULT_SIZE:
     PHANTOM_DESC[_k] = "61x61x150 slab @0.5x0.5x0.2cm (Sec. 3.1), %s middle" % _k.rsplit("_", 1)[1]
+PHANTOM_DESC["water64_e15"] = PHANTOM_DESC["water64_g15"] = "64^3 water @0.5cm (Sec. 4)"
 
 # Algorithmic ALU operations per unit of work (FP32 arithmetic, integer
 # arithmetic of the Philox rounds and index math, and special-function calls,

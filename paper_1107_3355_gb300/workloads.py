@@ -462,6 +462,22 @@ def paper_slab_problem(middle="lung", particle=PHOTON, n_histories=None, n_batch
                    e_min=0.005, e_max=e_max, seed=seed)
 
 
+def water64_problem(particle=PHOTON, n_histories=None, n_batches=10, seed=12345) -> Problem:
+    """The comparison case of Sec. 4: a homogeneous water phantom of 64^3
+    voxels of 0.5 cm, a 15 MeV monoenergetic, mono-directional beam entering
+    normally, annihilation photons switched off; 1e6 electrons or 4e6
+    photons by default.  The paper states neither the beam's width nor the
+    cutoffs: the beam is read as a pencil at the centre of the entry face and
+    the absorption energies as those of Sec. 3.1 (200 keV electrons, 50 keV
+    photons)."""
+    ph = homogeneous_phantom((64, 64, 64), (0.5, 0.5, 0.5), WATER, 1.0)
+    if n_histories is None:
+        n_histories = 1_000_000 if particle == ELECTRON else 4_000_000
+    return Problem(ph, pencil_source(ph, 15.0, particle), n_histories, n_batches, eabs_photon=0.05,
+                   eabs_electron=0.2, e_min=0.005, e_max=16.0, seed=seed,
+                   flags=FLAG_NO_ANNIHILATION)
+
+
 def beamlet_matrix_problem(n_beamlets=400, seed=7, n_batches=1, hist_range=(1e5, 5e6),
                            shape=(128, 128, 128), voxel=(0.25, 0.25, 0.25)) -> Problem:
     """Beamlet dose matrix on the 128^3 slab: n_beamlets square beamlets of
