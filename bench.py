@@ -629,9 +629,10 @@ def main():
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         tb = G.gdpm_tables_build(ctx, prob.phantom.materials, prob.e_min, prob.e_max, prob.n_energy,
-                                 prob.eabs_photon, prob.eabs_electron, prob.ms_loss_fraction, 0)
+                                 prob.eabs_photon, prob.eabs_electron, prob.ms_loss_fraction,
+                                 G.table_flags(prob))
         ph = G.gdpm_phantom_create(ctx, prob.phantom.shape, prob.phantom.voxel, mat_h, rho_h)
-        G.gdpm_source_set(ctx, prob.source)
+        G.gdpm_source_set(ctx, G.problem_source(prob))
         G.gdpm_simulate(ctx, ph, tb, n_hist, args.batches, dose_h, sig_h)
         G.gdpm_phantom_destroy(ph)
         G.gdpm_tables_destroy(tb)

@@ -110,7 +110,9 @@ __device__ double s_restricted(const Eph& q, double T, double wcc, double wcb) {
 }
 
 // int_a^b dT/S_r(T) with T = e^s, composite Simpson in s (32 panels),
-// split at the kinks of S_r (T = 2 W_cc and T = W_cb).
+// split at the kinks of S_r (T = 2 W_cc and T = W_cb).  Called by a whole
+// warp: lane k takes Simpson node k of each piece (lane 0 also node 32) and
+// the weighted values are summed across the warp; every lane gets the sum.
 __device__ double range_piece(const Eph& q, double a, double b, double wcc, double wcb) {
     if (b <= a) return 0.0;
     double cuts[4] = {a, 0.0, 0.0, b};
@@ -119,18 +121,20 @@ __device__ double range_piece(const Eph& q, double a, double b, double wcc, doub
     if (k1 > a && k1 < b) cuts[nc++] = k1;
     if (k2 > a && k2 < b && k2 != k1) cuts[nc++] = k2;
     cuts[nc] = b;
+    const int lane = int(threadIdx.x & 31u);
+    constexpr int np = 32;
     double total = 0.0;
     for (int c = 0; c < nc; ++c) {
         const double sa = log(cuts[c]), sb = log(cuts[c + 1]);
-        const int np = 32;
         const double h = (sb - sa) / np;
-        double acc = 0.0;
-        for (int k = 0; k <= np; ++k) {
+        auto node = [&](int k) {
             const double T = exp(sa + k * h);
-            const double f = T / s_restricted(q, T, wcc, wcb);
             const double wgt = (k == 0 || k == np) ? 1.0 : ((k & 1) ? 4.0 : 2.0);
-            acc += wgt * f;
-        }
+            return wgt * T / s_restricted(q, T, wcc, wcb);
+        };
+        double acc = node(lane);
+        if (lane == 0) acc += node(np);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
         total += acc * h / 3.0;
     }
     return total;
@@ -154,36 +158,53 @@ __device__ double r_interp(const double* R, double lemin, double dle, int n, dou
 }
 
 // ---------------------------------------------------------------- kernels
+// One warp per table point (material m, energy i): lane 0 stores the point
+// values, the warp shares the range integral over [E_{i-1}, E_i].
 __global__ void k_point(Build B) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int idx = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (idx >= B.n_mat * B.n) return;
     const int m = idx / B.n, i = idx % B.n;
     const MatDev& mt = B.mats[m];
     const double E = exp(B.lemin + i * B.dle);
     const bool conly = (B.flags & GDPM_FLAG_COMPTON_ONLY) != 0;
-    B.mu_c[idx] = mat_ne(mt) * sigma_kn(E);
-    B.mu_pe[idx] = conly ? 0.0 : kCpe * mat_sum(mt, 0) / (E * E * E);
     const double k = E / kMC2;
     const double th = k > 2.0 ? (k - 2.0) / k : 0.0;
-    B.mu_pair[idx] = conly ? 0.0 : kAlpha * kRe * kRe * mat_sum(mt, 1) * th * th * th;
     const Eph q = eph_of(mt);
+    const double iv = i > 0 ? range_piece(q, exp(B.lemin + (i - 1) * B.dle), E, B.eabs_el, B.eabs_ph) : 0.0;
+    if ((threadIdx.x & 31u) != 0u) return;
+    B.mu_c[idx] = mat_ne(mt) * sigma_kn(E);
+    B.mu_pe[idx] = conly ? 0.0 : kCpe * mat_sum(mt, 0) / (E * E * E);
+    B.mu_pair[idx] = conly ? 0.0 : kAlpha * kRe * kRe * mat_sum(mt, 1) * th * th * th;
     double sig, loss;
     moller_hard(q, E, B.eabs_el, sig, loss);
     B.sig_m[idx] = sig;
     B.sig_b[idx] = E > B.eabs_ph ? q.bconst * log(E / B.eabs_ph) : 0.0;
-    B.intv[idx] = i > 0 ? range_piece(q, exp(B.lemin + (i - 1) * B.dle), E, B.eabs_el, B.eabs_ph) : 0.0;
+    B.intv[idx] = iv;
 }
 
-// Per material: accumulate the range, shift it to R(E_abs) = 0, majorant
-// of the hard cross sections, X0.
+// Per material (one warp each): accumulate the range, shift it to
+// R(E_abs) = 0, majorant of the hard cross sections, X0.  The running sum
+// goes 32 points at a time: an inclusive shuffle scan of the chunk plus the
+// total so far.
 __global__ void k_scan(Build B) {
-    const int m = threadIdx.x;
+    const int m = int(blockIdx.x);
+    const int lane = int(threadIdx.x & 31u);
     if (m >= B.n_mat) return;
     const int n = B.n;
     double* R = B.R + size_t(m) * n;
     const double* I = B.intv + size_t(m) * n;
-    R[0] = 0.0;
-    for (int i = 1; i < n; ++i) R[i] = R[i - 1] + I[i];
+    double carry = 0.0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        double v = (i > 0 && i < n) ? I[i] : 0.0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (i < n) R[i] = carry + v;
+        carry += __shfl_sync(0xFFFFFFFFu, v, 31);
+    }
+    __syncwarp();
     const Eph q = eph_of(B.mats[m]);
     // c = int_{E_0}^{E_abs} dT/S_r
     const double le = log(B.eabs_el);
@@ -193,11 +214,14 @@ __global__ void k_scan(Build B) {
     const double c = R[k] + (B.eabs_el >= Ek ? range_piece(q, Ek, B.eabs_el, B.eabs_el, B.eabs_ph)
                                              : -range_piece(q, B.eabs_el, Ek, B.eabs_el, B.eabs_ph));
     double smax = 0.0;
-    for (int i = 0; i < n; ++i) {
+    for (int i = lane; i < n; i += 32) {
         R[i] -= c;
         const double s = B.sig_m[size_t(m) * n + i] + B.sig_b[size_t(m) * n + i];
         smax = s > smax ? s : smax;
     }
+    for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xFFFFFFFFu, smax, o));
+    __syncwarp();
+    if (lane != 0) return;
     double* sc = B.scal + 8 * m;
     sc[0] = 1.0 / q.bconst;
     sc[1] = smax;
@@ -247,8 +271,10 @@ __global__ void k_atab(Build B) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= B.n_a) return;
     const double g1 = exp(B.a_l1lo + k * B.a_dl);
+    // bisection on [-80, 40]: 72 halvings leave 120 / 2^72 = 2.5e-20, below
+    // the FP64 spacing of any root the table needs
     double lo = -80.0, hi = 40.0;
-    for (int it = 0; it < 140; ++it) {
+    for (int it = 0; it < 72; ++it) {
         const double mid = 0.5 * (lo + hi), A = exp(mid);
         const double h = 2.0 * A * ((1.0 + A) * log1p(1.0 / A) - 1.0);
         if (h < g1) lo = mid; else hi = mid;
@@ -309,11 +335,11 @@ int build_tables_device(gdpm_ctx* ctx, gdpm_tables* t, const gdpm_material_desc*
     cudaStream_t st = ctx->stream;
     GDPM_CUDA_TRY(cudaMemcpyAsync(dm.p, hm.data(), sizeof(MatDev) * M, cudaMemcpyHostToDevice, st));
     const int th = 128;
-    k_point<<<int((mn + th - 1) / th), th, 0, st>>>(B);
-    k_scan<<<1, 32, 0, st>>>(B);
+    k_point<<<int((mn * 32 + th - 1) / th), th, 0, st>>>(B);
+    k_scan<<<M, 32, 0, st>>>(B);
     k_derived<<<int((mn + th - 1) / th), th, 0, st>>>(B);
     k_rinv<<<int((size_t(M) * t->n_r + th - 1) / th), th, 0, st>>>(B);
-    k_atab<<<(t->n_a + th - 1) / th, th, 0, st>>>(B);
+    k_atab<<<(t->n_a + 31) / 32, 32, 0, st>>>(B);
     GDPM_CUDA_TRY(cudaGetLastError());
     std::vector<double> hs(8 * M);
     GDPM_CUDA_TRY(cudaMemcpyAsync(hs.data(), scal.p, sizeof(double) * 8 * M, cudaMemcpyDeviceToHost, st));

@@ -409,6 +409,20 @@ def gdpm_simulate_noalloc(ctx, phantom, tables, n_histories, n_batches, dose_out
 
 # ------------------------------------------------------------------ marshalling helper
 
+def table_flags(prob) -> int:
+    """The physics switches of a Problem that belong to the tables."""
+    return prob.flags & (GDPM_FLAG_COMPTON_ONLY | GDPM_FLAG_NO_HARD | GDPM_FLAG_SAUTER)
+
+
+def problem_source(prob):
+    """A Problem's source, with annihilation off when the Problem says so."""
+    src = prob.source
+    if prob.flags & W.FLAG_NO_ANNIHILATION and src.annihilation:
+        import dataclasses
+        src = dataclasses.replace(src, annihilation=False)
+    return src
+
+
 class Engine:
     """One context bound to a problem's phantom, tables and source.
 
@@ -433,14 +447,8 @@ class Engine:
         self.phantom = gdpm_phantom_create(self.ctx, ph.shape, ph.voxel, self.mat, self.rho)
         self.tables = gdpm_tables_build(self.ctx, ph.materials, prob.e_min, prob.e_max,
                                         prob.n_energy, prob.eabs_photon, prob.eabs_electron,
-                                        prob.ms_loss_fraction,
-                                        prob.flags & (GDPM_FLAG_COMPTON_ONLY | GDPM_FLAG_NO_HARD |
-                                                      GDPM_FLAG_SAUTER))
-        src = prob.source
-        if prob.flags & W.FLAG_NO_ANNIHILATION and src.annihilation:
-            import dataclasses
-            src = dataclasses.replace(src, annihilation=False)
-        gdpm_source_set(self.ctx, src)
+                                        prob.ms_loss_fraction, table_flags(prob))
+        gdpm_source_set(self.ctx, problem_source(prob))
 
     def set_param(self, param, value):
         gdpm_set_param(self.ctx, param, value)
