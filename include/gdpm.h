@@ -169,7 +169,8 @@ enum {
                                         by side (one tally grid per batch, n_batches <= 128,
                                         phases shared by all batches: up to 32M primaries
                                         where their queues fit in a quarter of the device's
-                                        memory, else 16M, 8M ...) */
+                                        memory, else 16M, 8M ...; at most 8M for requests
+                                        served by gdpm_request_submit) */
     GDPM_PARAM_CONCURRENT_MAX_HIST = 16, /* auto: side by side when histories per batch <= this
                                             (default 4e9, no limit) ... */
     GDPM_PARAM_CONCURRENT_MAX_MB = 17,   /* ... and the per-batch grids fit in this (default 16384) */
