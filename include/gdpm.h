@@ -152,7 +152,7 @@ int gdpm_context_destroy(gdpm_ctx *ctx);
 int gdpm_set_param(gdpm_ctx *ctx, int param, double value);
 enum {
     GDPM_PARAM_QUEUE_CAPACITY = 1,   /* particles per queue buffer (0 = automatic) */
-    GDPM_PARAM_BLOCK_THREADS = 2,    /* 64..1024, multiple of 32 (default 256) */
+    GDPM_PARAM_BLOCK_THREADS = 2,    /* 64..256, multiple of 32 (default 256) */
     GDPM_PARAM_BLOCKS_PER_SM = 3,    /* persistent CTAs per SM (0 = occupancy) */
     GDPM_PARAM_TALLY_MODE = 4,       /* 0: FP64 atomics; 1: FP32 compensated hi/lo pair */
     GDPM_PARAM_SOURCE_CHUNK = 5,     /* max primaries per transport phase (0 = auto) */
