@@ -151,11 +151,11 @@ int gdpm_context_destroy(gdpm_ctx *ctx);
  * out of range. */
 int gdpm_set_param(gdpm_ctx *ctx, int param, double value);
 enum {
-    GDPM_PARAM_QUEUE_CAPACITY = 1,   /* particles per queue buffer (0 = automatic) */
+    GDPM_PARAM_QUEUE_CAPACITY = 1,   /* particles per queue buffer (0 = automatic), <= 2^31 */
     GDPM_PARAM_BLOCK_THREADS = 2,    /* 64..256, multiple of 32 (default 256) */
     GDPM_PARAM_BLOCKS_PER_SM = 3,    /* persistent CTAs per SM (0 = occupancy) */
     GDPM_PARAM_TALLY_MODE = 4,       /* 0: FP64 atomics; 1: FP32 compensated hi/lo pair */
-    GDPM_PARAM_SOURCE_CHUNK = 5,     /* max primaries per transport phase (0 = auto) */
+    GDPM_PARAM_SOURCE_CHUNK = 5,     /* max primaries per transport phase (0 = auto), <= 2^28 */
     GDPM_PARAM_MAX_PHASES = 6,       /* phase cap per batch -> GDPM_E_TIMEOUT */
     GDPM_PARAM_REQUEST_ID = 7,       /* xored into the Philox key high word */
     GDPM_PARAM_SPECULATIVE = 8,      /* phase pairs issued per host check (>=1) */

@@ -1040,7 +1040,8 @@ int gdpm_set_param(gdpm_ctx* ctx, int param, double v) {
     if (!ctx) return GDPM_E_ARG;
     switch (param) {
     case GDPM_PARAM_QUEUE_CAPACITY:
-        if (v < 0 || v > 4.0e9) return GDPM_E_ARG;
+        // a phase's work indices (primaries + queued particles) are 32-bit
+        if (v < 0 || v > 2147483648.0) return GDPM_E_ARG;
         ctx->queue_capacity = uint32_t(v);
         return GDPM_OK;
     case GDPM_PARAM_BLOCK_THREADS:
@@ -1056,7 +1057,8 @@ int gdpm_set_param(gdpm_ctx* ctx, int param, double v) {
         ctx->tally_mode = int(v);
         return GDPM_OK;
     case GDPM_PARAM_SOURCE_CHUNK:
-        if (v < 0 || v > 4.0e9) return GDPM_E_ARG;
+        // the automatic queue capacity, 8 x chunk + 65536, must stay 32-bit
+        if (v < 0 || v > 268435456.0) return GDPM_E_ARG;
         ctx->source_chunk = uint32_t(v);
         return GDPM_OK;
     case GDPM_PARAM_MAX_PHASES:

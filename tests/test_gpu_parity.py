@@ -325,6 +325,11 @@ def test_bad_inputs_rejected():
         with pytest.raises(G.GdpmError):
             G.gdpm_phantom_create(eng.ctx, prob.phantom.shape, prob.phantom.voxel,
                                   prob.phantom.mat, bad_rho)
+        for param, bad in ((G.GDPM_PARAM_SOURCE_CHUNK, 2 ** 28 + 1), (G.GDPM_PARAM_QUEUE_CAPACITY, 2 ** 31 + 1),
+                           (G.GDPM_PARAM_BLOCK_THREADS, 512), (G.GDPM_PARAM_BLOCK_THREADS, 100)):
+            with pytest.raises(G.GdpmError) as e:            # 32-bit work indices, launch bounds
+                G.gdpm_set_param(eng.ctx, param, bad)
+            assert e.value.code == G.GDPM_E_ARG
         hot = W.Source(W.PHOTON, W.mono_spectrum(5.0), "pencil", (8, 8, 0), (0, 0, 1))
         G.gdpm_source_set(eng.ctx, hot)          # 5 MeV is beyond this table grid (1.5 MeV)
         with pytest.raises(G.GdpmError):
