@@ -638,6 +638,19 @@ def main():
         G.gdpm_tables_destroy(tb)
         e2e_s += time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, world, dev)          # the slowest rank's end-to-end time
+
+    # time to 1 % measured by running to it: a pilot of up to 5e7 histories,
+    # then runs of the histories sigma/Dmax ~ N^(-1/2) predicts (wall clock,
+    # device outputs, after the timed region)
+    pilot = min(n_hist, 50_000_000)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    st1, total1 = G.gdpm_simulate_to_precision(eng.ctx, eng.phantom, eng.tables, 0.01, pilot,
+                                               2 ** 32 - 1, args.batches, dose, sigma)
+    torch.cuda.synchronize(dev)
+    run_to_1pct = {"s": time.perf_counter() - t0, "pilot_histories": pilot,
+                   "histories_last_run": st1["n_primary"], "histories_all_runs": total1,
+                   "sigma_over_dmax": st1["sigma_over_dmax"]}
     e2e_value = world * args.e2e_steps * n_hist / e2e_s if args.e2e_steps > 0 else None
 
     # roofline of the dominant kernel kind, from its live event time
@@ -687,6 +700,7 @@ def main():
             "dtype": "f32",
             "data": "synthetic", "config": config,
             "time_to_1pct_s": t_to_1pct,
+            "time_to_1pct_run": run_to_1pct,
             "sigma_over_dmax": sig, "histories_for_1pct": n_to_1pct,
             "e2e": {"value": e2e_value, "unit": "histories/s",
                     "h2d_bytes_per_step": int(V * 5), "d2h_bytes_per_step": int(V * 16)},

@@ -227,6 +227,27 @@ int gdpm_source_set(gdpm_ctx *ctx, const gdpm_source_desc *src);
 int gdpm_simulate(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
                   int n_batches, double *dose_out, double *sigma_out, gdpm_stats *stats_out);
 
+/* Run until the dose reaches a target precision (Sec. 3.1's metric:
+ * sigma/Dmax averaged over the voxels with D > 0.5 Dmax, which Sec. 3.1 and
+ * Sec. 3.2 bring below 1 %).  A pilot run of n_pilot histories measures
+ * sigma/Dmax; since it falls as N^(-1/2), the next run takes
+ * n (sigma/Dmax / target)^2 x 1.4 histories (x 1.05 after that first step:
+ * a small pilot reads sigma/Dmax low, since noise inflates Dmax), and so on
+ * (at most 8 runs, at most n_max histories in one run) until a run meets
+ * the target.  A pilot of a few percent of the histories the target needs
+ * usually reaches it in one more run.  Each
+ * run is a complete gdpm_simulate in n_batches batches; the outputs and
+ * stats_out are those of the last run, *n_total_out (may be NULL) the
+ * histories of all runs together.  A run capped at n_max that misses the
+ * target still returns GDPM_OK: compare stats_out->sigma_over_dmax with
+ * the target.  dose_out / sigma_out as for gdpm_simulate (may be NULL).
+ * Errors: GDPM_E_ARG (target <= 0, n_pilot < n_batches, n_max < n_pilot or
+ * >= 2^32), GDPM_E_STATE (per-history records are set), and those of
+ * gdpm_simulate. */
+int gdpm_simulate_to_precision(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, double target,
+                               uint64_t n_pilot, uint64_t n_max, int n_batches, double *dose_out,
+                               double *sigma_out, gdpm_stats *stats_out, uint64_t *n_total_out);
+
 /* Checkpoint / resume.  The state of a run is the per-voxel sums over its
  * finished batches, sum1 = sum_b x_b and sum2 = sum_b x_b^2 with x_b the
  * energy per history of batch b (Sec. 2.2.1), plus the index of the next

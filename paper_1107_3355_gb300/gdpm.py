@@ -50,7 +50,7 @@ EXPORTED = ["gdpm_context_create", "gdpm_context_destroy", "gdpm_set_param",
             "gdpm_strerror", "gdpm_debug_philox", "gdpm_debug_sample", "gdpm_tables_export",
             "gdpm_debug_sources", "gdpm_debug_beamlets", "gdpm_simulate_noalloc",
             "gdpm_simulate_beamlets", "gdpm_autotune", "gdpm_simulate_part", "gdpm_finalize",
-            "gdpm_microbench"]
+            "gdpm_microbench", "gdpm_simulate_to_precision"]
 
 
 class gdpm_material_desc(C.Structure):
@@ -156,6 +156,8 @@ def lib():
                 "gdpm_simulate_part": [vp, vp, vp, u64, i, i, i, vp, vp, C.POINTER(gdpm_stats)],
                 "gdpm_finalize": [vp, vp, i, vp, vp, vp, vp, C.POINTER(gdpm_stats)],
                 "gdpm_microbench": [vp, i, vp, u64, u64, C.POINTER(d), C.POINTER(d)],
+                "gdpm_simulate_to_precision": [vp, vp, vp, d, u64, u64, i, vp, vp, C.POINTER(gdpm_stats),
+                                               C.POINTER(u64)],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -281,6 +283,18 @@ def gdpm_simulate(ctx, phantom, tables, n_histories, n_batches, dose_out=None, s
     _check(lib().gdpm_simulate(ctx, phantom, tables, n_histories, n_batches, _ptr(dose_out),
                                _ptr(sigma_out), C.byref(st)), "gdpm_simulate")
     return st.as_dict()
+
+
+def gdpm_simulate_to_precision(ctx, phantom, tables, target, n_pilot, n_max, n_batches,
+                               dose_out=None, sigma_out=None):
+    """Run until sigma/Dmax <= target (Sec. 3.1 metric); returns (stats of
+    the last run, histories of all runs)."""
+    st = gdpm_stats()
+    total = C.c_uint64()
+    _check(lib().gdpm_simulate_to_precision(ctx, phantom, tables, target, int(n_pilot), int(n_max),
+                                            n_batches, _ptr(dose_out), _ptr(sigma_out), C.byref(st),
+                                            C.byref(total)), "gdpm_simulate_to_precision")
+    return st.as_dict(), total.value
 
 
 def gdpm_simulate_beamlets(ctx, phantom, tables, n_histories, n_batches, dose_out,
