@@ -100,3 +100,54 @@ def test_request_that_can_never_fit_is_refused():
         assert st["n_primary"] == 20_000 and d.max() > 0
     finally:
         eng.close()
+
+
+def test_submit_and_poll_from_several_threads():
+    """gdpm_request_submit / gdpm_request_poll are the thread-safe calls of a
+    context: four host threads each submit and poll three requests at once,
+    and every result equals gdpm_simulate with the same stream id."""
+    import threading
+    prob = W.tiny_problem(n_histories=50_000, n_batches=10)
+    eng = G.Engine(prob)
+    V = prob.phantom.n_voxels
+    ids = [100 + 10 * t + j for t in range(4) for j in range(3)]
+    try:
+        ref = {}
+        for sid in ids:
+            G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_REQUEST_ID, sid)
+            d, _, _ = eng.run()
+            ref[sid] = d.cpu().numpy()
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_REQUEST_ID, 0)
+        results, errors = {}, []
+
+        def worker(t):
+            try:
+                for j in range(3):
+                    sid = 100 + 10 * t + j
+                    rid = G.gdpm_request_submit(eng.ctx, eng.phantom, eng.tables, prob.source, 50_000,
+                                                10, stream_id=sid)
+                    d, s = np.empty(V), np.empty(V)
+                    t0 = time.time()
+                    while True:
+                        done, _ = G.gdpm_request_poll(eng.ctx, rid, d, s)
+                        if done:
+                            break
+                        if time.time() - t0 > 120:
+                            raise TimeoutError(sid)
+                        time.sleep(0.0005)
+                    results[sid] = d
+            except Exception as e:                      # reported below, on the main thread
+                errors.append(e)
+
+        threads = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join(timeout=300)
+        assert not any(th.is_alive() for th in threads)
+    finally:
+        eng.close()
+    assert not errors, errors
+    assert sorted(results) == sorted(ids)
+    for sid in ids:
+        np.testing.assert_allclose(results[sid], ref[sid], rtol=1e-9, atol=1e-12 * ref[sid].max())
