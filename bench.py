@@ -120,6 +120,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-run-to-1pct", action="store_true",
+                    help="skip the measured run to 1 %% (e.g. for a launch list of the timed steps)")
     ap.add_argument("--mode", default="throughput", choices=["throughput", "serve", "beamlets",
                                                              "resources"])
     ap.add_argument("--matrix-beamlets", type=int, default=400)
@@ -642,15 +644,17 @@ def main():
     # time to 1 % measured by running to it: a pilot of up to 5e7 histories,
     # then runs of the histories sigma/Dmax ~ N^(-1/2) predicts (wall clock,
     # device outputs, after the timed region)
-    pilot = min(n_hist, 50_000_000)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    st1, total1 = G.gdpm_simulate_to_precision(eng.ctx, eng.phantom, eng.tables, 0.01, pilot,
-                                               2 ** 32 - 1, args.batches, dose, sigma)
-    torch.cuda.synchronize(dev)
-    run_to_1pct = {"s": time.perf_counter() - t0, "pilot_histories": pilot,
-                   "histories_last_run": st1["n_primary"], "histories_all_runs": total1,
-                   "sigma_over_dmax": st1["sigma_over_dmax"]}
+    run_to_1pct = None
+    if not args.no_run_to_1pct:
+        pilot = min(n_hist, 50_000_000)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        st1, total1 = G.gdpm_simulate_to_precision(eng.ctx, eng.phantom, eng.tables, 0.01, pilot,
+                                                   2 ** 32 - 1, args.batches, dose, sigma)
+        torch.cuda.synchronize(dev)
+        run_to_1pct = {"s": time.perf_counter() - t0, "pilot_histories": pilot,
+                       "histories_last_run": st1["n_primary"], "histories_all_runs": total1,
+                       "sigma_over_dmax": st1["sigma_over_dmax"]}
     e2e_value = world * args.e2e_steps * n_hist / e2e_s if args.e2e_steps > 0 else None
 
     # roofline of the dominant kernel kind, from its live event time
