@@ -174,12 +174,16 @@ enum {
     GDPM_PARAM_CONCURRENT_MAX_HIST = 16, /* auto: side by side when histories per batch <= this
                                             (default 4e9, no limit) ... */
     GDPM_PARAM_CONCURRENT_MAX_MB = 17,   /* ... and the per-batch grids fit in this (default 16384) */
-    GDPM_PARAM_GRAPH = 18            /* 1: batches side by side run their phases as one
+    GDPM_PARAM_GRAPH = 18,           /* 1: batches side by side run their phases as one
                                         CUDA graph launch, a conditional WHILE node that repeats
                                         photon phase, electron phase and a control kernel on the
                                         device until nothing is left (no host checks); 0: the host
                                         loop (default).  Profiling (GDPM_PARAM_PROFILE) uses the
                                         host loop. */
+    GDPM_PARAM_MAX_ITERS = 19        /* loop trips a warp may take in one transport phase
+                                        (1..2^31, default 2^22, far above real use).  A warp
+                                        that reaches it abandons its particles and the call
+                                        returns GDPM_E_TIMEOUT; the next call starts clean. */
 };
 
 /* ------------------------------------------------------------------ inputs */

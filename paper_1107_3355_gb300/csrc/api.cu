@@ -375,7 +375,7 @@ static SimParams base_params(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, u
     P.key0 = uint32_t(ctx->seed);
     P.key1 = uint32_t(ctx->seed >> 32) ^ request_id;
     P.tally_mode = ctx->tally_mode;
-    P.max_iters = 1u << 22;   // per-warp iterations in one phase; far above real use
+    P.max_iters = ctx->max_iters;   // loop trips per warp and phase (GDPM_PARAM_MAX_ITERS)
     P.tally_lo = 0;
     P.tally_hi = uint64_t(ph->nx) * ph->ny * ph->nz;   // one grid; widened by batched runs
     P.n_records = 0;
@@ -1072,6 +1072,10 @@ int gdpm_set_param(gdpm_ctx* ctx, int param, double v) {
     case GDPM_PARAM_GRAPH:
         if (v != 0 && v != 1) return GDPM_E_ARG;
         ctx->use_graph = int(v);
+        return GDPM_OK;
+    case GDPM_PARAM_MAX_ITERS:
+        if (v < 1 || v > 2147483648.0) return GDPM_E_ARG;
+        ctx->max_iters = uint32_t(v);
         return GDPM_OK;
     case GDPM_PARAM_SPECULATIVE:
         if (v < 1 || v > 64) return GDPM_E_ARG;

@@ -304,6 +304,30 @@ def test_phase_cap_reported():
         eng.close()
 
 
+def test_iteration_cap_reported_and_context_stays_usable():
+    """A persistent phase loop that reaches its trip limit abandons its
+    particles, sets the status word and the call returns GDPM_E_TIMEOUT; the
+    next call on the same context is complete and equal to the first."""
+    prob = W.tiny_problem(n_histories=20_000, n_batches=10)
+    eng = G.Engine(prob)
+    try:
+        d0, _, st0 = eng.run()
+        d0 = d0.cpu().numpy()
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_MAX_ITERS, 2)
+        with pytest.raises(G.GdpmError) as e:
+            eng.run()
+        assert e.value.code == G.GDPM_E_TIMEOUT
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_MAX_ITERS, 1 << 22)
+        d1, _, st1 = eng.run()
+        d1 = d1.cpu().numpy()
+        with pytest.raises(G.GdpmError):
+            G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_MAX_ITERS, 0)
+    finally:
+        eng.close()
+    assert st1["compton"] == st0["compton"] and st1["el_steps"] == st0["el_steps"]
+    np.testing.assert_allclose(d1, d0, rtol=1e-9, atol=1e-12 * d0.max())
+
+
 def test_bad_inputs_rejected():
     prob = W.tiny_problem(n_histories=1000, n_batches=10)
     eng = G.Engine(prob)
