@@ -81,7 +81,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # (profiles/dram_k_phase_slab128_6MV_1e8hist.md).  They hold while the
 # kernel sources hash to TRAFFIC_SOURCES_SHA1; otherwise traffic is null.
 TRAFFIC_SOURCES = ("transport.cu", "common.cuh", "internal.h")
-TRAFFIC_SOURCES_SHA1 = "c3e3bb40140323f19d97b4cfe518da3374abc746"
+TRAFFIC_SOURCES_SHA1 = "ec2bc4c6a88156324dd8cf61a72a1f16ac70c16d"
 TRAFFIC = {"workload": "slab128_6MV", "histories": 100_000_000, "batches": 100,
            "photon phase": (7, 1.74e10), "electron phase": (7, 1.01e10)}   # (launches, bytes)
 
