@@ -5,7 +5,8 @@
  * photon/electron Monte Carlo dose calculation of Jia et al. (gDPM v2.0,
  * arXiv:1107.3355), written to be checked by eye against the method's
  * definitions.  It shares no code with the CUDA path.  Only tests/,
- * __graft_entry__.smoke() and bench.py's CPU-baseline leg may load it.
+ * __graft_entry__.smoke() and bench.py's CPU-baseline and reference legs
+ * may load it.
  *
  * What the paper fixes, and where:
  *   - Sec. 2.1: Woodcock tracking for photons; condensed history for
@@ -31,6 +32,13 @@
  * Z^4/E^3 photoelectric, Bethe-Heitler-shaped pair, Bethe stopping power,
  * Moller, Kramers-type 1/k bremsstrahlung, screened Rutherford angular
  * distribution with Rossi-Greisen scattering power), each marked READING.
+ *
+ * Pins (tests/test_oracle_pins.py, test_oracle_beamlets.py,
+ * test_oracle_variants.py, test_oracle_paper_values.py): each function is
+ * checked against closed forms, invariants, exact probabilities or
+ * brute-force histograms, and the batch precision against the values the
+ * paper prints (Table 1).  Parity unpinned: agreement of the dose itself with
+ * DPM's physics data, which is not available; the formulas here are readings.
  *
  * Units: MeV, cm, g/cm3; per-unit-density quantities in cm2/g or MeV cm2/g.
  */

@@ -1,6 +1,6 @@
 """ctypes wrapper around the CPU oracle (``gdpm_oracle.c``) -- TEST INFRASTRUCTURE.
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline and reference legs of
 ``bench.py`` use this module.  It converts a ``workloads.Problem`` into the
 oracle's own C struct and calls the plain single-threaded FP64 oracle.
 It imports nothing from the CUDA path.
