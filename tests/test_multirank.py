@@ -81,3 +81,19 @@ def test_parallel_oracle_baseline_runs_disjoint_processes():
     rates = bench.oracle_rate_parallel("water32_1MeV_pencil", 300, 2, steps=2)
     assert len(rates) == 2 and all(r > 0 for r in rates)
     assert bench.host_cores() >= 1
+
+
+def test_sharded_oracle_matches_one_process():
+    """The test helper that spreads the oracle over host cores: four shards
+    on disjoint streams, combined, agree with one process of the same size
+    (per-voxel t-test, Sec. 3.1) and carry the N^-1/2 uncertainty."""
+    from oracle import oracle as O
+    from paper_1107_3355_gb300 import workloads as W
+    from tests._oracle_parallel import run_sharded
+    from tests._stats import sigma_over_dmax, t_test
+    prob = W.tiny_problem(n_histories=8000, n_batches=10)
+    d1, s1, _ = O.run(prob)
+    d4, s4 = run_sharded(prob, 8000, procs=4)
+    r = t_test(d1, s1, d4, s4, high_frac=0.1)
+    assert r["P_high"] > 0.9, r
+    assert sigma_over_dmax(d4, s4) == pytest.approx(sigma_over_dmax(d1, s1), rel=0.25)
