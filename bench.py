@@ -81,7 +81,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # (profiles/dram_k_phase_slab128_6MV_1e8hist.md).  They hold while the
 # kernel sources hash to TRAFFIC_SOURCES_SHA1; otherwise traffic is null.
 TRAFFIC_SOURCES = ("transport.cu", "common.cuh", "internal.h")
-TRAFFIC_SOURCES_SHA1 = "ec2bc4c6a88156324dd8cf61a72a1f16ac70c16d"
+TRAFFIC_SOURCES_SHA1 = "7702613e28c2adf5a4e970db42b2cf20a05f1c09"
 TRAFFIC = {"workload": "slab128_6MV", "histories": 100_000_000, "batches": 100,
            "photon phase": (7, 1.74e10), "electron phase": (7, 1.01e10)}   # (launches, bytes)
 

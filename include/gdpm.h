@@ -408,7 +408,10 @@ int gdpm_microbench(gdpm_ctx *ctx, int kind, void *buf, uint64_t n_slots, uint64
  *   0 mu_compton [m][i], 1 mu_compton + mu_photo, 2 total mu (cm2/g; the
  *   cumulative forms the transport stores and samples from), 3 CSDA range
  *   (g/cm2), 4 hard Moller, 5 hard bremsstrahlung (cm2/g), 6 energy grid (i),
- *   7 per-material X0 (g/cm2), 8 per-material hard-event majorant (cm2/g).
+ *   7 per-material X0 (g/cm2), 8 per-material hard-event majorant (cm2/g),
+ *   9 ln A of the screened-Rutherford distribution at 1024 points
+ *   ln G1 = ln 1e-10 + k (ln 0.999 - ln 1e-10) / 1023 (the same for every
+ *   material set; a context computes it once).
  * *count receives the number of values written (out may be NULL to query). */
 int gdpm_tables_export(gdpm_tables *t, int which, double *out, int64_t *count);
 

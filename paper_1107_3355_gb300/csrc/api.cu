@@ -1031,6 +1031,7 @@ int gdpm_context_destroy(gdpm_ctx* ctx) {
     cudaSetDevice(ctx->device);
     for (auto& kv : ctx->requests) release(kv.second->result);
     for (Buffer& b : ctx->result_pool) release(b);
+    release(ctx->atab_cache);
     runner_free(ctx->run);
     delete ctx;
     return GDPM_OK;
@@ -1705,6 +1706,11 @@ int gdpm_tables_export(gdpm_tables* t, int which, double* out, int64_t* count) {
         for (int m = 0; m < M; ++m) v.push_back(t->dev.x0[m]);
     } else if (which == 8) {
         for (int m = 0; m < M; ++m) v.push_back(t->dev.sigmax[m]);
+    } else if (which == 9) {
+        std::vector<float> a(size_t(t->n_a));
+        GDPM_CUDA_TRY(cudaMemcpyAsync(a.data(), t->atab.p, a.size() * 4, cudaMemcpyDeviceToHost, s));
+        GDPM_CUDA_TRY(cudaStreamSynchronize(s));
+        for (float x : a) v.push_back(x);
     } else {
         return GDPM_E_ARG;
     }

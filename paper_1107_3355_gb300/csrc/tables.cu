@@ -339,7 +339,16 @@ int build_tables_device(gdpm_ctx* ctx, gdpm_tables* t, const gdpm_material_desc*
     k_scan<<<M, 32, 0, st>>>(B);
     k_derived<<<int((mn + th - 1) / th), th, 0, st>>>(B);
     k_rinv<<<int((size_t(M) * t->n_r + th - 1) / th), th, 0, st>>>(B);
-    k_atab<<<(t->n_a + 31) / 32, 32, 0, st>>>(B);
+    // the screened-Rutherford table depends on no material or grid: the
+    // context computes it once and copies it into later table sets
+    const size_t atab_bytes = sizeof(float) * size_t(t->n_a);
+    if (ctx->atab_cache.p && ctx->atab_cache.bytes >= atab_bytes) {
+        GDPM_CUDA_TRY(cudaMemcpyAsync(t->atab.p, ctx->atab_cache.p, atab_bytes, cudaMemcpyDeviceToDevice, st));
+    } else {
+        k_atab<<<(t->n_a + 31) / 32, 32, 0, st>>>(B);
+        if (ensure(ctx->atab_cache, atab_bytes) == GDPM_OK)
+            GDPM_CUDA_TRY(cudaMemcpyAsync(ctx->atab_cache.p, t->atab.p, atab_bytes, cudaMemcpyDeviceToDevice, st));
+    }
     GDPM_CUDA_TRY(cudaGetLastError());
     std::vector<double> hs(8 * M);
     GDPM_CUDA_TRY(cudaMemcpyAsync(hs.data(), scal.p, sizeof(double) * 8 * M, cudaMemcpyDeviceToHost, st));

@@ -129,6 +129,38 @@ def test_tables_match_oracle():
         eng.close()
 
 
+def test_screening_table_solves_its_equation_and_is_reused():
+    """ln A(ln G1) of the screened-Rutherford hinge: every entry solves
+    2A[(1+A) ln(1+1/A) - 1] = G1 (FP32 storage), and a second table set in
+    the same context (copied from the context's cache) equals the first and
+    a fresh context's."""
+    prob = W.tiny_problem(n_histories=1000, n_batches=10)
+
+    def atab(ctx):
+        tb = G.gdpm_tables_build(ctx, prob.phantom.materials, prob.e_min, prob.e_max, prob.n_energy,
+                                 prob.eabs_photon, prob.eabs_electron, prob.ms_loss_fraction, 0)
+        n = G.gdpm_tables_export(tb, 9)
+        out = cuda_f64(n)
+        G.gdpm_tables_export(tb, 9, out)
+        G.gdpm_tables_destroy(tb)
+        return out.cpu().numpy()
+
+    c1, c2 = G.gdpm_context_create(0), G.gdpm_context_create(0)
+    try:
+        a1, a2, a3 = atab(c1), atab(c1), atab(c2)
+    finally:
+        G.gdpm_context_destroy(c1)
+        G.gdpm_context_destroy(c2)
+    assert a1.size == 1024
+    assert np.array_equal(a1, a2) and np.array_equal(a1, a3)
+    g1 = np.exp(np.log(1e-10) + np.arange(1024) * (np.log(0.999) - np.log(1e-10)) / 1023)
+    A = np.exp(a1)
+    h = 2 * A * ((1 + A) * np.log1p(1 / A) - 1)
+    # ln A is stored in FP32 (|ln A| <= 27 here): exact roots rounded to FP32
+    # reproduce G1 to 1e-6 relative
+    np.testing.assert_allclose(h, g1, rtol=1e-5)
+
+
 # --------------------------------------------------------------------- samplers
 
 @pytest.mark.parametrize("kind,a,b", [(0, 0.1, 0), (0, 1.0, 0), (0, 6.0, 0), (1, 1.0, 0.2),
