@@ -1,5 +1,5 @@
 """CPU oracle for the gDPM dose engine -- TEST INFRASTRUCTURE ONLY.
 
-Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
-import this package.  The product path never does.
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs may import this package.  The product path never does.
 """

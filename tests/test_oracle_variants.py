@@ -1,4 +1,4 @@
-"""Pins for the oracle's physics variants (SURVEY NEXT-4; paper Sec. 4).
+"""Pins for the oracle's physics variants (paper Sec. 4).
 
 * Sauter photoelectron angles: the sampler against the density it reads,
   p(mu) ~ (1-mu^2)/(1-beta mu)^4 [1 + gamma(gamma-1)(gamma-2)(1-beta mu)/2],
