@@ -1,0 +1,60 @@
+"""bench.py's host logic (no GPU): workload defaults, the published rates
+vs_baseline divides by, the gate on measured DRAM traffic, and the clock
+sampler's timestamp parsing."""
+import argparse
+import os
+import sys
+
+import pytest
+
+import bench
+from tests.paper_values import GOLDEN
+
+
+def parse(*argv):
+    old = sys.argv
+    sys.argv = ["bench.py", *argv]
+    try:
+        return bench.parse()
+    finally:
+        sys.argv = old
+
+
+def test_workload_defaults():
+    a = parse()
+    assert (a.workload, a.histories, a.batches, a.steps, a.warmup) == ("slab128_6MV", 1e8, 100, 10, 3)
+    a = parse("--workload", "paper_slab_6MV_lung")
+    assert (a.histories, a.batches) == (2.5e8, 10)
+    a = parse("--workload", "water64_e15", "--histories", "2e5")
+    assert (a.histories, a.batches) == (2e5, 10)
+    assert set(bench.DEFAULT_SIZE) <= set(bench.WORKLOADS) and set(bench.PAPER_RATE) <= set(bench.WORKLOADS)
+
+
+def test_published_rates_come_from_the_paper():
+    """vs_baseline divides by histories / T_GPU as the paper prints them
+    (fixture tests/golden/paper_gpu_times.txt: Table 2 and Sec. 4)."""
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "paper_gpu_times.txt")):
+        if line.strip() and not line.startswith("#"):
+            name, n, t = line.split()
+            rows[name] = (float(n), float(t))
+    assert set(rows) == set(bench.PAPER_RATE)
+    for name, (n, t) in rows.items():
+        assert bench.PAPER_RATE[name] == pytest.approx(n / t, rel=1e-12)
+        assert bench.DEFAULT_SIZE[name][0] == n            # the paper's history count
+
+
+def test_traffic_is_reported_only_for_the_captured_configuration():
+    ns = argparse.Namespace(workload="slab128_6MV", histories=1e8, batches=100, tally="fp64")
+    got = bench.measured_traffic(ns, "electron phase")
+    assert got == pytest.approx(bench.TRAFFIC["electron phase"][1] / bench.TRAFFIC["electron phase"][0])
+    for change in (dict(histories=1e7), dict(batches=10), dict(tally="fp32pair"), dict(workload="ct256_imrt7")):
+        assert bench.measured_traffic(argparse.Namespace(**{**vars(ns), **change}), "electron phase") is None
+    assert bench.measured_traffic(ns, "batch fold") is None
+
+
+def test_clock_sampler_reads_nvidia_smi_timestamps():
+    import datetime
+    t = bench.Clocks._stamp("2026/12/03 12:34:56.789")
+    assert t == pytest.approx(datetime.datetime(2026, 12, 3, 12, 34, 56, 789000).timestamp())
+    assert bench.Clocks._stamp("not a time") is None
