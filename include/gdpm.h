@@ -142,13 +142,20 @@ typedef struct {
 
 /* Create a context on CUDA device `device` issuing work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  `seed` keys the
- * Philox4x32-10 generator: key = (seed lo 32 bits, seed hi 32 bits ^
- * request id).  Errors: GDPM_E_ARG (bad device), GDPM_E_CUDA. */
+ * Philox4x32-10 generator that stands in for the per-thread generator
+ * states of Sec. 2.2.2: key = (seed lo 32 bits, seed hi 32 bits ^ request
+ * id).  The context owns the device memory it allocates.
+ * Errors: GDPM_E_ARG (bad device, NULL out), GDPM_E_CUDA. */
 int gdpm_context_create(gdpm_ctx **out, int device, void *cuda_stream, uint64_t seed);
+/* Destroy a context: stops its serving workers and frees its device memory.
+ * Phantoms and tables made on it must be destroyed first.
+ * Errors: GDPM_E_ARG (NULL). */
 int gdpm_context_destroy(gdpm_ctx *ctx);
 
-/* Tuning and run parameters (see GDPM_PARAM_*).  GDPM_E_ARG if unknown or
- * out of range. */
+/* Tuning and run parameters of the transport loop of Sec. 2.2.1 (see
+ * GDPM_PARAM_*; each states its range).  They change how the work is
+ * launched, not what is computed.
+ * Errors: GDPM_E_ARG (unknown parameter or value out of range). */
 int gdpm_set_param(gdpm_ctx *ctx, int param, double value);
 enum {
     GDPM_PARAM_QUEUE_CAPACITY = 1,   /* particles per queue buffer (0 = automatic), <= 2^31 */
@@ -194,6 +201,8 @@ enum {
  * Errors: GDPM_E_ARG (non-positive sizes, nx|ny|nz > 1024), GDPM_E_NOMEM. */
 int gdpm_phantom_create(gdpm_ctx *ctx, int nx, int ny, int nz, float dx, float dy, float dz,
                         const uint8_t *material, const float *density, gdpm_phantom **out);
+/* Release a phantom (Sec. 2.2.1) and its device memory; waits for work on
+ * its context's stream.  Errors: GDPM_E_ARG (NULL). */
 int gdpm_phantom_destroy(gdpm_phantom *ph);
 
 /* Build the interpolation tables (Sec. 2.2.2) for n_mats materials on a
@@ -210,6 +219,8 @@ int gdpm_phantom_destroy(gdpm_phantom *ph);
 int gdpm_tables_build(gdpm_ctx *ctx, const gdpm_material_desc *mats, int n_mats,
                       double e_min, double e_max, int n_energy, double eabs_photon,
                       double eabs_electron, double ms_loss, int flags, gdpm_tables **out);
+/* Release a table set (Sec. 2.2.2) and its device memory; waits for work on
+ * its context's stream.  Errors: GDPM_E_ARG (NULL). */
 int gdpm_tables_destroy(gdpm_tables *t);
 
 /* Set the primary source (Sec. 2.3.1-2.3.3).  Copies everything it needs.
@@ -270,6 +281,9 @@ int gdpm_simulate_to_precision(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb,
 int gdpm_simulate_part(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
                        int n_batches, int first_batch, int n_part, double *sum1, double *sum2,
                        gdpm_stats *stats_out);
+/* gdpm_finalize: the batch statistics of Sec. 2.2.1 Step 4 and the Sec. 3.1
+ * metric from the sums above.  Errors: GDPM_E_ARG (NULL context, phantom or
+ * sums, n_batches < 2), GDPM_E_NOMEM, GDPM_E_CUDA. */
 int gdpm_finalize(gdpm_ctx *ctx, gdpm_phantom *ph, int n_batches, const double *sum1,
                   const double *sum2, double *dose_out, double *sigma_out, gdpm_stats *stats_out);
 
@@ -302,7 +316,8 @@ typedef struct {
     double histories_per_s;    /* of the best candidate (wall clock, whole call) */
 } gdpm_tune_result;
 
-/* Autotuner: run the calculation gdpm_simulate(ph, tb, n_histories,
+/* Autotuner for the launch configuration of the Sec. 2.2.1 transport loop:
+ * run the calculation gdpm_simulate(ph, tb, n_histories,
  * n_batches) with the current source under each candidate launch
  * configuration -- batches side by side (when their grids fit) or one after
  * another, 1M / 4M primaries per phase or the side-by-side default (8M or
@@ -314,7 +329,8 @@ typedef struct {
 int gdpm_autotune(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
                   int n_batches, double budget_ms, gdpm_tune_result *out);
 
-/* Optional per-history records for the next gdpm_simulate on this context:
+/* Optional per-history records of the Sec. 2.2.1 transport, for the next
+ * gdpm_simulate on this context:
  * rec (device, n*4 int32: real photon interactions, electron steps, hard
  * electron events, banked secondaries) and recd (device, n*2 doubles:
  * escaped energy, electron mass path in g/cm2), indexed by history id.
@@ -323,9 +339,10 @@ int gdpm_set_history_records(gdpm_ctx *ctx, int32_t *rec, double *recd, uint64_t
 
 /* ------------------------------------------------------------------ serving */
 
-/* A dose request: the source to use, history count and batch count, run on
- * a phantom/table pair that stays resident.  Results are kept on the device
- * until polled. */
+/* A dose request: one Sec. 2.2.1 calculation (source, history count and
+ * batch count) on a phantom/table pair that stays resident.  Serving is not
+ * in the paper: requests share the GPU and keep their own random streams.
+ * Results are kept on the device until polled. */
 typedef struct {
     gdpm_phantom *phantom;
     gdpm_tables *tables;
@@ -336,7 +353,8 @@ typedef struct {
                                       0 = use the request id */
 } gdpm_request_desc;
 
-/* Queue a request; returns at once with its id.  Requests arriving while
+/* Queue a request (one Sec. 2.2.1 calculation); returns at once with its
+ * id.  Requests arriving while
  * others run are admitted as slots and device memory free up and share the
  * device with them (continuous batching); each request keeps its own Philox
  * key (request id), so its result does not depend on what else runs.
@@ -344,6 +362,7 @@ typedef struct {
 int gdpm_request_submit(gdpm_ctx *ctx, const gdpm_request_desc *req, uint64_t *req_id);
 
 /* Poll a request: *done = 1 when finished, then copies its dose/sigma
+ * (the batch statistics of Sec. 2.2.1 Step 4)
  * (host or device arrays, nx*ny*nz doubles, may be NULL) and stats, and
  * releases it.  *done = 0 while queued or running.  Thread-safe.
  * Errors: GDPM_E_ARG (unknown id), or the request's own failure code. */
@@ -355,9 +374,10 @@ int gdpm_request_poll(gdpm_ctx *ctx, uint64_t req_id, int *done, double *dose_ou
 /* Human-readable text for a status code (static storage). */
 const char *gdpm_strerror(int code);
 
-/* Philox4x32-10 on the device for n counters (device arrays of 4*n uint32
- * each, in and out), key (k0, k1).  For bitwise comparison with other
- * implementations.  Errors: GDPM_E_ARG, GDPM_E_CUDA. */
+/* Philox4x32-10 (the generator that replaces Sec. 2.2.2's) on the device for
+ * n counters (device arrays of 4*n uint32 each, in and out), key (k0, k1).
+ * For bitwise comparison with other implementations.
+ * Errors: GDPM_E_ARG (NULL or host arrays), GDPM_E_CUDA. */
 int gdpm_debug_philox(gdpm_ctx *ctx, const uint32_t *ctr, uint32_t k0, uint32_t k1,
                       uint32_t *out, uint64_t n);
 
@@ -370,7 +390,13 @@ int gdpm_debug_philox(gdpm_ctx *ctx, const uint32_t *ctr, uint32_t k0, uint32_t 
  *   kind 3 screened Rutherford with screening a: out1 = mu
  *   kind 4 isotropic: out1 = cos(theta), out2 = phi
  *   kind 5 Sauter photoelectron of kinetic energy a: out1 = cos(theta), out2 = phi
- * out1/out2: device arrays of n doubles (out2 may be NULL). */
+ * These are the interactions of Sec. 2.1 (photons: Compton; electrons: hard
+ * Moller and bremsstrahlung events, multiple-scattering deflection; the
+ * Sec. 4 photoelectron variant).
+ * out1/out2: device arrays of n doubles (out2 may be NULL).
+ * Errors: GDPM_E_ARG (unknown kind, host or NULL out1, parameters outside the
+ * sampler's domain: a > 0; Moller a > 2b > 0; bremsstrahlung a > b > 0),
+ * GDPM_E_CUDA. */
 int gdpm_debug_sample(gdpm_ctx *ctx, int kind, double a, double b, uint64_t n,
                       uint64_t seed, double *out1, double *out2);
 
@@ -412,14 +438,18 @@ int gdpm_microbench(gdpm_ctx *ctx, int kind, void *buf, uint64_t n_slots, uint64
  *   9 ln A of the screened-Rutherford distribution at 1024 points
  *   ln G1 = ln 1e-10 + k (ln 0.999 - ln 1e-10) / 1023 (the same for every
  *   material set; a context computes it once).
- * *count receives the number of values written (out may be NULL to query). */
+ * These are the tables of Sec. 2.2.2 as the transport reads them.
+ * *count receives the number of values written (out may be NULL to query).
+ * Errors: GDPM_E_ARG (NULL table set or count, unknown kind), GDPM_E_CUDA. */
 int gdpm_tables_export(gdpm_tables *t, int which, double *out, int64_t *count);
 
 /* Generate the primaries of histories [first, first+n) of batch 0 of an
  * n_histories/n_batches run with the current source, as the transport does
  * (Sec. 2.3), without transporting them.  out (device, n*8 doubles per
  * primary: x y z u v w E entered) -- position is on the phantom surface
- * after entry; entered = 0 if the primary misses the phantom. */
+ * after entry; entered = 0 if the primary misses the phantom.
+ * Errors: those of gdpm_simulate's argument checks; GDPM_E_ARG (host or NULL
+ * out, first + n beyond the histories of batch 0). */
 int gdpm_debug_sources(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
                        int n_batches, uint64_t first, uint64_t n, double *out);
 
@@ -433,8 +463,9 @@ int gdpm_debug_beamlets(gdpm_ctx *ctx, uint64_t first, uint64_t n, int32_t *out)
 
 /* ------------------------------------------------------------------ no allocation */
 
-/* gdpm_simulate_noalloc -- the same dose calculation as gdpm_simulate, for
- * small problems, without allocating any memory.  The paper has no
+/* gdpm_simulate_noalloc -- the same dose calculation as gdpm_simulate
+ * (Sec. 2.2.1), for small problems, without allocating any memory.  The
+ * paper has no
  * counterpart; this exists for callers that cannot call cudaMalloc: code that
  * runs while a CUDA graph is being captured (allocation is not allowed during
  * stream capture), and host applications that hand all device memory to
@@ -463,7 +494,8 @@ int gdpm_debug_beamlets(gdpm_ctx *ctx, uint64_t first, uint64_t n, int32_t *out)
  * contents (the call clears what must start at zero).  Calls whose work
  * overlaps on the same GPU -- from two streams, two contexts or two threads
  * -- race on that array and corrupt each other's results: run them one after
- * another. */
+ * another.
+ * Errors: those of gdpm_simulate, and GDPM_E_ARG beyond the limits above. */
 #define GDPM_NOALLOC_MAX_VOXELS 32768
 #define GDPM_NOALLOC_QUEUE_CAPACITY 16384
 #define GDPM_NOALLOC_MAX_PREFIX 65536
