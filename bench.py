@@ -81,9 +81,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # (profiles/dram_k_phase_slab128_6MV_1e8hist.md).  They hold while the
 # kernel sources hash to TRAFFIC_SOURCES_SHA1; otherwise traffic is null.
 TRAFFIC_SOURCES = ("transport.cu", "common.cuh", "internal.h")
-TRAFFIC_SOURCES_SHA1 = "7702613e28c2adf5a4e970db42b2cf20a05f1c09"
+TRAFFIC_SOURCES_SHA1 = "f95a93d52e589eb14878327c497c6c2e9adeefe7"
 TRAFFIC = {"workload": "slab128_6MV", "histories": 100_000_000, "batches": 100,
-           "photon phase": (7, 1.74e10), "electron phase": (7, 1.01e10)}   # (launches, bytes)
+           "photon phase": (7, 1.798e10), "electron phase": (7, 1.015e10)}   # (launches, bytes)
 
 
 def measured_traffic(args, kernel):
