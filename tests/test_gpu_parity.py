@@ -274,6 +274,30 @@ def test_slab_electron_same_seed():
     assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97
 
 
+def test_random_hinge_depth_moment_closed_form():
+    """The CUDA electron transport (CSDA steps, random hinge, deflection,
+    voxel walk and tally) against the closed form of the energy-weighted
+    depth of a 2 MeV pencil's dose, hard events off (derivation in
+    tests/_hinge.py): eight independent runs of 1e5 histories."""
+    from tests import _hinge as H
+    expect = H.closed_form(H.problem(1))
+    cents = []
+    for rid in range(8):
+        prob = H.problem(100_000, request_id=rid)
+        d, _, st = run_gpu(prob)
+        check_ledger(st, prob.n_histories, 1e-5)
+        assert st["escaped"] == 0.0
+        z, e = H.depth_moment(d)
+        assert e == pytest.approx(H.T0, rel=1e-4)
+        cents.append(z)
+    se = np.std(cents, ddof=1) / np.sqrt(len(cents))
+    print("GPU depth moment %.5f cm, closed form %.5f, se %.5f" % (np.mean(cents), expect, se))
+    assert se < 5e-4
+    # beyond the statistical band: voxel centres for positions (far below dz)
+    # and FP32 tables and steps; a per-step mean cosine 2 % low moves it 6e-3
+    assert abs(np.mean(cents) - expect) < 4.0 * se + 5e-4
+
+
 def test_tally_modes_agree():
     prob = W.tiny_problem(n_histories=50_000)
     d64, _, st64 = run_gpu(prob)

@@ -372,63 +372,20 @@ def test_csda_track_length(T0):
 
 
 def test_random_hinge_depth_moment():
-    """Mean depth of the deposited energy of a 2 MeV electron pencil deep in
-    water, hard events off (Sec. 2.1 condensed history: CSDA steps, random
-    hinge, screened-Rutherford deflection).
-
-    With no hard events every step is fixed by its start energy: mass length
-    x_j, energy loss dT_j, and a deflection whose mean cosine is
-    m_j = 1 - G1_j, G1_j = x_j (E_s / p beta c)^2 / (2 X0) at the mid-step
-    energy.  Deflections with a uniform azimuth scale the expected direction
-    by m_j (Lewis' moment argument), so before step j the expected direction
-    along the beam is c_j = prod_{i<j} m_i.  For a hinge at zeta ~ U(0,1) and
-    the loss spread evenly along the step, the expected depth averaged over
-    the step is Z_j + x_j c_j (1/3 + m_j/6), and the step moves the expected
-    depth by x_j c_j (1 + m_j)/2.  The energy-weighted depth of the dose
-    must equal sum_j dT_j (...) plus E_abs at the track end, over T0.  A hinge
-    at either end of the step, or G1 off by a factor of two, moves it by 50
-    to 100 standard errors; a per-step mean cosine 2 % low, by 10."""
-    from scipy import optimize
-    T0, nz, dz, z0 = 2.0, 200, 0.02, 1.5
-    ph = W.homogeneous_phantom((1, 1, nz), (100.0, 100.0, dz), W.WATER, 1.0)
-    src = W.Source(W.ELECTRON, W.mono_spectrum(T0), "pencil", (50.0, 50.0, z0), (0.0, 0.0, 1.0))
-    p = W.Problem(ph, src, 5000, 2, eabs_photon=0.05, eabs_electron=0.2, e_min=0.005,
-                  e_max=T0 * 1.05, flags=W.FLAG_NO_HARD)
-    k, eabs, es = p.ms_loss_fraction, p.eabs_electron, 21.2
-    rng_of = lambda t: float(O.evaluate(p, 0, O.OF_RANGE, t)[0])      # CSDA range, g/cm^2
-    x0 = 1.0 / float(O.evaluate(p, 0, O.OF_BCONST, 1.0)[0])           # radiation length
-    # the step sequence: down by the loss fraction k, the last step to E_abs
-    steps, E = [], T0
-    while True:
-        r0 = rng_of(E)
-        x_cut, x_ms = r0 - rng_of(eabs), r0 - rng_of((1.0 - k) * E)
-        if x_cut <= x_ms:
-            x, te = x_cut, eabs
-        else:
-            x = x_ms
-            te = optimize.brentq(lambda t: rng_of(t) - (r0 - x), eabs, E, xtol=1e-13)
-        tm = 0.5 * (E + te)
-        pbc = tm * (tm + 2 * MC2) / (tm + MC2)
-        g1 = x * (es / pbc) ** 2 / (2.0 * x0)
-        steps.append((x, E - te, 0.0 if g1 >= 1.0 else 1.0 - g1))
-        if te <= eabs:
-            break
-        E = te
-    Z, c, num = z0, 1.0, 0.0
-    for x, dT, m in steps:                      # density 1: mass length = cm
-        num += dT * (Z + x * c * (1.0 / 3.0 + m / 6.0))
-        Z += x * c * (1.0 + m) / 2.0
-        c *= m
-    expect = (num + eabs * Z) / T0
-    # sixteen independent runs of the oracle: mean and standard error
-    zc = (np.arange(nz) + 0.5) * dz
+    """Energy-weighted depth of the dose of a 2 MeV electron pencil deep in
+    water, hard events off, against its closed form from Lewis-type first
+    moments over the deterministic step sequence (derivation in
+    tests/_hinge.py).  Sixteen independent oracle runs give the mean and its
+    standard error."""
+    from tests import _hinge as H
+    expect = H.closed_form(H.problem(1))
     cents = []
     for rid in range(16):
-        dose, _, led = O.run(p.with_(request_id=rid))
+        dose, _, led = O.run(H.problem(5000, request_id=rid))
         assert led["escaped"] == 0.0
-        e = dose * (100.0 * 100.0 * dz)                # MeV per history in each voxel
-        assert e.sum() == pytest.approx(T0, rel=1e-9)
-        cents.append(float((e * zc).sum() / e.sum()))
+        z, e = H.depth_moment(dose)
+        assert e == pytest.approx(H.T0, rel=1e-9)
+        cents.append(z)
     se = np.std(cents, ddof=1) / math.sqrt(len(cents))
     print("depth moment %.5f cm, closed form %.5f, se %.5f" % (np.mean(cents), expect, se))
     assert se < 1e-3
