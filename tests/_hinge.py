@@ -70,3 +70,34 @@ def depth_moment(dose):
     e = np.asarray(dose, np.float64) * (AREA * DZ)
     zc = (np.arange(NZ) + 0.5) * DZ
     return float((e * zc).sum() / e.sum()), float(e.sum())
+
+
+# The same electron in z-layers of water at different densities.  Every step
+# quantity is per unit mass (mass length, G1 with X0 in g/cm^2) and the voxel
+# walk spends the step's mass length voxel by voxel, so along z the mass depth
+# moves by w dm whatever the densities: with the same random draws the
+# mass-depth history equals the homogeneous one, up to the rounding of
+# positions and the binning of the grid.
+LAYER_RHO = (1.0, 0.5, 1.5, 0.3)
+LAYER_NZ, LAYER_M0 = 300, 2.0         # start at mass depth 2 g/cm^2
+
+
+def layered_problem(n_histories, request_id=0):
+    rho = np.resize(np.array(LAYER_RHO), LAYER_NZ).astype(np.float32)
+    faces = np.concatenate([[0.0], np.cumsum(rho.astype(np.float64) * DZ)])
+    iz = int(np.searchsorted(faces, LAYER_M0) - 1)
+    z0 = iz * DZ + (LAYER_M0 - faces[iz]) / float(rho[iz])
+    ph = W.Phantom((1, 1, LAYER_NZ), (100.0, 100.0, DZ), np.zeros(LAYER_NZ, np.uint8), rho,
+                   [W.WATER])
+    src = W.Source(W.ELECTRON, W.mono_spectrum(T0), "pencil", (50.0, 50.0, z0), (0.0, 0.0, 1.0))
+    return W.Problem(ph, src, n_histories, 2, eabs_photon=0.05, eabs_electron=0.2, e_min=0.005,
+                     e_max=T0 * 1.05, flags=W.FLAG_NO_HARD, request_id=request_id)
+
+
+def mass_depth_moment(dose, rho):
+    """(energy-weighted mass depth in g/cm^2, energy per history in MeV)."""
+    rho = np.asarray(rho, np.float64)
+    faces = np.concatenate([[0.0], np.cumsum(rho * DZ)])
+    e = np.asarray(dose, np.float64) * rho * (AREA * DZ)
+    mc = 0.5 * (faces[:-1] + faces[1:])
+    return float((e * mc).sum() / e.sum()), float(e.sum())
