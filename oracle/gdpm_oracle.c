@@ -650,15 +650,21 @@ static void bank(orc_sim *S, orc_particle *parent, int type, double E, const dou
     push(S, &c);
 }
 
-/* ---------------------------------------------------------------- photons */
-static void compton(orc_sim *S, orc_particle *p, int *alive)
+/* ---------------------------------------------------------------- samplers
+ * One function per interaction sampler, called by the transport and by
+ * orc_sample (which the sampler pins test), so that the pins reach the code
+ * that makes the dose. */
+
+/* Klein-Nishina in eps = E'/E by the two-branch mixture method (1/eps and
+ * eps branches, rejection on 1 - eps sin^2/(1+eps^2)).  Returns eps, the
+ * photon's polar cosine 1 - t, and the fourth uniform of the accepted draw
+ * (the caller's azimuth). */
+static double kn_sample(orc_sim *S, orc_particle *p, double E, double *cost, double *c3)
 {
-    double E = p->E, k = E / MC2;
+    double k = E / MC2;
     double e0 = 1.0 / (1.0 + 2.0 * k);
     double a1 = log(1.0 + 2.0 * k), a2 = 0.5 * (1.0 - e0 * e0);
     double eps, t, c[4];
-    /* Klein-Nishina in eps = E'/E by the two-branch mixture method
-     * (1/eps and eps branches, rejection on 1 - eps sin^2/(1+eps^2)). */
     for (;;) {
         draw4(S, p, c);
         if (c[0] * (a1 + a2) < a1) eps = exp(-a1 * c[1]);
@@ -668,7 +674,59 @@ static void compton(orc_sim *S, orc_particle *p, int *alive)
         double g = 1.0 - eps * sin2 / (1.0 + eps * eps);
         if (c[2] <= g) break;
     }
-    double cost = 1.0 - t, phi = 2.0 * PI * c[3];
+    *cost = 1.0 - t;
+    *c3 = c[3];
+    return eps;
+}
+
+/* Moller energy fraction eps = W/T on [W_cc/T, 1/2]: proposal 1/eps^2,
+ * rejection on the rest of the Moller density.  Also returns the third
+ * uniform of the accepted draw (the caller's azimuth). */
+static double moller_sample(orc_sim *S, orc_particle *p, double Tn, double wcc, double *w2)
+{
+    double tau = Tn / MC2;
+    double c1 = (tau / (tau + 1.0)) * (tau / (tau + 1.0));
+    double c2 = (2.0 * tau + 1.0) / ((tau + 1.0) * (tau + 1.0));
+    double ec = wcc / Tn, eps, w[4];
+    for (;;) {
+        draw4(S, p, w);
+        eps = ec / (1.0 - w[0] * (1.0 - 2.0 * ec));
+        double x = eps / (1.0 - eps);
+        double g = 1.0 + x * x + c1 * eps * eps - c2 * x;
+        if (w[1] * (2.0 + 0.25 * c1) <= g) break;
+    }
+    *w2 = w[2];
+    return eps;
+}
+
+/* Polar cosine of an electron of kinetic energy W leaving a binary
+ * collision of an electron of kinetic energy T (energy and momentum
+ * conservation, target at rest). */
+static double binary_cos(double T, double W)
+{
+    return sqrt(W * (T + 2.0 * MC2) / (T * (W + 2.0 * MC2)));
+}
+
+/* Hard bremsstrahlung photon energy on [W_cb, T] for dSigma/dk = B/k:
+ * k = W_cb (T/W_cb)^xi. */
+static double brems_k(double Tn, double wcb, double xi)
+{
+    return wcb * pow(Tn / wcb, xi);
+}
+
+/* Screened Rutherford p(mu) ~ (1 - mu + 2A)^-2 by inversion of its
+ * cumulative distribution at the uniform u. */
+static double sr_mu(double A, double u)
+{
+    return 1.0 - 2.0 * A * u / (1.0 - u + A);
+}
+
+/* ---------------------------------------------------------------- photons */
+static void compton(orc_sim *S, orc_particle *p, int *alive)
+{
+    double E = p->E, cost, c3;
+    double eps = kn_sample(S, p, E, &cost, &c3);
+    double phi = 2.0 * PI * c3;
     double Ep = eps * E, Te = E - Ep;
     double uold[3] = {p->u[0], p->u[1], p->u[2]};
     rotate(p->u, cost, phi);
@@ -870,7 +928,7 @@ static void electron_track(orc_sim *S, orc_particle *p)
         if (G1 >= 1.0) mu = 2.0 * u[2] - 1.0;
         else {
             double A = solve_A(G1);
-            mu = 1.0 - 2.0 * A * u[2] / (1.0 - u[2] + A);
+            mu = sr_mu(A, u[2]);
         }
         double phi = 2.0 * PI * u[3];
         double zeta = u[1];
@@ -896,21 +954,12 @@ static void electron_track(orc_sim *S, orc_particle *p)
         if (v[1] * sh < sm) {
             /* Moller: eps = W/T on [W_cc/T, 1/2], proposal 1/eps^2 + rejection */
             S->res->moller++;
-            double tau = Tn / MC2;
-            double c1 = (tau / (tau + 1.0)) * (tau / (tau + 1.0));
-            double c2 = (2.0 * tau + 1.0) / ((tau + 1.0) * (tau + 1.0));
-            double ec = wcc / Tn, eps, w[4];
-            for (;;) {
-                draw4(S, p, w);
-                eps = ec / (1.0 - w[0] * (1.0 - 2.0 * ec));
-                double x = eps / (1.0 - eps);
-                double g = 1.0 + x * x + c1 * eps * eps - c2 * x;
-                if (w[1] * (2.0 + 0.25 * c1) <= g) break;
-            }
-            double ph = 2.0 * PI * w[2];
+            double w2;
+            double eps = moller_sample(S, p, Tn, wcc, &w2);
+            double ph = 2.0 * PI * w2;
             double W = eps * Tn, Tp = Tn - W;
-            double cd = sqrt(W * (Tn + 2.0 * MC2) / (Tn * (W + 2.0 * MC2)));
-            double cp = sqrt(Tp * (Tn + 2.0 * MC2) / (Tn * (Tp + 2.0 * MC2)));
+            double cd = binary_cos(Tn, W);
+            double cp = binary_cos(Tn, Tp);
             double ud[3] = {p->u[0], p->u[1], p->u[2]};
             rotate(ud, cd, ph);
             bank(S, p, PT_ELECTRON, W, p->x, ud, p->iv);
@@ -919,7 +968,7 @@ static void electron_track(orc_sim *S, orc_particle *p)
         } else {
             /* bremsstrahlung: k = W_cb (T/W_cb)^xi, photon along the electron */
             S->res->brems++;
-            double kph = wcb * pow(Tn / wcb, v[2]);
+            double kph = brems_k(Tn, wcb, v[2]);
             bank(S, p, PT_PHOTON, kph, p->x, p->u, p->iv);
             p->E = Tn - kph;
         }
@@ -1342,38 +1391,18 @@ int orc_sample(int which, double a, double b, long long n, unsigned long long se
         memset(&p, 0, sizeof p);
         p.hist = (uint32_t)s; p.pid = 1;
         if (which == OS_KN) {
-            double E = a, k = E / MC2;
-            double e0 = 1.0 / (1.0 + 2.0 * k);
-            double a1 = log(1.0 + 2.0 * k), a2 = 0.5 * (1.0 - e0 * e0);
-            double eps, t, c[4];
-            for (;;) {
-                draw4(&S, &p, c);
-                if (c[0] * (a1 + a2) < a1) eps = exp(-a1 * c[1]);
-                else eps = sqrt(e0 * e0 + (1.0 - e0 * e0) * c[1]);
-                t = (1.0 - eps) / (k * eps);
-                double g = 1.0 - eps * t * (2.0 - t) / (1.0 + eps * eps);
-                if (c[2] <= g) break;
-            }
-            out1[s] = eps; out2[s] = 1.0 - t;
+            double cost, c3;
+            out1[s] = kn_sample(&S, &p, a, &cost, &c3);
+            out2[s] = cost;
         } else if (which == OS_MOLLER) {
-            double Tn = a, wcc = b;
-            double tau = Tn / MC2;
-            double c1 = (tau / (tau + 1.0)) * (tau / (tau + 1.0));
-            double c2 = (2.0 * tau + 1.0) / ((tau + 1.0) * (tau + 1.0));
-            double ec = wcc / Tn, eps, w[4];
-            for (;;) {
-                draw4(&S, &p, w);
-                eps = ec / (1.0 - w[0] * (1.0 - 2.0 * ec));
-                double x = eps / (1.0 - eps);
-                double g = 1.0 + x * x + c1 * eps * eps - c2 * x;
-                if (w[1] * (2.0 + 0.25 * c1) <= g) break;
-            }
+            double w2;
+            double eps = moller_sample(&S, &p, a, b, &w2);
             out1[s] = eps;
-            if (out2) out2[s] = sqrt(eps * Tn * (Tn + 2.0 * MC2) / (Tn * (eps * Tn + 2.0 * MC2)));
+            if (out2) out2[s] = binary_cos(a, eps * a);
         } else if (which == OS_BREMS) {
             double v[4];
             draw4(&S, &p, v);
-            out1[s] = b * pow(a / b, v[2]);
+            out1[s] = brems_k(a, b, v[2]);
         } else if (which == OS_SAUTER) {
             double mu, phi;
             sample_sauter(&S, &p, a, &mu, &phi);
@@ -1382,8 +1411,7 @@ int orc_sample(int which, double a, double b, long long n, unsigned long long se
         } else if (which == OS_SR) {
             double u[4];
             draw4(&S, &p, u);
-            double A = a;
-            out1[s] = 1.0 - 2.0 * A * u[2] / (1.0 - u[2] + A);
+            out1[s] = sr_mu(a, u[2]);
         } else {
             double u[4];
             draw4(&S, &p, u);
