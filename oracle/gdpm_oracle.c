@@ -746,11 +746,40 @@ static void compton(orc_sim *S, orc_particle *p, int *alive)
     }
 }
 
-static void photon_track(orc_sim *S, orc_particle *p)
+/* One Woodcock flight against the majorant mu_max(E) (Sec. 2.2.1 photon
+ * transport): fly -ln(u0)/mu_max; if still inside, the collision is real
+ * with probability mu(E, m) rho / mu_max (u1), and then Compton,
+ * photoelectric or pair by the partial coefficients (u2).  Returns 0 when
+ * the photon left the phantom, 1 for a virtual collision, 2 for a real one
+ * with *type 0 Compton, 1 photoelectric, 2 pair. */
+static int woodcock_flight(orc_sim *S, orc_particle *p, const double u[4], int *type)
 {
     const orc_problem *P = S->P;
     const orc_tables *T = &S->T;
     int n = T->n;
+    int i; double f;
+    grid_pos(T, p->E, &i, &f);
+    double mumax = lerp_tab(T->mumax, i, f);
+    double s = -log(u[0]) / mumax;
+    for (int a = 0; a < 3; a++) p->x[a] += s * p->u[a];
+    if (!inside(P, p->x)) return 0;
+    voxel_of(P, p->x, p->iv);
+    size_t v = vidx(P, p->iv);
+    int m = P->mat[v];
+    double rho = P->rho[v];
+    double muc = lerp_tab(T->mu_c + (size_t)m * n, i, f);
+    double mupe = lerp_tab(T->mu_pe + (size_t)m * n, i, f);
+    double mupp = lerp_tab(T->mu_pair + (size_t)m * n, i, f);
+    double mut = muc + mupe + mupp;
+    if (u[1] * mumax >= mut * rho) return 1;     /* virtual (delta) collision */
+    double r = u[2] * mut;
+    *type = r < muc ? 0 : (r < muc + mupe ? 1 : 2);
+    return 2;
+}
+
+static void photon_track(orc_sim *S, orc_particle *p)
+{
+    const orc_problem *P = S->P;
     if (p->E < P->eabs_ph) {           /* never transported */
         if (inside(P, p->x)) { voxel_of(P, p->x, p->iv); deposit(S, p->iv, p->E); }
         else S->res->escaped += p->E;
@@ -761,32 +790,20 @@ static void photon_track(orc_sim *S, orc_particle *p)
     while (alive) {
         double u[4];
         draw4(S, p, u);
-        int i; double f;
-        grid_pos(T, p->E, &i, &f);
-        double mumax = lerp_tab(T->mumax, i, f);
-        double s = -log(u[0]) / mumax;
-        for (int a = 0; a < 3; a++) p->x[a] += s * p->u[a];
-        if (!inside(P, p->x)) {
+        int type = 0;
+        int fl = woodcock_flight(S, p, u, &type);
+        if (fl == 0) {
             S->res->escaped += p->E;
             S->res->ph_terminated++;
             return;
         }
-        voxel_of(P, p->x, p->iv);
-        size_t v = vidx(P, p->iv);
-        int m = P->mat[v];
-        double rho = P->rho[v];
-        double muc = lerp_tab(T->mu_c + (size_t)m * n, i, f);
-        double mupe = lerp_tab(T->mu_pe + (size_t)m * n, i, f);
-        double mupp = lerp_tab(T->mu_pair + (size_t)m * n, i, f);
-        double mut = muc + mupe + mupp;
         S->res->ph_flights++;
-        if (u[1] * mumax >= mut * rho) continue;     /* virtual (delta) collision */
+        if (fl == 1) continue;
         S->res->ph_real++;
         if (S->hrec) S->hrec[(S->cur_hist - S->hrec_base) * HR_NI + HR_PH_REAL]++;
-        double r = u[2] * mut;
-        if (r < muc) {
+        if (type == 0) {
             compton(S, p, &alive);
-        } else if (r < muc + mupe) {
+        } else if (type == 1) {
             S->res->photoelectric++;
             double d[3] = {p->u[0], p->u[1], p->u[2]};
             if (P->flags & ORC_SAUTER) {
@@ -1430,8 +1447,6 @@ int orc_first_interaction(const orc_problem *P, long long n, double *out_z, int 
     orc_sim S;
     orc_result res;
     sim_init(&S, P, &res);
-    const orc_tables *T = &S.T;
-    int nn = T->n;
     for (long long h = 0; h < n; h++) {
         orc_particle p;
         make_primary(&S, (uint32_t)h, P->edges[0], P->edges[1], &p);
@@ -1440,23 +1455,12 @@ int orc_first_interaction(const orc_problem *P, long long n, double *out_z, int 
         for (;;) {
             double u[4];
             draw4(&S, &p, u);
-            int i; double f;
-            grid_pos(T, p.E, &i, &f);
-            double mumax = lerp_tab(T->mumax, i, f);
-            double s = -log(u[0]) / mumax;
-            for (int a = 0; a < 3; a++) p.x[a] += s * p.u[a];
-            if (!inside(P, p.x)) break;
-            voxel_of(P, p.x, p.iv);
-            size_t v = vidx(P, p.iv);
-            int m = P->mat[v];
-            double muc = lerp_tab(T->mu_c + (size_t)m * nn, i, f);
-            double mupe = lerp_tab(T->mu_pe + (size_t)m * nn, i, f);
-            double mupp = lerp_tab(T->mu_pair + (size_t)m * nn, i, f);
-            double mut = muc + mupe + mupp;
-            if (u[1] * mumax >= mut * P->rho[v]) continue;
-            double r = u[2] * mut;
+            int type = 0;
+            int fl = woodcock_flight(&S, &p, u, &type);
+            if (fl == 0) break;
+            if (fl == 1) continue;
             out_z[h] = p.x[2];
-            out_type[h] = r < muc ? 0 : (r < muc + mupe ? 1 : 2);
+            out_type[h] = type;
             break;
         }
     }
