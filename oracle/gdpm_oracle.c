@@ -39,6 +39,9 @@
  * brute-force histograms, and the batch precision against the values the
  * paper prints (Table 1).  Parity unpinned: agreement of the dose itself with
  * DPM's physics data, which is not available; the formulas here are readings.
+ * The test entries at the end of the file (orc_sample, orc_first_interaction,
+ * orc_rotate, ...) call the transport's own functions, so a pin on a sampler
+ * or on the Woodcock flight tests the code that makes the dose.
  *
  * Units: MeV, cm, g/cm3; per-unit-density quantities in cm2/g or MeV cm2/g.
  */
