@@ -1,6 +1,6 @@
 """bench.py's host logic (no GPU): workload defaults, the published rates
-vs_baseline divides by, the gate on measured DRAM traffic, and the clock
-sampler's timestamp parsing."""
+vs_baseline divides by, the gate on measured DRAM traffic, the clock
+sampler's timestamp parsing, and the reference arm (the CPU oracle)."""
 import argparse
 import os
 import sys
@@ -58,3 +58,39 @@ def test_clock_sampler_reads_nvidia_smi_timestamps():
     t = bench.Clocks._stamp("2026/12/03 12:34:56.789")
     assert t == pytest.approx(datetime.datetime(2026, 12, 3, 12, 34, 56, 789000).timestamp())
     assert bench.Clocks._stamp("not a time") is None
+
+
+def test_reference_arm_prints_its_line():
+    """`bench.py --impl reference` times the CPU oracle (no GPU, no torch on
+    its path) and prints one JSON line with the contract's keys."""
+    import json
+    import subprocess
+    here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload",
+                          "water32_1MeV_pencil", "--steps", "1", "--warmup", "3",
+                          "--cpu-seconds", "1"], cwd=here, capture_output=True, text=True,
+                         timeout=300, env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "histories/s" and d["unit"] == "histories/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
+    assert d["config"]["workload"] == "water32_1MeV_pencil"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "histories/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs the reference arm; the others exit 0
+    without output or work."""
+    import subprocess
+    here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="", RANK="1", LOCAL_RANK="1", WORLD_SIZE="2")
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2",
+                          "--steps", "1", "--warmup", "3"], cwd=here, capture_output=True,
+                         text=True, timeout=120, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.strip() == ""
