@@ -911,6 +911,26 @@ static void electron_escape(orc_sim *S, orc_particle *p, double energy)
 
 enum { EV_CUT = 0, EV_HARD = 1, EV_MS = 2 };
 
+/* Hard Moller collision of an electron of kinetic energy Tn (Sec. 2.1 hard
+ * inelastic event above W_cc): eps = W/Tn from moller_sample; the delta ray
+ * (energy W) is banked at the binary-collision cosine and azimuth ph, and
+ * the primary (energy Tn - W) turns by its own binary cosine at ph + pi, so
+ * that momentum is conserved. */
+static void moller_event(orc_sim *S, orc_particle *p, double Tn, double wcc)
+{
+    double w2;
+    double eps = moller_sample(S, p, Tn, wcc, &w2);
+    double ph = 2.0 * PI * w2;
+    double W = eps * Tn, Tp = Tn - W;
+    double cd = binary_cos(Tn, W);
+    double cp = binary_cos(Tn, Tp);
+    double ud[3] = {p->u[0], p->u[1], p->u[2]};
+    rotate(ud, cd, ph);
+    bank(S, p, PT_ELECTRON, W, p->x, ud, p->iv);
+    rotate(p->u, cp, ph + PI);
+    p->E = Tp;
+}
+
 static void electron_track(orc_sim *S, orc_particle *p)
 {
     const orc_problem *P = S->P;
@@ -972,19 +992,8 @@ static void electron_track(orc_sim *S, orc_particle *p)
         if (!(v[0] * T->sigmax[m] < sh)) continue;
         if (S->hrec) S->hrec[(S->cur_hist - S->hrec_base) * HR_NI + HR_HARD]++;
         if (v[1] * sh < sm) {
-            /* Moller: eps = W/T on [W_cc/T, 1/2], proposal 1/eps^2 + rejection */
             S->res->moller++;
-            double w2;
-            double eps = moller_sample(S, p, Tn, wcc, &w2);
-            double ph = 2.0 * PI * w2;
-            double W = eps * Tn, Tp = Tn - W;
-            double cd = binary_cos(Tn, W);
-            double cp = binary_cos(Tn, Tp);
-            double ud[3] = {p->u[0], p->u[1], p->u[2]};
-            rotate(ud, cd, ph);
-            bank(S, p, PT_ELECTRON, W, p->x, ud, p->iv);
-            rotate(p->u, cp, ph + PI);
-            p->E = Tp;
+            moller_event(S, p, Tn, wcc);
         } else {
             /* bremsstrahlung: k = W_cb (T/W_cb)^xi, photon along the electron */
             S->res->brems++;
@@ -1478,6 +1487,50 @@ int orc_allot(const orc_problem *P, unsigned long long nb, unsigned long long *c
     uint64_t c[ORC_MAX_BINS];
     allot(P, nb, c);
     for (int j = 0; j < P->n_bins; j++) cnt[j] = c[j];
+    return 0;
+}
+
+/* One interaction event as the transport applies it (for the kinematics
+ * checks): kind 0 a Compton collision of a photon of energy E, kind 1 a
+ * hard Moller collision of an electron of kinetic energy E with cut `cut`.
+ * The particle moves along the unit vector u; sample s uses history s.
+ * out[8 s ..]: the particle after the event (E, u), then the banked
+ * secondary (E, u).  Absorption energies are set to zero, so every
+ * secondary is banked.  Returns 0, or -1 for a bad kind. */
+int orc_event(int kind, double E, const double u[3], double cut, unsigned long long seed,
+              long long n, double *out)
+{
+    if (kind != 0 && kind != 1) return -1;
+    orc_problem P;
+    memset(&P, 0, sizeof P);
+    P.nx = P.ny = P.nz = 1;
+    orc_sim S;
+    memset(&S, 0, sizeof S);
+    S.P = &P;
+    orc_result res;
+    memset(&res, 0, sizeof res);
+    S.res = &res;
+    S.key[0] = (uint32_t)seed; S.key[1] = (uint32_t)(seed >> 32);
+    for (long long s = 0; s < n; s++) {
+        orc_particle p;
+        memset(&p, 0, sizeof p);
+        p.hist = (uint32_t)s; p.pid = 1; p.E = E;
+        p.type = kind == 0 ? PT_PHOTON : PT_ELECTRON;
+        for (int a = 0; a < 3; a++) p.u[a] = u[a];
+        S.sp = 0;
+        if (kind == 0) {
+            int alive = 1;
+            compton(&S, &p, &alive);
+        } else {
+            moller_event(&S, &p, E, cut);
+        }
+        double *o = out + 8 * s;
+        o[0] = p.E;
+        for (int a = 0; a < 3; a++) o[1 + a] = p.u[a];
+        o[4] = S.sp ? S.stack[S.sp - 1].E : -1.0;
+        for (int a = 0; a < 3; a++) o[5 + a] = S.sp ? S.stack[S.sp - 1].u[a] : 0.0;
+    }
+    free(S.stack);
     return 0;
 }
 

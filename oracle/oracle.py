@@ -109,6 +109,9 @@ def lib():
                                             C.c_void_p]
         L.orc_allot.argtypes = [C.POINTER(OrcProblem), C.c_ulonglong, C.c_void_p]
         L.orc_rotate.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p]
+        L.orc_event.argtypes = [C.c_int, C.c_double, C.c_void_p, C.c_double, C.c_ulonglong,
+                                C.c_longlong, C.c_void_p]
+        L.orc_event.restype = C.c_int
         L.orc_sources.argtypes = [C.POINTER(OrcProblem), C.c_ulonglong, C.c_ulonglong, C.c_void_p]
         L.orc_beamlet_tables.argtypes = [C.POINTER(OrcProblem), C.c_void_p, C.c_void_p,
                                          C.c_void_p]
@@ -262,6 +265,17 @@ def rotate(u, cost: float, phi: float) -> np.ndarray:
     o = np.zeros(3)
     lib().orc_rotate(_ptr(a), cost, phi, _ptr(o))
     return o
+
+
+def event(kind: int, E: float, u, cut: float, n: int, seed: int = 1) -> np.ndarray:
+    """n single events as the transport applies them: kind 0 Compton of a
+    photon of energy E, kind 1 hard Moller of an electron of kinetic energy E
+    (cut W_cc).  Rows: particle after the event (E, u), banked secondary (E, u)."""
+    out = np.zeros((n, 8))
+    uu = np.ascontiguousarray(u, np.float64)
+    if lib().orc_event(kind, E, _ptr(uu), cut, seed, n, _ptr(out)) != 0:
+        raise ValueError("bad event kind")
+    return out
 
 
 def sources(prob, first: int, n: int) -> np.ndarray:

@@ -128,6 +128,43 @@ def test_kn_sampler_chi2(E):
     assert pv > 1e-3
 
 
+@pytest.mark.parametrize("kind,E,cut", [(0, 0.1, 0.0), (0, 1.5, 0.0), (0, 15.0, 0.0),
+                                        (1, 0.5, 0.2), (1, 3.0, 0.2), (1, 20.0, 0.2)])
+def test_event_conserves_energy_and_momentum(kind, E, cut):
+    """One Compton (kind 0) or hard Moller (kind 1) event as the transport
+    applies it: sampler, rotation of the particle, direction of the banked
+    secondary (Sec. 2.1 interactions, target electron at rest).  Kinetic
+    energy and the momentum vector are conserved to rounding, the Moller
+    delta ray is the slower electron and above the cut, and the scattered
+    particle's azimuth about the incoming direction is uniform."""
+    rng = np.random.default_rng(4)
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    n = 4000
+    ev = O.event(kind, E, u, cut, n, seed=9)
+    E1, u1, E2, u2 = ev[:, 0], ev[:, 1:4], ev[:, 4], ev[:, 5:8]
+    np.testing.assert_allclose(np.linalg.norm(u1, axis=1), 1.0, atol=1e-12)
+    np.testing.assert_allclose(np.linalg.norm(u2, axis=1), 1.0, atol=1e-12)
+    np.testing.assert_allclose(E1 + E2, E, rtol=1e-13)
+    pe = lambda T: np.sqrt(T * (T + 2 * MC2))          # electron momentum, MeV/c
+    if kind == 0:
+        p_in, p1 = E, E1                                  # photon momentum = energy
+        assert np.all(E1 >= E / (1 + 2 * E / MC2) * (1 - 1e-12))
+    else:
+        p_in, p1 = pe(E), pe(E1)
+        assert np.all(E2 <= E1 * (1 + 1e-12)) and np.all(E2 >= cut * (1 - 1e-12))
+    mom = p1[:, None] * u1 + pe(E2)[:, None] * u2
+    np.testing.assert_allclose(mom, np.broadcast_to(p_in * u, mom.shape), atol=1e-10 * p_in)
+    # azimuth of the outgoing particle about u
+    e1 = np.cross(u, [1.0, 0.0, 0.0])
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(u, e1)
+    phi = np.arctan2(u1 @ e2, u1 @ e1)
+    h, _ = np.histogram(phi, bins=16, range=(-math.pi, math.pi))
+    pv, _ = chi2_pvalue(h, np.full(16, n / 16))
+    assert pv > 1e-3
+
+
 def test_compton_electron_momentum():
     """|E u - E' u'| equals the recoil momentum sqrt(T(T+2mc2))."""
     E = 2.0
