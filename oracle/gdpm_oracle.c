@@ -1492,15 +1492,17 @@ int orc_allot(const orc_problem *P, unsigned long long nb, unsigned long long *c
 
 /* One interaction event as the transport applies it (for the kinematics
  * checks): kind 0 a Compton collision of a photon of energy E, kind 1 a
- * hard Moller collision of an electron of kinetic energy E with cut `cut`.
+ * hard Moller collision of an electron of kinetic energy E with cut `cut`,
+ * kind 2 the annihilation of a positron at rest at the end of its track.
  * The particle moves along the unit vector u; sample s uses history s.
  * out[8 s ..]: the particle after the event (E, u), then the banked
- * secondary (E, u).  Absorption energies are set to zero, so every
- * secondary is banked.  Returns 0, or -1 for a bad kind. */
+ * secondary (E, u); for kind 2 the two banked photons.  Absorption energies
+ * are set to zero, so every secondary is banked.  Returns 0, or -1 for a
+ * bad kind. */
 int orc_event(int kind, double E, const double u[3], double cut, unsigned long long seed,
               long long n, double *out)
 {
-    if (kind != 0 && kind != 1) return -1;
+    if (kind < 0 || kind > 2) return -1;
     orc_problem P;
     memset(&P, 0, sizeof P);
     P.nx = P.ny = P.nz = 1;
@@ -1515,16 +1517,24 @@ int orc_event(int kind, double E, const double u[3], double cut, unsigned long l
         orc_particle p;
         memset(&p, 0, sizeof p);
         p.hist = (uint32_t)s; p.pid = 1; p.E = E;
-        p.type = kind == 0 ? PT_PHOTON : PT_ELECTRON;
+        p.type = kind == 0 ? PT_PHOTON : (kind == 1 ? PT_ELECTRON : PT_POSITRON);
         for (int a = 0; a < 3; a++) p.u[a] = u[a];
         S.sp = 0;
+        double *o = out + 8 * s;
+        if (kind == 2) {
+            annihilate(&S, &p);
+            for (int k = 0; k < 2; k++) {
+                o[4 * k] = S.sp == 2 ? S.stack[k].E : -1.0;
+                for (int a = 0; a < 3; a++) o[4 * k + 1 + a] = S.sp == 2 ? S.stack[k].u[a] : 0.0;
+            }
+            continue;
+        }
         if (kind == 0) {
             int alive = 1;
             compton(&S, &p, &alive);
         } else {
             moller_event(&S, &p, E, cut);
         }
-        double *o = out + 8 * s;
         o[0] = p.E;
         for (int a = 0; a < 3; a++) o[1 + a] = p.u[a];
         o[4] = S.sp ? S.stack[S.sp - 1].E : -1.0;

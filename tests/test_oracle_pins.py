@@ -165,6 +165,25 @@ def test_event_conserves_energy_and_momentum(kind, E, cut):
     assert pv > 1e-3
 
 
+def test_annihilation_photons_back_to_back_and_isotropic():
+    """A positron at rest at the end of its track gives two photons of m c^2
+    each, back to back, with an isotropic direction (Sec. 2.1 positrons):
+    zero total momentum, uniform cos(theta) and azimuth."""
+    n = 20000
+    ev = O.event(2, 0.0, [0.0, 0.0, 1.0], 0.0, n, seed=21)
+    E1, u1, E2, u2 = ev[:, 0], ev[:, 1:4], ev[:, 4], ev[:, 5:8]
+    assert np.all(E1 == MC2) and np.all(E2 == MC2)
+    np.testing.assert_allclose(np.linalg.norm(u1, axis=1), 1.0, atol=1e-12)
+    np.testing.assert_allclose(u1 + u2, 0.0, atol=1e-15)
+    # a uniform direction has a uniform cosine on every axis and a uniform
+    # azimuth about z
+    for x, lo, hi in [(u1[:, 2], -1.0, 1.0), (u1[:, 0], -1.0, 1.0),
+                      (np.arctan2(u1[:, 1], u1[:, 0]), -math.pi, math.pi)]:
+        h, _ = np.histogram(x, bins=20, range=(lo, hi))
+        pv, _ = chi2_pvalue(h, np.full(20, n / 20))
+        assert pv > 1e-3
+
+
 def test_compton_electron_momentum():
     """|E u - E' u'| equals the recoil momentum sqrt(T(T+2mc2))."""
     E = 2.0
