@@ -780,6 +780,17 @@ static int woodcock_flight(orc_sim *S, orc_particle *p, const double u[4], int *
     return 2;
 }
 
+/* Pair production by a photon of energy E > 2 m c^2 (READING): the electron
+ * takes the share xi of E - 2 m c^2, the positron the rest, both along the
+ * photon. */
+static void pair_event(orc_sim *S, orc_particle *p, double xi)
+{
+    double tav = p->E - 2.0 * MC2;
+    double t1 = xi * tav, t2 = tav - t1;
+    bank(S, p, PT_ELECTRON, t1, p->x, p->u, p->iv);
+    bank(S, p, PT_POSITRON, t2, p->x, p->u, p->iv);
+}
+
 static void photon_track(orc_sim *S, orc_particle *p)
 {
     const orc_problem *P = S->P;
@@ -819,11 +830,7 @@ static void photon_track(orc_sim *S, orc_particle *p)
             alive = 0;
         } else {
             S->res->pair++;
-            double tav = p->E - 2.0 * MC2;
-            double t1 = u[3] * tav, t2 = tav - t1;
-            bank(S, p, PT_ELECTRON, t1, p->x, p->u, p->iv);
-            bank(S, p, PT_POSITRON, t2, p->x, p->u, p->iv);
-            if (P->flags & ORC_NO_ANNIHILATION) {}   /* rest mass accounted at positron end */
+            pair_event(S, p, u[3]);     /* rest mass accounted at the positron's end */
             S->res->ph_terminated++;
             alive = 0;
         }
@@ -1493,16 +1500,19 @@ int orc_allot(const orc_problem *P, unsigned long long nb, unsigned long long *c
 /* One interaction event as the transport applies it (for the kinematics
  * checks): kind 0 a Compton collision of a photon of energy E, kind 1 a
  * hard Moller collision of an electron of kinetic energy E with cut `cut`,
- * kind 2 the annihilation of a positron at rest at the end of its track.
+ * kind 2 the annihilation of a positron at rest at the end of its track,
+ * kind 3 pair production by a photon of energy E (its share from the
+ * fourth uniform of one draw, as the flight supplies it).
  * The particle moves along the unit vector u; sample s uses history s.
  * out[8 s ..]: the particle after the event (E, u), then the banked
- * secondary (E, u); for kind 2 the two banked photons.  Absorption energies
+ * secondary (E, u); for kinds 2 and 3 the two banked particles (for kind 3
+ * the electron, then the positron).  Absorption energies
  * are set to zero, so every secondary is banked.  Returns 0, or -1 for a
  * bad kind. */
 int orc_event(int kind, double E, const double u[3], double cut, unsigned long long seed,
               long long n, double *out)
 {
-    if (kind < 0 || kind > 2) return -1;
+    if (kind < 0 || kind > 3) return -1;
     orc_problem P;
     memset(&P, 0, sizeof P);
     P.nx = P.ny = P.nz = 1;
@@ -1517,12 +1527,18 @@ int orc_event(int kind, double E, const double u[3], double cut, unsigned long l
         orc_particle p;
         memset(&p, 0, sizeof p);
         p.hist = (uint32_t)s; p.pid = 1; p.E = E;
-        p.type = kind == 0 ? PT_PHOTON : (kind == 1 ? PT_ELECTRON : PT_POSITRON);
+        p.type = (kind == 0 || kind == 3) ? PT_PHOTON : (kind == 1 ? PT_ELECTRON : PT_POSITRON);
         for (int a = 0; a < 3; a++) p.u[a] = u[a];
         S.sp = 0;
         double *o = out + 8 * s;
-        if (kind == 2) {
-            annihilate(&S, &p);
+        if (kind >= 2) {
+            if (kind == 2) {
+                annihilate(&S, &p);
+            } else {
+                double w[4];
+                draw4(&S, &p, w);
+                pair_event(&S, &p, w[3]);
+            }
             for (int k = 0; k < 2; k++) {
                 o[4 * k] = S.sp == 2 ? S.stack[k].E : -1.0;
                 for (int a = 0; a < 3; a++) o[4 * k + 1 + a] = S.sp == 2 ? S.stack[k].u[a] : 0.0;

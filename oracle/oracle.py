@@ -270,9 +270,10 @@ def rotate(u, cost: float, phi: float) -> np.ndarray:
 def event(kind: int, E: float, u, cut: float, n: int, seed: int = 1) -> np.ndarray:
     """n single events as the transport applies them: kind 0 Compton of a
     photon of energy E, kind 1 hard Moller of an electron of kinetic energy E
-    (cut W_cc), kind 2 annihilation of a positron at rest.  Rows: particle
-    after the event (E, u), banked secondary (E, u); for kind 2 the two
-    photons."""
+    (cut W_cc), kind 2 annihilation of a positron at rest, kind 3 pair
+    production by a photon of energy E.  Rows: particle after the event
+    (E, u), banked secondary (E, u); for kind 2 the two photons, for kind 3
+    the electron and the positron."""
     out = np.zeros((n, 8))
     uu = np.ascontiguousarray(u, np.float64)
     if lib().orc_event(kind, E, _ptr(uu), cut, seed, n, _ptr(out)) != 0:

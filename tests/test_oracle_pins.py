@@ -184,6 +184,25 @@ def test_annihilation_photons_back_to_back_and_isotropic():
         assert pv > 1e-3
 
 
+@pytest.mark.parametrize("E", [1.5, 6.0])
+def test_pair_split_uniform_and_along_the_photon(E):
+    """Pair production (Sec. 2.1 photon interactions; the paper gives no
+    energy split, the reading is a uniform share): electron and positron
+    kinetic energies add to E - 2 m c^2, the electron's share is uniform on
+    (0, 1), and both leave along the photon."""
+    n = 20000
+    u = np.array([0.6, 0.0, 0.8])
+    ev = O.event(3, E, u, 0.0, n, seed=17)
+    t1, u1, t2, u2 = ev[:, 0], ev[:, 1:4], ev[:, 4], ev[:, 5:8]
+    tav = E - 2 * MC2
+    np.testing.assert_allclose(t1 + t2, tav, rtol=1e-13)
+    assert np.all(t1 >= 0) and np.all(t2 >= 0)
+    assert np.all(u1 == u) and np.all(u2 == u)
+    h, _ = np.histogram(t1 / tav, bins=20, range=(0.0, 1.0))
+    pv, _ = chi2_pvalue(h, np.full(20, n / 20))
+    assert pv > 1e-3
+
+
 def test_compton_electron_momentum():
     """|E u - E' u'| equals the recoil momentum sqrt(T(T+2mc2))."""
     E = 2.0
