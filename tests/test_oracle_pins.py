@@ -549,6 +549,40 @@ def test_subcutoff_electron_deposits_in_first_voxel():
     assert np.count_nonzero(edep) == 1
 
 
+@pytest.mark.parametrize("case", ["ssd100_field10", "paper_sec31"])
+def test_point_field_primaries(case):
+    """Point source aimed uniformly at a rectangle (Sec. 2.3 field
+    geometry): each primary enters the phantom on the z = 0 face, along the
+    line from the source, with its entry point uniform over the field as
+    seen on that face.  For the Sec. 3.1 set-up (SSD 90 cm, 10 x 10 cm at
+    SAD 100 cm) the central projection makes that a 9 x 9 cm square."""
+    if case == "ssd100_field10":
+        p = W.slab_photon_problem(n_histories=20000, n_batches=1, shape=(64, 64, 32))
+        half, ssd = 5.0, 100.0
+    else:
+        p = W.paper_slab_problem("lung", W.PHOTON, n_histories=20000, n_batches=1)
+        half, ssd = 4.5, 90.0
+    n = 20000
+    rows = O.sources(p, 0, n)
+    x, u, entered = rows[:, 0:3], rows[:, 3:6], rows[:, 7]
+    X, Y, _ = p.phantom.extent
+    src = np.array([X / 2, Y / 2, -ssd])
+    assert np.all(entered == 1.0)
+    np.testing.assert_allclose(x[:, 2], 0.0, atol=1e-9)
+    d = x - src
+    np.testing.assert_allclose(u, d / np.linalg.norm(d, axis=1)[:, None], atol=1e-12)
+    for c, mid in [(x[:, 0], X / 2), (x[:, 1], Y / 2)]:
+        assert np.all(np.abs(c - mid) <= half * (1 + 1e-9))
+        h, _ = np.histogram(c, bins=20, range=(mid - half, mid + half))
+        pv, _ = chi2_pvalue(h, np.full(20, n / 20))
+        assert pv > 1e-3
+    # the two coordinates are independent: uniform over the square
+    h2, _, _ = np.histogram2d(x[:, 0], x[:, 1], bins=8,
+                              range=[[X / 2 - half, X / 2 + half], [Y / 2 - half, Y / 2 + half]])
+    pv, _ = chi2_pvalue(h2.ravel(), np.full(64, n / 64))
+    assert pv > 1e-3
+
+
 def test_spectrum_allotment():
     p = W.slab_photon_problem(n_histories=1)
     w = p.source.spectrum.weights
