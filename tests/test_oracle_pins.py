@@ -583,6 +583,44 @@ def test_point_field_primaries(case):
     assert pv > 1e-3
 
 
+@pytest.mark.parametrize("gantry", [0.0, 51.4, 243.0])
+def test_beamlet_primaries(gantry):
+    """A fluence-map beamlet (Sec. 2.3.1 beamlets in a gantry frame): the
+    source sits at SAD from the isocentre along the gantry direction; each
+    primary's ray, back-projected to the isocentre plane, lands uniformly in
+    the beamlet's rectangle, and the primary enters on a face of the phantom
+    along that ray."""
+    ph = W.homogeneous_phantom((64, 64, 64), (0.5, 0.5, 0.5), W.WATER)
+    u0, v0, size = -2.0, 1.0, 3.0
+    src_desc = W.single_beamlet(ph, gantry, u0, v0, size)
+    p = W.Problem(ph, src_desc, 20000, 1, eabs_photon=0.05, eabs_electron=0.2, e_min=0.005,
+                  e_max=6.5)
+    row = np.asarray(src_desc.beamlets, np.float64)[0]
+    src, iso, au, av = row[0:3], row[3:6], row[6:9], row[9:12]
+    t = math.radians(gantry)
+    np.testing.assert_allclose(src - iso, 100.0 * np.array([math.sin(t), -math.cos(t), 0.0]),
+                               atol=1e-12)
+    n = 20000
+    rows = O.sources(p, 0, n)
+    x, u, entered = rows[:, 0:3], rows[:, 3:6], rows[:, 7]
+    assert np.all(entered == 1.0)
+    d = x - src
+    np.testing.assert_allclose(u, d / np.linalg.norm(d, axis=1)[:, None], atol=1e-12)
+    ext = np.array(ph.extent)
+    on_face = np.min(np.minimum(np.abs(x), np.abs(x - ext)), axis=1)
+    assert np.all(on_face < 1e-9)
+    nrm = (iso - src) / np.linalg.norm(iso - src)
+    s_hit = ((iso - src) @ nrm) / (u @ nrm)
+    hit = src + s_hit[:, None] * u - iso
+    a, b = hit @ au, hit @ av
+    np.testing.assert_allclose(hit @ nrm, 0.0, atol=1e-9)
+    for c, lo in [(a, u0), (b, v0)]:
+        assert np.all((c >= lo - 1e-9) & (c <= lo + size + 1e-9))
+        h, _ = np.histogram(c, bins=15, range=(lo, lo + size))
+        pv, _ = chi2_pvalue(h, np.full(15, n / 15))
+        assert pv > 1e-3
+
+
 def test_spectrum_allotment():
     p = W.slab_photon_problem(n_histories=1)
     w = p.source.spectrum.weights
