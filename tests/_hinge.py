@@ -35,8 +35,9 @@ def problem(n_histories, request_id=0):
                      e_max=T0 * 1.05, flags=W.FLAG_NO_HARD, request_id=request_id)
 
 
-def closed_form(p):
-    """Expected energy-weighted depth (cm) from the deterministic step sequence."""
+def step_sequence(p):
+    """The deterministic CSDA steps from T0 to E_abs: (mass length, energy
+    loss, mean deflection cosine m) per step."""
     k, eabs = p.ms_loss_fraction, p.eabs_electron
     rng_of = lambda t: float(O.evaluate(p, 0, O.OF_RANGE, t)[0])      # CSDA range, g/cm^2
     x0 = 1.0 / float(O.evaluate(p, 0, O.OF_BCONST, 1.0)[0])           # radiation length
@@ -56,6 +57,13 @@ def closed_form(p):
         if te <= eabs:
             break
         E = te
+    return steps
+
+
+def closed_form(p):
+    """Expected energy-weighted depth (cm) from the deterministic step sequence."""
+    eabs = p.eabs_electron
+    steps = step_sequence(p)
     Z, c, num = Z0, 1.0, 0.0
     for x, dT, m in steps:                      # density 1: mass length = cm
         num += dT * (Z + x * c * (1.0 / 3.0 + m / 6.0))

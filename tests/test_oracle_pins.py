@@ -454,6 +454,14 @@ def test_random_hinge_depth_moment():
     standard error."""
     from tests import _hinge as H
     expect = H.closed_form(H.problem(1))
+    # the steps themselves are deterministic: every history takes the same
+    # number of them and the same mass path, the closed-form sequence's
+    steps = H.step_sequence(H.problem(1))
+    _, _, _, rec, recd = O.run(H.problem(2000), per_history=True)
+    assert np.all(rec[:, O.HR_EL_STEPS] == len(steps))
+    path = recd[:, O.HD_EL_MASSPATH]
+    assert path.max() - path.min() <= 1e-12 * path.max()
+    assert path[0] == pytest.approx(sum(x for x, _, _ in steps), rel=1e-4)
     cents = []
     for rid in range(16):
         dose, _, led = O.run(H.problem(5000, request_id=rid))
