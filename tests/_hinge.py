@@ -72,12 +72,64 @@ def closed_form(p):
     return (num + eabs * Z) / T0
 
 
+def _g1_of_a(a):
+    return 2.0 * a * ((1.0 + a) * np.log1p(1.0 / a) - 1.0)
+
+
+def _mu2_mean(g1):
+    """E[mu^2] of the screened-Rutherford law p(mu) ~ (1 - mu + 2A)^-2 whose
+    E[1 - mu] is g1 (quadrature of the density; isotropic for g1 >= 1)."""
+    from scipy import integrate
+    if g1 >= 1.0:
+        return 1.0 / 3.0
+    a = optimize.brentq(lambda x: _g1_of_a(x) - g1, 1e-30, 1e12, xtol=1e-300, rtol=1e-15)
+    f = lambda mu: (1.0 - mu + 2.0 * a) ** -2
+    pts = [1.0 - 1e-3, 1.0 - 1e-6]
+    nrm = integrate.quad(f, -1.0, 1.0, epsabs=0, epsrel=1e-12, points=pts)[0]
+    return integrate.quad(lambda mu: mu * mu * f(mu), -1.0, 1.0, epsabs=0, epsrel=1e-12,
+                          points=pts)[0] / nrm
+
+
+def second_moment(p):
+    """Expected energy-weighted (z - Z0)^2 (cm^2).  Along z only: a straight
+    piece of length s moves z by s w, a deflection scales E[w] and E[z w] by
+    m_j and maps E[w^2] to q E[w^2] + (1 - q)(1 - E[w^2])/2 with q = E[mu^2]
+    (uniform azimuth).  The hinge position zeta ~ U(0,1) enters as a
+    polynomial of degree 3, averaged exactly by 8-point Gauss-Legendre."""
+    zeta, wq = np.polynomial.legendre.leggauss(8)
+    zeta, wq = 0.5 * (zeta + 1.0), 0.5 * wq
+    z, w, z2, zw, w2 = 0.0, 1.0, 0.0, 0.0, 1.0
+    num = 0.0
+    for x, dT, m in step_sequence(p):
+        q = _mu2_mean(1.0 - m)
+        acc = np.zeros(6)
+        for zt, wt in zip(zeta, wq):
+            a, b = zt * x, (1.0 - zt) * x
+            avg1 = z2 + a * zw + a * a * w2 / 3.0
+            z_1, z2_1, zw_1 = z + a * w, z2 + 2 * a * zw + a * a * w2, zw + a * w2
+            w_d, zw_d, w2_d = m * w, m * zw_1, q * w2 + (1.0 - q) * (1.0 - w2) / 2.0
+            avg2 = z2_1 + b * zw_d + b * b * w2_d / 3.0
+            acc += wt * np.array([(a * avg1 + b * avg2) / x, z_1 + b * w_d,
+                                  z2_1 + 2 * b * zw_d + b * b * w2_d, zw_d + b * w2_d, w2_d, w_d])
+        num += dT * acc[0]
+        z, z2, zw, w2, w = acc[1], acc[2], acc[3], acc[4], acc[5]
+    return (num + p.eabs_electron * z2) / T0
+
+
 def depth_moment(dose):
     """(energy-weighted depth in cm, energy per history in MeV) of a dose grid
     in MeV/g per history; voxel centres stand in for positions inside a voxel."""
     e = np.asarray(dose, np.float64) * (AREA * DZ)
     zc = (np.arange(NZ) + 0.5) * DZ
     return float((e * zc).sum() / e.sum()), float(e.sum())
+
+
+def depth_second_moment(dose):
+    """Energy-weighted (z - Z0)^2 of a dose grid (cm^2), with the DZ^2/12 of
+    positions spread over a voxel added to the voxel-centre sum."""
+    e = np.asarray(dose, np.float64) * (AREA * DZ)
+    zc = (np.arange(NZ) + 0.5) * DZ - Z0
+    return float((e * zc * zc).sum() / e.sum()) + DZ * DZ / 12.0
 
 
 # The same electron in z-layers of water at different densities.  Every step

@@ -462,18 +462,26 @@ def test_random_hinge_depth_moment():
     path = recd[:, O.HD_EL_MASSPATH]
     assert path.max() - path.min() <= 1e-12 * path.max()
     assert path[0] == pytest.approx(sum(x for x, _, _ in steps), rel=1e-4)
-    cents = []
+    cents, secs = [], []
     for rid in range(16):
         dose, _, led = O.run(H.problem(5000, request_id=rid))
         assert led["escaped"] == 0.0
         z, e = H.depth_moment(dose)
         assert e == pytest.approx(H.T0, rel=1e-9)
         cents.append(z)
+        secs.append(H.depth_second_moment(dose))
     se = np.std(cents, ddof=1) / math.sqrt(len(cents))
     print("depth moment %.5f cm, closed form %.5f, se %.5f" % (np.mean(cents), expect, se))
     assert se < 1e-3
     # voxel centres stand in for positions inside a voxel: a bias far below dz
     assert abs(np.mean(cents) - expect) < 4.0 * se + 2e-4
+    # the second moment also sees the spread of the deflection law: the same
+    # mean cosine at a fixed angle would read 0.1232 instead of 0.1398 cm^2
+    expect2 = H.second_moment(H.problem(1))
+    se2 = np.std(secs, ddof=1) / math.sqrt(len(secs))
+    print("second moment %.6f cm^2, closed form %.6f, se %.6f" % (np.mean(secs), expect2, se2))
+    assert se2 < 1e-3
+    assert abs(np.mean(secs) - expect2) < 4.0 * se2 + 2e-4
 
 
 def test_walk_spends_mass_length_voxel_by_voxel():
