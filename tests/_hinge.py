@@ -161,3 +161,13 @@ def mass_depth_moment(dose, rho):
     e = np.asarray(dose, np.float64) * rho * (AREA * DZ)
     mc = 0.5 * (faces[:-1] + faces[1:])
     return float((e * mc).sum() / e.sum()), float(e.sum())
+
+
+def mass_depth_second_moment(dose, rho, m0):
+    """Energy-weighted (m - m0)^2 in mass depth (g^2/cm^4), with each voxel's
+    (rho DZ)^2/12 of positions spread over it."""
+    rho = np.asarray(rho, np.float64)
+    faces = np.concatenate([[0.0], np.cumsum(rho * DZ)])
+    e = np.asarray(dose, np.float64) * rho * (AREA * DZ)
+    mc = 0.5 * (faces[:-1] + faces[1:]) - m0
+    return float((e * (mc * mc + (rho * DZ) ** 2 / 12.0)).sum() / e.sum())

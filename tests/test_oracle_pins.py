@@ -503,6 +503,10 @@ def test_walk_spends_mass_length_voxel_by_voxel():
         print("run %d: layered %.6f, homogeneous %.6f g/cm^2 past the start"
               % (rid, ml - H.LAYER_M0, zh - H.Z0))
         assert abs((ml - H.LAYER_M0) - (zh - H.Z0)) < 3e-4
+        # and its spread: the second moment in mass depth
+        sl = H.mass_depth_second_moment(dl, pl.phantom.rho, H.LAYER_M0)
+        sh = H.depth_second_moment(dh)
+        assert abs(sl - sh) < 3e-4, (sl, sh)
 
 
 # --------------------------------------------------------------------- whole runs
