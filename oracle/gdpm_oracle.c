@@ -780,6 +780,20 @@ static int woodcock_flight(orc_sim *S, orc_particle *p, const double u[4], int *
     return 2;
 }
 
+/* Photoelectric absorption (READING): the photoelectron takes the photon's
+ * whole energy (no binding), along the photon or, with ORC_SAUTER, at an
+ * angle from Sauter's K-shell distribution. */
+static void photoelectric_event(orc_sim *S, orc_particle *p)
+{
+    double d[3] = {p->u[0], p->u[1], p->u[2]};
+    if (S->P->flags & ORC_SAUTER) {
+        double mu, phi;
+        sample_sauter(S, p, p->E, &mu, &phi);
+        rotate(d, mu, phi);
+    }
+    bank(S, p, PT_ELECTRON, p->E, p->x, d, p->iv);
+}
+
 /* Pair production by a photon of energy E > 2 m c^2 (READING): the electron
  * takes the share xi of E - 2 m c^2, the positron the rest, both along the
  * photon. */
@@ -819,13 +833,7 @@ static void photon_track(orc_sim *S, orc_particle *p)
             compton(S, p, &alive);
         } else if (type == 1) {
             S->res->photoelectric++;
-            double d[3] = {p->u[0], p->u[1], p->u[2]};
-            if (P->flags & ORC_SAUTER) {
-                double mu, phi;
-                sample_sauter(S, p, p->E, &mu, &phi);
-                rotate(d, mu, phi);
-            }
-            bank(S, p, PT_ELECTRON, p->E, p->x, d, p->iv);
+            photoelectric_event(S, p);
             S->res->ph_terminated++;
             alive = 0;
         } else {
@@ -938,6 +946,16 @@ static void moller_event(orc_sim *S, orc_particle *p, double Tn, double wcc)
     p->E = Tp;
 }
 
+/* Hard bremsstrahlung of an electron of kinetic energy Tn (READING): a
+ * photon of energy k = W_cb (Tn/W_cb)^xi along the electron, which goes on
+ * with Tn - k. */
+static void brems_event(orc_sim *S, orc_particle *p, double Tn, double wcb, double xi)
+{
+    double kph = brems_k(Tn, wcb, xi);
+    bank(S, p, PT_PHOTON, kph, p->x, p->u, p->iv);
+    p->E = Tn - kph;
+}
+
 static void electron_track(orc_sim *S, orc_particle *p)
 {
     const orc_problem *P = S->P;
@@ -1002,11 +1020,8 @@ static void electron_track(orc_sim *S, orc_particle *p)
             S->res->moller++;
             moller_event(S, p, Tn, wcc);
         } else {
-            /* bremsstrahlung: k = W_cb (T/W_cb)^xi, photon along the electron */
             S->res->brems++;
-            double kph = brems_k(Tn, wcb, v[2]);
-            bank(S, p, PT_PHOTON, kph, p->x, p->u, p->iv);
-            p->E = Tn - kph;
+            brems_event(S, p, Tn, wcb, v[2]);
         }
     }
 }
@@ -1502,7 +1517,11 @@ int orc_allot(const orc_problem *P, unsigned long long nb, unsigned long long *c
  * hard Moller collision of an electron of kinetic energy E with cut `cut`,
  * kind 2 the annihilation of a positron at rest at the end of its track,
  * kind 3 pair production by a photon of energy E (its share from the
- * fourth uniform of one draw, as the flight supplies it).
+ * fourth uniform of one draw, as the flight supplies it), kind 4 the
+ * photoelectric absorption of a photon of energy E (Sauter angles when
+ * cut != 0), kind 5 a hard bremsstrahlung event of an electron of kinetic
+ * energy E with cut W_cb = cut (its uniform the third of one draw, as the
+ * hard-event candidate supplies it).
  * The particle moves along the unit vector u; sample s uses history s.
  * out[8 s ..]: the particle after the event (E, u), then the banked
  * secondary (E, u); for kinds 2 and 3 the two banked particles (for kind 3
@@ -1512,10 +1531,11 @@ int orc_allot(const orc_problem *P, unsigned long long nb, unsigned long long *c
 int orc_event(int kind, double E, const double u[3], double cut, unsigned long long seed,
               long long n, double *out)
 {
-    if (kind < 0 || kind > 3) return -1;
+    if (kind < 0 || kind > 5) return -1;
     orc_problem P;
     memset(&P, 0, sizeof P);
     P.nx = P.ny = P.nz = 1;
+    if (kind == 4 && cut != 0.0) P.flags |= ORC_SAUTER;
     orc_sim S;
     memset(&S, 0, sizeof S);
     S.P = &P;
@@ -1527,11 +1547,12 @@ int orc_event(int kind, double E, const double u[3], double cut, unsigned long l
         orc_particle p;
         memset(&p, 0, sizeof p);
         p.hist = (uint32_t)s; p.pid = 1; p.E = E;
-        p.type = (kind == 0 || kind == 3) ? PT_PHOTON : (kind == 1 ? PT_ELECTRON : PT_POSITRON);
+        p.type = (kind == 0 || kind == 3 || kind == 4) ? PT_PHOTON
+               : (kind == 2 ? PT_POSITRON : PT_ELECTRON);
         for (int a = 0; a < 3; a++) p.u[a] = u[a];
         S.sp = 0;
         double *o = out + 8 * s;
-        if (kind >= 2) {
+        if (kind == 2 || kind == 3) {
             if (kind == 2) {
                 annihilate(&S, &p);
             } else {
@@ -1548,8 +1569,14 @@ int orc_event(int kind, double E, const double u[3], double cut, unsigned long l
         if (kind == 0) {
             int alive = 1;
             compton(&S, &p, &alive);
-        } else {
+        } else if (kind == 1) {
             moller_event(&S, &p, E, cut);
+        } else if (kind == 4) {
+            photoelectric_event(&S, &p);
+        } else {
+            double v[4];
+            draw4(&S, &p, v);
+            brems_event(&S, &p, E, cut, v[2]);
         }
         o[0] = p.E;
         for (int a = 0; a < 3; a++) o[1 + a] = p.u[a];

@@ -271,9 +271,10 @@ def event(kind: int, E: float, u, cut: float, n: int, seed: int = 1) -> np.ndarr
     """n single events as the transport applies them: kind 0 Compton of a
     photon of energy E, kind 1 hard Moller of an electron of kinetic energy E
     (cut W_cc), kind 2 annihilation of a positron at rest, kind 3 pair
-    production by a photon of energy E.  Rows: particle after the event
-    (E, u), banked secondary (E, u); for kind 2 the two photons, for kind 3
-    the electron and the positron."""
+    production by a photon of energy E, kind 4 photoelectric absorption
+    (Sauter angles when cut != 0), kind 5 hard bremsstrahlung (cut W_cb).
+    Rows: particle after the event (E, u), banked secondary (E, u); for
+    kind 2 the two photons, for kind 3 the electron and the positron."""
     out = np.zeros((n, 8))
     uu = np.ascontiguousarray(u, np.float64)
     if lib().orc_event(kind, E, _ptr(uu), cut, seed, n, _ptr(out)) != 0:

@@ -203,6 +203,43 @@ def test_pair_split_uniform_and_along_the_photon(E):
     assert pv > 1e-3
 
 
+@pytest.mark.parametrize("sauter", [False, True])
+def test_photoelectric_event(sauter):
+    """Photoelectric absorption (Sec. 2.1 photon interactions; reading: no
+    binding): the photoelectron takes the whole photon energy, along the
+    photon, or with the Sauter variant (Sec. 4) at the angle the Sauter
+    sampler draws for the same history (same random stream)."""
+    n, E = 5000, 0.08
+    u = np.array([0.0, 0.6, 0.8])
+    ev = O.event(4, E, u, 1.0 if sauter else 0.0, n, seed=13)
+    Ee, ue = ev[:, 4], ev[:, 5:8]
+    assert np.all(Ee == E)
+    np.testing.assert_allclose(np.linalg.norm(ue, axis=1), 1.0, atol=1e-12)
+    if sauter:
+        mu, _ = O.sample(O.OS_SAUTER, E, 0.0, n, seed=13)
+        np.testing.assert_allclose(ue @ u, mu, atol=1e-12)
+    else:
+        assert np.all(ue == u)
+
+
+@pytest.mark.parametrize("T", [0.5, 6.0, 20.0])
+def test_bremsstrahlung_event(T):
+    """Hard bremsstrahlung (Sec. 2.1 hard events; reading dSigma/dk = B/k):
+    the photon energy k lies in [W_cb, T] with ln(k/W_cb)/ln(T/W_cb)
+    uniform, the photon leaves along the electron, and the electron goes on
+    in the same direction with T - k."""
+    n, wcb = 20000, 0.05
+    u = np.array([0.6, 0.0, 0.8])
+    ev = O.event(5, T, u, wcb, n, seed=19)
+    Te, ue, k, uk = ev[:, 0], ev[:, 1:4], ev[:, 4], ev[:, 5:8]
+    np.testing.assert_allclose(Te + k, T, rtol=1e-13)
+    assert np.all(k >= wcb * (1 - 1e-12)) and np.all(k <= T * (1 + 1e-12))
+    assert np.all(ue == u) and np.all(uk == u)
+    h, _ = np.histogram(np.log(k / wcb) / math.log(T / wcb), bins=20, range=(0.0, 1.0))
+    pv, _ = chi2_pvalue(h, np.full(20, n / 20))
+    assert pv > 1e-3
+
+
 def test_compton_electron_momentum():
     """|E u - E' u'| equals the recoil momentum sqrt(T(T+2mc2))."""
     E = 2.0
