@@ -85,3 +85,21 @@ def test_sec_4_water_case():
         assert p.n_histories == n and p.flags & W.FLAG_NO_ANNIHILATION
         assert p.source.kind == "pencil" and p.source.origin[:2] == (16.0, 16.0)
         assert p.source.spectrum.edges[0] == p.source.spectrum.edges[-1] == 15.0
+
+
+def test_vmat_apertures_have_uniform_fluence():
+    """Each control point's MLC aperture is a set of leaf-pair openings whose
+    weights equal their open areas, so the fluence is uniform over the
+    aperture (Sec. 2.3 aperture sources); the pairs tile the field along v
+    without overlap and open inside it along u."""
+    ph = W.ct_phantom((64, 64, 32), (1.0, 1.0, 1.0))
+    rows = np.asarray(W.vmat_arc(ph, n_points=12).beamlets)
+    u0, u1, v0, v1, wgt = rows[:, 12], rows[:, 13], rows[:, 14], rows[:, 15], rows[:, 16]
+    np.testing.assert_allclose(wgt, (u1 - u0) * (v1 - v0), rtol=1e-12)
+    assert np.all(u1 > u0) and np.all(u0 >= -5.0) and np.all(u1 <= 5.0)
+    np.testing.assert_allclose(v1 - v0, 0.5)
+    for src in np.unique(np.round(rows[:, :3], 9), axis=0):
+        cp = rows[np.all(np.abs(rows[:, :3] - src) < 1e-6, axis=1)]
+        vs = np.sort(cp[:, 14])
+        assert np.all(np.diff(vs) >= 0.5 - 1e-12)
+        assert vs[0] >= -5.0 - 1e-12 and vs[-1] + 0.5 <= 5.0 + 1e-12
