@@ -198,7 +198,8 @@ enum {
 /* Upload a voxel phantom (Sec. 2.2.1 initialisation): `material` is nx*ny*nz
  * uint8 material indices into the table set, `density` nx*ny*nz float
  * densities in g/cm3 (> 0), both x fastest.  Host or device arrays; copied.
- * Errors: GDPM_E_ARG (non-positive sizes, nx|ny|nz > 1024), GDPM_E_NOMEM. */
+ * Errors: GDPM_E_ARG (non-positive sizes, nx|ny|nz > 1024, a density that is
+ * zero, negative, NaN or infinite), GDPM_E_NOMEM. */
 int gdpm_phantom_create(gdpm_ctx *ctx, int nx, int ny, int nz, float dx, float dy, float dz,
                         const uint8_t *material, const float *density, gdpm_phantom **out);
 /* Release a phantom (Sec. 2.2.1) and its device memory; waits for work on
@@ -463,13 +464,14 @@ int gdpm_debug_beamlets(gdpm_ctx *ctx, uint64_t first, uint64_t n, int32_t *out)
 
 /* ------------------------------------------------------------------ no allocation */
 
-/* gdpm_simulate_noalloc -- the same dose calculation as gdpm_simulate
- * (Sec. 2.2.1), for small problems, without allocating any memory.  The
- * paper has no
- * counterpart; this exists for callers that cannot call cudaMalloc: code that
- * runs while a CUDA graph is being captured (allocation is not allowed during
- * stream capture), and host applications that hand all device memory to
- * their own allocator and forbid libraries from allocating behind it.
+/* gdpm_simulate_noalloc -- the same dose calculation as gdpm_simulate, for
+ * small problems, without allocating any memory.  The paper has no
+ * counterpart.  It exists for callers that cannot call cudaMalloc: host
+ * applications that hand all device memory to their own allocator (a pool
+ * sized at start-up, a planning system with a fixed memory budget) and
+ * forbid libraries from allocating behind it.  The call synchronizes its
+ * stream and stages small arrays through host memory before it returns, so
+ * it is an ordinary blocking call.
  *
  * All work buffers (batch tally, batch sums, particle queues, counters,
  * source arrays, Woodcock majorant) come from one file-scope device array of

@@ -1,9 +1,10 @@
 // gdpm_simulate_noalloc: the dose calculation of gdpm_simulate for small
-// problems, for callers that must not allocate device memory -- for example
-// code that runs while a larger CUDA graph is being captured (an allocation
-// during stream capture is not allowed), or a host application that hands
-// the GPU's memory to its own allocator and forbids libraries from calling
-// cudaMalloc behind its back.  Every work buffer (batch tally, batch sums,
+// problems, for callers that must not allocate device memory -- a host
+// application that hands the GPU's memory to its own allocator (a memory
+// pool sized at start-up, an embedded planning system with a fixed budget)
+// and forbids libraries from calling cudaMalloc behind its back.  The call
+// synchronizes its stream and copies through host memory, so it is an
+// ordinary blocking call.  Every work buffer (batch tally, batch sums,
 // particle queues, counters, source arrays, majorant) is carved from one
 // fixed-size array in device memory that exists for as long as the library
 // is loaded; the caller passes the phantom, tables and output arrays.
@@ -208,7 +209,14 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     GDPM_CUDA_TRY(cudaMemcpyAsync(prefix_d, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, s));
 
     // the array keeps the previous call's contents: clear what accumulates
-    GDPM_CUDA_TRY(cudaMemsetAsync(edep, 0, V * 8, s));
+    // FP32 pair mode keeps hi in the first V floats and lo from the next
+    // 256-byte boundary: the batch fold reads both halves as float2, so lo
+    // must stay 8-byte aligned when V is odd.  al(4V) + 4V <= 8 * kNaMaxVoxels
+    // for every V <= kNaMaxVoxels, so both halves fit the edep region.
+    const size_t lo_off = al(V * 4);
+    const size_t tally_bytes = ctx->tally_mode == 0 ? V * 8 : lo_off + V * 4;
+    if (tally_bytes > al(kNaMaxVoxels * 8)) return GDPM_E_ARG;
+    GDPM_CUDA_TRY(cudaMemsetAsync(edep, 0, tally_bytes, s));
     GDPM_CUDA_TRY(cudaMemsetAsync(s1, 0, V * 8, s));
     GDPM_CUDA_TRY(cudaMemsetAsync(s2, 0, V * 8, s));
     GDPM_CUDA_TRY(cudaMemsetAsync(counters, 0, C_NCOUNT * 8, s));
@@ -234,8 +242,9 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     P.tally_hi = V;
     P.n_records = 0;
     P.edep = edep;
-    P.edep_hi = reinterpret_cast<float*>(edep);            // FP32 pair mode: two V-float halves
-    P.edep_lo = reinterpret_cast<float*>(edep) + V;
+    P.edep_hi = reinterpret_cast<float*>(edep);            // FP32 pair mode: hi, then lo
+    P.edep_lo = reinterpret_cast<float*>(base + kOffEdep + lo_off);
+    if (reinterpret_cast<uintptr_t>(P.edep_lo) % 8 != 0) return GDPM_E_ARG;
     P.counters = counters;
     P.ledger = ledger;
     P.status = status;

@@ -11,8 +11,8 @@ namespace gdpm {
 namespace {
 
 // Largest density per material index (positive floats order like their bit
-// patterns, so an integer atomicMax on the bits is exact); counts voxels with
-// non-positive density.
+// patterns, so an integer atomicMax on the bits is exact); counts voxels whose
+// density is not a positive finite number (zero, negative, NaN or infinite).
 __global__ void k_rhomax(const uint8_t* __restrict__ mat, const float* __restrict__ rho, size_t V,
                          int* rmax_bits, unsigned int* n_bad) {
     __shared__ int s_max[256];
@@ -22,7 +22,7 @@ __global__ void k_rhomax(const uint8_t* __restrict__ mat, const float* __restric
     for (size_t v = blockIdx.x * size_t(blockDim.x) + threadIdx.x; v < V;
          v += size_t(gridDim.x) * blockDim.x) {
         const float r = rho[v];
-        if (!(r > 0.f)) { ++bad; continue; }
+        if (!(r > 0.f) || isinf(r)) { ++bad; continue; }
         atomicMax(&s_max[mat[v]], __float_as_int(r));
     }
     if (bad) atomicAdd(n_bad, bad);

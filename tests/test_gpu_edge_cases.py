@@ -96,3 +96,19 @@ def test_few_and_ragged_histories_per_batch(n, nb):
     prob = W.tiny_problem(n_histories=n, n_batches=nb)
     d_o, d_g, st, _ = same_seed(prob, min_identical=0.95)
     assert st["n_primary"] == n
+
+
+@pytest.mark.parametrize("bad", [0.0, -1.0, float("nan"), float("inf")])
+def test_phantom_rejects_densities_that_are_not_positive_and_finite(bad):
+    """A voxel of zero mass has no dose (its dose would be energy / 0), and a
+    negative, NaN or infinite density has no meaning: the phantom is refused."""
+    ph = W.homogeneous_phantom((8, 8, 8), (0.5, 0.5, 0.5), W.WATER, 1.0)
+    rho = ph.rho.copy()
+    rho[137] = bad
+    ctx = G.gdpm_context_create(0)
+    try:
+        with pytest.raises(G.GdpmError) as e:
+            G.gdpm_phantom_create(ctx, ph.shape, ph.voxel, ph.mat, rho)
+        assert e.value.code == G.GDPM_E_ARG
+    finally:
+        G.gdpm_context_destroy(ctx)

@@ -1,7 +1,8 @@
 """gdpm_simulate_noalloc: the dose calculation without any allocation.
 
-Some callers cannot call cudaMalloc -- code running while a CUDA graph is
-captured, or applications whose own allocator owns the GPU's memory -- so the
+Some callers cannot call cudaMalloc -- applications whose own allocator owns
+the GPU's memory (a pool sized at start-up, a planning system with a fixed
+memory budget) and that forbid libraries from allocating behind it -- so the
 library offers one entry point whose work buffers all live in a fixed static
 device array.  This file is named so that pytest collects it last.
 """
@@ -44,6 +45,38 @@ def test_noalloc_matches_simulate_on_two_calls():
                 assert st[k] == st_ref[k], k
             assert st["deposited"] == pytest.approx(st_ref["deposited"], rel=1e-12)
             assert st["sigma_over_dmax"] == pytest.approx(st_ref["sigma_over_dmax"], rel=1e-6)
+    finally:
+        eng.close()
+
+
+def test_noalloc_fp32_pair_tally_on_odd_grid():
+    """The compensated FP32 tally keeps two float halves in the scratch; on a
+    grid with an odd voxel count (31^3) the low half must still be read as
+    aligned float pairs.  Two calls in a row equal gdpm_simulate's result in
+    the same tally mode."""
+    base = W.tiny_problem(n_histories=40_000, n_batches=10)
+    ph = W.homogeneous_phantom((31, 31, 31), (0.5, 0.5, 0.5))
+    prob = base.with_(phantom=ph, source=W.pencil_source(ph, 1.0))
+    eng = G.Engine(prob, params={G.GDPM_PARAM_TALLY_MODE: 1})
+    try:
+        V = ph.n_voxels
+        assert V % 2 == 1
+        d_ref, s_ref, st_ref = eng.run()
+        d_ref = d_ref.cpu().numpy()
+        s_ref = s_ref.cpu().numpy()
+        for _ in range(2):
+            d = torch.full((V,), -1.0, dtype=torch.float64, device="cuda")
+            s = torch.full((V,), -1.0, dtype=torch.float64, device="cuda")
+            st = G.gdpm_simulate_noalloc(eng.ctx, eng.phantom, eng.tables, prob.n_histories,
+                                         prob.n_batches, d, s)
+            torch.cuda.synchronize()
+            np.testing.assert_allclose(d.cpu().numpy(), d_ref, rtol=1e-9,
+                                       atol=1e-12 * d_ref.max())
+            np.testing.assert_allclose(s.cpu().numpy(), s_ref, rtol=1e-6,
+                                       atol=1e-9 * s_ref.max())
+            for k in ("n_primary", "compton", "el_steps", "crossings"):
+                assert st[k] == st_ref[k], k
+            assert st["deposited"] == pytest.approx(st_ref["deposited"], rel=1e-9)
     finally:
         eng.close()
 
