@@ -341,6 +341,75 @@ def test_bethe_textbook_value():
     assert O.evaluate(p, 0, O.OF_SCOL, 1.0)[0] == pytest.approx(1.85, rel=0.03)
 
 
+# Tabulated collision stopping powers of liquid water (NIST ESTAR, I = 75 eV;
+# MeV cm2/g, four significant figures).  Sternheimer's density-effect
+# correction for water is zero below beta*gamma = 10^0.24 (T < 0.515 MeV), so at
+# these energies the tabulated value is the Bethe formula itself and the
+# oracle must reproduce it to the table's rounding (<= 2.5e-4).  Dropping the
+# F(tau) term moves it by 0.19, 0.71 and 1.3 % at 0.1, 0.2 and 0.5 MeV, and
+# flipping the sign of tau^2/8 by 0.12 and 0.33 % at 0.2 and 0.5 MeV (both
+# checked by hand on a copy of the formula).
+@pytest.mark.parametrize("T,tab", [(0.1, 4.115), (0.2, 2.793), (0.5, 2.034)])
+def test_bethe_below_density_effect_matches_tabulated_water(T, tab):
+    p = water_problem()
+    assert O.evaluate(p, 0, O.OF_SCOL, T)[0] == pytest.approx(tab, rel=4e-4)
+
+
+# Radiation lengths tabulated by the Particle Data Group (Tsai's complete-
+# screening form with the Coulomb correction), g/cm2.  The oracle's
+# bremsstrahlung constant B = 1/X0 is Rossi's older ln(183 Z^-1/3) reading,
+# 1.5-4 % longer than these; 5 % holds it while failing a Z^2 in place of
+# Z(Z+1) (+9..21 %), ln(183 Z^+1/3) (-17..-27 %), ln 183 alone (-8..-15 %) or
+# a dropped factor 4 (x4), each checked by hand.
+_CARBON = W.Material("graphite", 2.0, 78e-6, ((6, 12.011, 1.0),))
+_ALUMINIUM = W.Material("aluminium", 2.7, 166e-6, ((13, 26.9815, 1.0),))
+_X0_TABULATED = [(W.WATER, 36.08), (W.AIR, 36.62), (_CARBON, 42.70), (_ALUMINIUM, 24.01)]
+
+
+def _material_problem(mat):
+    ph = W.homogeneous_phantom((2, 2, 2), (1.0, 1.0, 1.0), mat, 1.0)
+    return water_problem(phantom=ph)
+
+
+@pytest.mark.parametrize("mat,x0", _X0_TABULATED, ids=[m.name for m, _ in _X0_TABULATED])
+def test_radiation_length_against_tabulated(mat, x0):
+    B = O.evaluate(_material_problem(mat), 0, O.OF_BCONST, 0.0)[0]
+    assert 1.0 / B == pytest.approx(x0, rel=0.05)
+
+
+def test_hard_bremsstrahlung_cross_section_from_radiation_length():
+    """Kramers' 1/k spectrum normalised by the radiation length: photons
+    above W_cb per unit mass path Sigma_b(T) = ln(T/W_cb)/X0, none at or
+    below W_cb.  With X0 the tabulated 36.08 g/cm2 (5 %, the Rossi reading's
+    spread), and the ln(T/W_cb) shape exact between energies."""
+    p = water_problem(eabs_photon=0.05)
+    wcb = p.eabs_photon
+    sig = {T: O.evaluate(p, 0, O.OF_SIG_BREMS, T)[0] for T in (0.04, 0.05, 1.0, 5.0, 20.0)}
+    assert sig[0.04] == 0.0 and sig[0.05] == 0.0
+    for T in (1.0, 5.0, 20.0):
+        assert sig[T] == pytest.approx(math.log(T / wcb) / 36.08, rel=0.05)
+    assert sig[20.0] / sig[1.0] == pytest.approx(math.log(20.0 / wcb) / math.log(1.0 / wcb), rel=1e-12)
+
+
+def test_radiative_loss_soft_plus_hard_is_T_over_X0():
+    """The radiation length is the mass path over which radiation takes the
+    fraction 1 - 1/e of a fast electron's energy: radiative loss per unit
+    mass path T/X0.  Split at W_cb into the soft part inside the restricted
+    stopping power, S_r - (S_col - hard Moller loss), and the hard part
+    Sigma_b(T) x E[k], with E[k] taken from the oracle's own 1/k sampler
+    (2e5 draws).  Against X0 = 36.08 g/cm2 within 5 %, at 2, 6 and 20 MeV."""
+    p = water_problem(eabs_photon=0.05, eabs_electron=0.2)
+    for j, T in enumerate((2.0, 6.0, 20.0)):
+        soft = (O.evaluate(p, 0, O.OF_SREST, T)[0] - O.evaluate(p, 0, O.OF_SCOL, T)[0]
+                + O.evaluate(p, 0, O.OF_LOSS_MOLLER, T)[0])
+        k, _ = O.sample(O.OS_BREMS, T, p.eabs_photon, 200_000, seed=31 + j)
+        hard = O.evaluate(p, 0, O.OF_SIG_BREMS, T)[0] * k.mean()
+        assert soft > 0 and hard > 0
+        assert soft + hard == pytest.approx(T / 36.08, rel=0.05)
+        # the soft share is the spectrum's part below W_cb: W_cb / T of the total
+        assert soft / (soft + hard) == pytest.approx(p.eabs_photon / T, rel=0.02)
+
+
 def _moller_closed(T, wcc, ne):
     """Analytic hard-Moller cross section and energy loss (antiderivatives
     of the Moller density in eps = W/T on [W_cc/T, 1/2])."""
