@@ -1,11 +1,16 @@
 #!/usr/bin/env python
 """Throughput benchmark of the GB300 gDPM engine.
 
-Workload (default): the 128^3 water/lung/bone/water slab phantom at 0.25 cm,
-6 MV-like photon beam (Kramers thick-target spectrum, 24 equal intervals),
-10x10 cm field at SSD 100 cm, cutoffs 50 keV / 200 keV, 1e8 histories in
+Workload (default, ``ct256_imrt7``): the 256x256x128 patient-like CT phantom
+at 0.25 cm (seeded ellipsoids: body, lungs, spine and ribs, an air cavity)
+under a 7-beam coplanar IMRT plan, each beam a 20x20 fluence map of 1 cm
+beamlets with seeded intensities, 6 MV-like spectrum (Kramers thick target,
+24 equal intervals), SAD 100 cm, cutoffs 50 keV / 200 keV, 1e8 histories in
 100 batches, FP32 transport with FP64 tallies.  One step = one full dose
-calculation of that workload (all batches, statistics and sigma/Dmax).
+calculation of that workload (all batches, statistics and sigma/Dmax); the
+line also carries the time to sigma/Dmax = 1 % measured by running to it.
+``--workload slab128_6MV`` is the 128^3 water/lung/bone/water slab with a
+10x10 cm field at SSD 100 cm.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
 Under torchrun each rank runs the same workload with its own Philox key
@@ -59,10 +64,18 @@ for _k in DEFAULT_SIZE:
     PHANTOM_DESC[_k] = "61x61x150 slab @0.5x0.5x0.2cm (Sec. 3.1), %s middle" % _k.rsplit("_", 1)[1]
 PHANTOM_DESC["water64_e15"] = PHANTOM_DESC["water64_g15"] = "64^3 water @0.5cm (Sec. 4)"
 
-# Algorithmic ALU operations per unit of work (FP32 arithmetic, integer
-# arithmetic of the Philox rounds and index math, and special-function calls,
-# one each; counted from the algorithm's steps).  Units come from the
-# engine's own event counters.
+# Nominal algorithmic FP32 work per unit of the method's steps: a Woodcock
+# flight about 30 operations, a Klein-Nishina interaction about 60, an
+# electron condensed-history step about 100 (its voxel crossings, range
+# inverse and angular deflection included).  The roofline fraction `frac` is
+# taken with these; units come from the engine's own event counters.
+NOMINAL_OPS = {"ph_flights": 30, "compton": 60, "el_steps": 100}
+
+# Detailed count of the same steps as this engine executes them (FP32
+# arithmetic, integer arithmetic of the Philox rounds and index math, and
+# special-function calls, one each), reported beside `frac` as
+# `frac_detailed`: it adds the random-number generation (Philox4x32-10 per
+# four uniforms) and prices voxel crossings and hard events separately.
 OPS_PER_DRAW = 72          # Philox4x32-10 (10 rounds x 6 ops) + 4 uniform conversions x 3
 OPS = {
     "ph_flights": 32 + OPS_PER_DRAW + 10,     # Woodcock flight: lerps, log, move, voxel, test
@@ -76,32 +89,37 @@ LANES_PER_SM = 128
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-# DRAM bytes (read + write) of the phase kernels in one step of slab128_6MV
-# at 1e8 histories and 100 batches, from one ncu capture of that step
-# (profiles/dram_k_phase_slab128_6MV_1e8hist.md).  They hold while the
-# kernel sources hash to TRAFFIC_SOURCES_SHA1; otherwise traffic is null.
+# DRAM bytes (read + write) per source history of the phase kernels, from
+# one ncu capture per workload (dram__bytes_read.sum + dram__bytes_write.sum
+# over every launch of the kernel in one calculation, divided by its
+# histories; profiles/ holds the summaries).  A capture may be of a smaller
+# history count than the bench step: the per-launch figure is then the
+# per-history bytes times the step's histories over the step's launches of
+# that kernel.  They hold while the kernel sources hash to `sha1`; otherwise
+# traffic is null.
 TRAFFIC_SOURCES = ("transport.cu", "common.cuh", "internal.h")
-TRAFFIC_SOURCES_SHA1 = "f95a93d52e589eb14878327c497c6c2e9adeefe7"
-TRAFFIC = {"workload": "slab128_6MV", "histories": 100_000_000, "batches": 100,
-           "photon phase": (7, 1.798e10), "electron phase": (7, 1.015e10)}   # (launches, bytes)
+TRAFFIC = {}
 
 
-def measured_traffic(args, kernel):
-    """Average DRAM bytes per launch of the named kernel from the ncu
-    capture, or None when this run is not the captured configuration or the
-    kernels changed."""
+def sources_sha1():
     import hashlib
-    run = (args.workload, int(args.histories), args.batches, args.tally)
-    if run != (TRAFFIC["workload"], TRAFFIC["histories"], TRAFFIC["batches"], "fp64") or kernel not in TRAFFIC:
-        return None
     h = hashlib.sha1()
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(HERE, "paper_1107_3355_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != TRAFFIC_SOURCES_SHA1:
+    return h.hexdigest()
+
+
+def measured_traffic(args, kernel, launches_per_step):
+    """DRAM bytes per launch of the named kernel, scaled from the workload's
+    ncu capture, or None when there is none for this workload and tally
+    mode, or the kernels changed since."""
+    cap = TRAFFIC.get(args.workload)
+    if not cap or args.tally != cap["tally"] or kernel not in cap["bytes_per_history"]:
         return None
-    launches, nbytes = TRAFFIC[kernel]
-    return nbytes / launches
+    if sources_sha1() != cap["sha1"] or launches_per_step <= 0:
+        return None
+    return cap["bytes_per_history"][kernel] * float(args.histories) / launches_per_step
 
 
 def parse():
@@ -110,7 +128,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gdpm", choices=["gdpm", "reference"])
-    ap.add_argument("--workload", default="slab128_6MV", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="ct256_imrt7", choices=sorted(WORKLOADS))
     ap.add_argument("--histories", type=float, default=None,
                     help="histories per step (default 1e8; the paper's count for its cases)")
     ap.add_argument("--batches", type=int, default=None,
@@ -662,12 +680,15 @@ def main():
     kms = agg.get("kernel_ms", [0, 0, 0, 0])
     dom = max(range(3), key=lambda i: kms[i])
     if dom == 0:
-        ops = agg["ph_flights"] * OPS["ph_flights"] + agg["compton"] * OPS["compton"]
+        ops = agg["ph_flights"] * NOMINAL_OPS["ph_flights"] + agg["compton"] * NOMINAL_OPS["compton"]
+        ops_detailed = agg["ph_flights"] * OPS["ph_flights"] + agg["compton"] * OPS["compton"]
     else:
-        ops = (agg["el_steps"] * OPS["el_steps"] + agg["crossings"] * OPS["crossings"] +
-               agg["moller"] * OPS["moller"] + agg["brems"] * OPS["brems"])
+        ops = agg["el_steps"] * NOMINAL_OPS["el_steps"]
+        ops_detailed = (agg["el_steps"] * OPS["el_steps"] + agg["crossings"] * OPS["crossings"] +
+                        agg["moller"] * OPS["moller"] + agg["brems"] * OPS["brems"])
     launches_dom = max(1, agg.get("kernel_launches", [1, 1, 1, 1])[dom])
     achieved = ops / (kms[dom] / 1e3) / 1e12
+    achieved_detailed = ops_detailed / (kms[dom] / 1e3) / 1e12
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peak = props.multi_processor_count * LANES_PER_SM * sm_mhz * 1e6 / 1e12
@@ -711,9 +732,20 @@ def main():
             "gpu_launches": int(agg.get("launches", 0)),
             "roofline": {"bound": "alu", "kernel": kinds[dom], "achieved": achieved,
                          "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                         "traffic": measured_traffic(args, kinds[dom]),
-                         "traffic_unit": "DRAM bytes per launch (ncu)",
-                         "note": "ALU lane-operations/s vs SMs x 128 lanes x sampled SM clock"},
+                         "traffic": measured_traffic(args, kinds[dom], launches_dom / args.steps),
+                         "traffic_unit": "DRAM bytes per launch (ncu, scaled per history)",
+                         "launches_per_step": launches_dom / args.steps,
+                         "ops_per_unit": {k: NOMINAL_OPS[k] for k in
+                                          (("ph_flights", "compton") if dom == 0 else ("el_steps",))},
+                         "achieved_detailed": achieved_detailed,
+                         "frac_detailed": achieved_detailed / peak,
+                         "ops_per_unit_detailed": ({k: OPS[k] for k in ("ph_flights", "compton")}
+                                                   if dom == 0 else
+                                                   {k: OPS[k] for k in ("el_steps", "crossings",
+                                                                        "moller", "brems")}),
+                         "note": "ALU lane-operations/s vs SMs x 128 lanes x sampled SM clock; "
+                                 "achieved = events x ops_per_unit / the kernel's summed event "
+                                 "time (kernel_ms_per_step x steps)"},
             "resources": resources,
             "kernel_ms_per_step": [k / args.steps for k in kms],
             "events_per_history": {k: agg[k] / (args.steps * n_hist) for k in

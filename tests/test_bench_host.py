@@ -22,7 +22,7 @@ def parse(*argv):
 
 def test_workload_defaults():
     a = parse()
-    assert (a.workload, a.histories, a.batches, a.steps, a.warmup) == ("slab128_6MV", 1e8, 100, 10, 3)
+    assert (a.workload, a.histories, a.batches, a.steps, a.warmup) == ("ct256_imrt7", 1e8, 100, 10, 3)
     a = parse("--workload", "paper_slab_6MV_lung")
     assert (a.histories, a.batches) == (2.5e8, 10)
     a = parse("--workload", "water64_e15", "--histories", "2e5")
@@ -44,13 +44,32 @@ def test_published_rates_come_from_the_paper():
         assert bench.DEFAULT_SIZE[name][0] == n            # the paper's history count
 
 
-def test_traffic_is_reported_only_for_the_captured_configuration():
-    ns = argparse.Namespace(workload="slab128_6MV", histories=1e8, batches=100, tally="fp64")
-    got = bench.measured_traffic(ns, "electron phase")
-    assert got == pytest.approx(bench.TRAFFIC["electron phase"][1] / bench.TRAFFIC["electron phase"][0])
-    for change in (dict(histories=1e7), dict(batches=10), dict(tally="fp32pair"), dict(workload="ct256_imrt7")):
-        assert bench.measured_traffic(argparse.Namespace(**{**vars(ns), **change}), "electron phase") is None
-    assert bench.measured_traffic(ns, "batch fold") is None
+def test_traffic_is_scaled_per_history_and_gated_on_the_sources(monkeypatch):
+    """The ncu bytes per history of a capture, times the step's histories,
+    over the step's launches of that kernel; None for another workload, tally
+    mode or kernel, or once the kernel sources no longer hash to the
+    capture's value."""
+    cap = {"tally": "fp64", "sha1": bench.sources_sha1(),
+           "bytes_per_history": {"electron phase": 120.0, "photon phase": 180.0}}
+    monkeypatch.setitem(bench.TRAFFIC, "ct256_imrt7", cap)
+    ns = argparse.Namespace(workload="ct256_imrt7", histories=1e8, batches=100, tally="fp64")
+    assert bench.measured_traffic(ns, "electron phase", 8.0) == pytest.approx(120.0 * 1e8 / 8.0)
+    assert bench.measured_traffic(argparse.Namespace(**{**vars(ns), "histories": 1e7}),
+                                  "photon phase", 2.0) == pytest.approx(180.0 * 1e7 / 2.0)
+    for change in (dict(tally="fp32pair"), dict(workload="slab128_e20MeV")):
+        assert bench.measured_traffic(argparse.Namespace(**{**vars(ns), **change}), "electron phase", 8.0) is None
+    assert bench.measured_traffic(ns, "batch fold", 1.0) is None
+    monkeypatch.setitem(bench.TRAFFIC, "ct256_imrt7", dict(cap, sha1="0" * 40))
+    assert bench.measured_traffic(ns, "electron phase", 8.0) is None
+
+
+def test_nominal_and_detailed_op_counts():
+    """frac takes the nominal per-unit work of the method's steps (30 per
+    Woodcock flight, 60 per Klein-Nishina interaction, 100 per electron
+    step); the detailed counts only add work (random numbers, crossings)."""
+    assert bench.NOMINAL_OPS == {"ph_flights": 30, "compton": 60, "el_steps": 100}
+    for k, v in bench.NOMINAL_OPS.items():
+        assert bench.OPS[k] >= v
 
 
 def test_clock_sampler_reads_nvidia_smi_timestamps():
