@@ -16,6 +16,22 @@ def _shard(args):
     return n, d, s
 
 
+def _shard_dose(args):
+    prob, n, rid = args
+    from oracle import oracle as O
+    d, _, led = O.run(prob.with_(n_histories=n, request_id=rid))
+    return n, d, led
+
+
+def run_shards(prob, n_total, procs=None, first_request_id=1000):
+    """The shards themselves: a list of (histories, dose, ledger), one per
+    process, each an independent estimate of the dose (use them as batches)."""
+    procs = procs or min(16, os.cpu_count() or 1)
+    n = [n_total // procs + (1 if k < n_total % procs else 0) for k in range(procs)]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_shard_dose, [(prob, n[k], first_request_id + k) for k in range(procs)])
+
+
 def run_sharded(prob, n_total, procs=None, first_request_id=1000):
     procs = procs or min(16, os.cpu_count() or 1)
     n = [n_total // procs + (1 if k < n_total % procs else 0) for k in range(procs)]

@@ -26,6 +26,22 @@ def t_test(d1, s1, d2, s2, high_frac=0.1, threshold=2.0):
                 n_high=int(high.sum()))
 
 
+# Gate 1 of the dose comparison: the signed bias |sum dD| / sum D over the
+# voxels above 10 % of Dmax stays within 0.5 %.
+BIAS_GATE = 0.005
+
+
+def signed_bias(d_ref, d, high_frac=0.1):
+    """sum(d_ref - d) / sum(d_ref) over voxels with d_ref > high_frac * Dmax
+    (0 when no voxel holds dose)."""
+    d_ref = np.asarray(d_ref, np.float64); d = np.asarray(d, np.float64)
+    dmax = max(float(d_ref.max()), float(d.max()))
+    if dmax <= 0:
+        return 0.0
+    high = d_ref > high_frac * dmax
+    return float((d_ref - d)[high].sum() / d_ref[high].sum())
+
+
 def chi2_pvalue(observed, expected, ddof=0):
     from scipy import stats
     observed = np.asarray(observed, np.float64); expected = np.asarray(expected, np.float64)

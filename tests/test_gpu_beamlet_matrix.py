@@ -12,7 +12,7 @@ import pytest
 from oracle import oracle as O
 from paper_1107_3355_gb300 import gdpm as G
 from paper_1107_3355_gb300 import workloads as W
-from tests._stats import t_test
+from tests._stats import BIAS_GATE, t_test
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,6 +47,7 @@ def test_dose_matrix_matches_oracle_per_beamlet():
         r = t_test(d_o, s_o, dose[k], sigma[k], high_frac=0.1)
         print("beamlet", k, sub.n_histories, r)
         assert r["P_high"] >= 0.95, (k, r)
+        assert abs(r["bias"]) <= BIAS_GATE, (k, r)
     same = np.all(np.concatenate(recs) == rec, axis=1)
     print("dose matrix identical records: %.5f" % same.mean())
     assert same.mean() > 0.999

@@ -1,0 +1,116 @@
+"""Dose parity gate 2 on the 128^3 slab: binned central-axis depth dose and
+lateral profiles, GPU against the oracle on independent random streams.
+
+Sec. 3.1 compares depth-dose curves and lateral profiles of the two codes.
+A mean |dD|/D over single voxels measures mostly noise (about 1.1 times the
+combined relative sigma), so the dose is binned until each bin's relative
+sigma is a few tenths of a percent, and then the curves must agree to 0.5 %
+on average over the bins above 10 % of the curve's maximum, with a signed
+bias within 0.5 % (gate 1 on the binned curve).
+
+Bins (0.25 cm voxels): the depth dose averages a central column (6 x 6 cm
+for 6 MV, 4 x 4 cm for 20 MeV electrons) over 1 cm (6 MV) or 0.5 cm (20 MeV)
+of depth; each lateral profile averages 1 cm in x over a central band in y
+and a band of depth.  The oracle runs as one single-thread process per host
+core on its own random stream; each process is one batch of the binned
+estimate.  The GPU runs ten times the histories, split into 16 runs on their
+own streams, so its sigma adds about 5 % to the oracle's.  With the oracle's
+mean per-bin sigma at <= 0.3 %, pure noise gives a mean |dD|/D of about
+1.18 x 0.3 % = 0.35 %.
+"""
+import numpy as np
+import pytest
+
+from paper_1107_3355_gb300 import gdpm as G
+from paper_1107_3355_gb300 import workloads as W
+from tests._oracle_parallel import run_shards
+from tests._stats import BIAS_GATE
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N = 128                    # voxels per axis; 0.25 cm voxels
+
+
+def _band(c0_cm, c1_cm):
+    return slice(int(round(c0_cm / 0.25)), int(round(c1_cm / 0.25)))
+
+
+CASES = {
+    # depth: column half width (cm), depth bin (voxels); lateral: (z band, y half width)
+    "6MV": dict(make=lambda n, nb: W.slab_photon_problem(n_histories=n, n_batches=nb),
+                n_oracle=12_000_000, half=3.0, dz_bin=4,
+                lateral=[((1.0, 3.0), 4.0), ((14.0, 18.0), 4.0)]),
+    "e20": dict(make=lambda n, nb: W.slab_electron_problem(n_histories=n, n_batches=nb),
+                n_oracle=600_000, half=2.0, dz_bin=2,
+                lateral=[((1.0, 3.0), 3.0), ((5.0, 9.0), 3.0)]),
+}
+
+
+def binned_curves(d, case):
+    """Mean dose of each bin: the central-axis depth dose and the lateral
+    profiles (x in 1 cm bins) of the case.  d: flat x-fastest grid."""
+    g = np.asarray(d, np.float64).reshape(N, N, N)           # [z, y, x]
+    cfg = CASES[case]
+    col = _band(16.0 - cfg["half"], 16.0 + cfg["half"])
+    depth = g[:, col, col].mean(axis=(1, 2))
+    out = {"depth": depth.reshape(-1, cfg["dz_bin"]).mean(axis=1)}
+    for (z0, z1), hy in cfg["lateral"]:
+        sub = g[_band(z0, z1), _band(16.0 - hy, 16.0 + hy), :]
+        out["x@z%.0f-%.0f" % (z0, z1)] = sub.mean(axis=(0, 1)).reshape(-1, 4).mean(axis=1)
+    return out
+
+
+def mean_and_sigma(estimates):
+    """Mean of equal-weight independent estimates and its standard error."""
+    keys = estimates[0].keys()
+    a = {k: np.stack([e[k] for e in estimates]) for k in keys}
+    return ({k: v.mean(axis=0) for k, v in a.items()},
+            {k: v.std(axis=0, ddof=1) / np.sqrt(v.shape[0]) for k, v in a.items()})
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_binned_depth_dose_and_profiles_agree(case):
+    cfg = CASES[case]
+    orc = cfg["make"](cfg["n_oracle"], 10).with_(seed=101)
+    shards = run_shards(orc, cfg["n_oracle"])
+    n_sh = [n for n, _, _ in shards]
+    assert max(n_sh) - min(n_sh) <= 1
+    mo, so = mean_and_sigma([binned_curves(d, case) for _, d, _ in shards])
+
+    runs = 16
+    n_gpu = 10 * cfg["n_oracle"] // runs
+    gpu = cfg["make"](n_gpu, 10).with_(seed=202)
+    eng = G.Engine(gpu)
+    est = []
+    try:
+        dose = torch.empty(gpu.phantom.n_voxels, dtype=torch.float64, device="cuda")
+        for rid in range(runs):
+            G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_REQUEST_ID, rid + 1)
+            G.gdpm_simulate(eng.ctx, eng.phantom, eng.tables, n_gpu, 10, dose, None)
+            est.append(binned_curves(dose.cpu().numpy(), case))
+    finally:
+        eng.close()
+    mg, sg = mean_and_sigma(est)
+
+    all_t, all_rel = [], []
+    for k in mo:
+        sel = mo[k] > 0.1 * mo[k].max()
+        srel = so[k][sel] / mo[k][sel]
+        rel = np.abs(mo[k] - mg[k])[sel] / mo[k][sel]
+        bias = float((mo[k] - mg[k])[sel].sum() / mo[k][sel].sum())
+        t = (mo[k] - mg[k])[sel] / np.sqrt(so[k][sel] ** 2 + sg[k][sel] ** 2)
+        print("%s %-9s bins %3d  oracle sigma_rel mean %.4f%% max %.4f%%  mean|dD|/D %.4f%%  "
+              "max %.4f%%  bias %+.4f%%  |t|<=2 %.3f"
+              % (case, k, sel.sum(), 100 * srel.mean(), 100 * srel.max(), 100 * rel.mean(),
+                 100 * rel.max(), 100 * bias, np.mean(np.abs(t) <= 2)))
+        assert sel.sum() >= 8, k
+        assert srel.mean() <= 0.003, (k, srel.mean())         # the precision the gate needs
+        assert rel.mean() <= 0.005, (k, rel.mean())           # gate 2
+        assert abs(bias) <= BIAS_GATE, (k, bias)              # gate 1 on the binned curve
+        all_t.append(t)
+        all_rel.append(rel)
+    every = np.concatenate(all_t)
+    # with 15 degrees of freedom per sigma, P(|t| <= 2) is about 0.94
+    assert np.mean(np.abs(every) <= 2.0) >= 0.85, np.mean(np.abs(every) <= 2.0)
+    assert np.concatenate(all_rel).mean() <= 0.005

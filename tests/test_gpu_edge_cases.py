@@ -13,6 +13,7 @@ import pytest
 from oracle import oracle as O
 from paper_1107_3355_gb300 import gdpm as G
 from paper_1107_3355_gb300 import workloads as W
+from tests._stats import BIAS_GATE, signed_bias
 from tests.test_gpu_parity import check_ledger, run_gpu
 
 torch = pytest.importorskip("torch")
@@ -31,6 +32,7 @@ def same_seed(prob, min_identical=0.99):
     same = np.all(rec_o == rec_g, axis=1).mean()
     assert same >= min_identical, same
     assert st["source_energy"] == pytest.approx(led_o["source_energy"], rel=1e-6)
+    assert abs(signed_bias(d_o, d_g)) <= BIAS_GATE
     return d_o, d_g, st, led_o
 
 

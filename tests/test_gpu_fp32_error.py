@@ -1,0 +1,110 @@
+"""FP32 transport against the FP64 oracle on the same histories.
+
+The CUDA path transports in FP32 and tallies in FP64; the oracle does
+everything in FP64.  With the shared random-number protocol a history takes
+the same events on both sides unless an FP32 rounding flips a branch.  This
+measures what FP32 costs on histories that did NOT flip: the calculation is
+split into chunks of a few histories (a beamlet dose matrix whose rows are
+all the same field, so chunk k holds history ids k*n .. k*n+n-1 and is its
+own calculation, Sec. 2.3.1 beamlets); a chunk counts when every one of its
+histories has the same event record on both sides; over those chunks the
+summed doses are compared voxel by voxel, and each history's escaped energy
+and electron mass path one by one.
+"""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+from paper_1107_3355_gb300 import gdpm as G
+from paper_1107_3355_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def chunk_problem(case):
+    """(problem, chunk size) of a case: one beamlet row repeated K times, each
+    row a 10 x 10 cm field from a point source 100 cm above the z = 0 face."""
+    if case == "6MV":
+        ph = W.slab_phantom((64, 64, 128), (0.25, 0.25, 0.25))
+        spec, particle, K, n, e_max = W.kramers_spectrum(), W.PHOTON, 100, 200, 6.5
+    else:
+        ph = W.slab_phantom((48, 48, 96), (0.25, 0.25, 0.25))
+        spec, particle, K, n, e_max = W.mono_spectrum(20.0), W.ELECTRON, 400, 5, 21.0
+    X, Y, _ = ph.extent
+    fr = W.BeamFrame((X / 2, Y / 2, -100.0), (X / 2, Y / 2, 0.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.0))
+    rows = [W.beamlet_row(fr, -5.0, 5.0, -5.0, 5.0, 1.0)] * K
+    prob = W.Problem(ph, W.beamlet_source(rows, spec, particle), K * n, 2, eabs_photon=0.05,
+                     eabs_electron=0.2, e_min=0.005, e_max=e_max, sub_histories=(n,) * K)
+    return prob, n
+
+
+def _oracle_chunks(args):
+    """Oracle runs of chunks ks; a chunk whose records all equal the GPU's
+    adds n * dose into the sum.  Returns (sum, identical chunk ids, per-history
+    [escaped, mass path] of the identical chunks' histories)."""
+    case, ks, gpu_rec = args
+    from oracle import oracle as O
+    prob, n = chunk_problem(case)
+    acc = np.zeros(prob.phantom.n_voxels)
+    same, recd_all = [], []
+    for k, rg in zip(ks, gpu_rec):
+        d, _, _, rec, recd = O.run(prob.sub_problem(k), per_history=True)
+        if np.array_equal(rec, rg):
+            acc += n * d
+            same.append(k)
+            recd_all.append(recd)
+    return acc, same, (np.concatenate(recd_all) if recd_all else np.zeros((0, 2)))
+
+
+@pytest.mark.parametrize("case", ["6MV", "e20"])
+def test_fp32_dose_error_on_identical_histories(case):
+    prob, n = chunk_problem(case)
+    K, V, total = len(prob.sub_histories), prob.phantom.n_voxels, prob.n_histories
+    eng = G.Engine(prob)
+    try:
+        rec = torch.zeros(total * 4, dtype=torch.int32, device="cuda")
+        recd = torch.zeros(total * 2, dtype=torch.float64, device="cuda")
+        G.gdpm_set_history_records(eng.ctx, rec, recd, total)
+        dose, _, st = eng.run_beamlets(with_sigma=False)
+        rec = rec.cpu().numpy().reshape(K, n, 4)
+        recd = recd.cpu().numpy().reshape(K, n, 2)
+        procs = min(16, os.cpu_count() or 1)
+        groups = [list(range(K))[g::procs] for g in range(procs)]
+        with mp.get_context("spawn").Pool(procs) as pool:
+            parts = pool.map(_oracle_chunks, [(case, ks, [rec[k] for k in ks]) for ks in groups])
+        d_o = sum(p[0] for p in parts)
+        same = sorted(k for p in parts for k in p[1])
+        recd_o = np.concatenate([p[2] for p in parts])
+        order = np.argsort(np.concatenate([np.asarray(p[1], np.int64) for p in parts]), kind="stable")
+        idx = torch.tensor(same, dtype=torch.int64, device="cuda")
+        d_g = (dose.index_select(0, idx).sum(dim=0) * n).cpu().numpy()
+    finally:
+        eng.close()
+    frac = len(same) / K
+    # the oracle's per-history values, in the order of the sorted chunk ids
+    recd_o = recd_o.reshape(-1, n, 2)[order].reshape(-1, 2)
+    recd_g = recd[same].reshape(-1, 2)
+    high = d_o > 0.1 * d_o.max()
+    rel = np.abs(d_g - d_o)[high] / d_o[high]
+    dep_rel = abs(d_g.sum() - d_o.sum()) / d_o.sum()
+    esc = recd_o[:, 0] > 0
+    esc_rel = np.abs(recd_g[esc, 0] - recd_o[esc, 0]) / recd_o[esc, 0]
+    mp_ = recd_o[:, 1] > 0
+    path_rel = np.abs(recd_g[mp_, 1] - recd_o[mp_, 1]) / recd_o[mp_, 1]
+    print("%s: %d of %d chunks identical (%.3f), %d histories; dose over D > 10%% Dmax (%d voxels): "
+          "mean |dD|/D %.2e, max %.2e; all voxels' summed energy %.2e; per history: escaped "
+          "energy mean %.2e max %.2e (%d), electron mass path mean %.2e max %.2e (%d)"
+          % (case, len(same), K, frac, len(same) * n, high.sum(), rel.mean(), rel.max(), dep_rel,
+             esc_rel.mean() if esc.any() else 0, esc_rel.max() if esc.any() else 0, esc.sum(),
+             path_rel.mean(), path_rel.max(), mp_.sum()))
+    assert frac >= 0.8
+    assert high.sum() >= 100
+    # FP32 positions, directions and energies against FP64: rounding-level on
+    # average; a deposit split at a voxel face can move between neighbours
+    assert rel.mean() <= 1e-4
+    assert rel.max() <= 1e-2
+    assert dep_rel <= 1e-5
+    assert path_rel.mean() <= 1e-4

@@ -13,7 +13,7 @@ import pytest
 
 from paper_1107_3355_gb300 import gdpm as G
 from paper_1107_3355_gb300 import workloads as W
-from tests._stats import t_test
+from tests._stats import BIAS_GATE, t_test
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -54,6 +54,7 @@ def test_graph_loop_matches_host_loop(case):
     assert same > 0.999
     r = t_test(d_h, s_h, d_g, s_g, high_frac=0.1)
     assert r["P_high"] >= 0.99, r
+    assert abs(r["bias"]) <= BIAS_GATE, r
     assert st_g["n_primary"] == prob.n_histories
     bal = st_g["deposited"] + st_g["escaped"] + st_g["discarded"]
     assert bal == pytest.approx(st_g["source_energy"], rel=1e-5)

@@ -16,7 +16,7 @@ import pytest
 from oracle import oracle as O
 from paper_1107_3355_gb300 import gdpm as G
 from paper_1107_3355_gb300 import workloads as W
-from tests._stats import t_test
+from tests._stats import BIAS_GATE, t_test
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -226,7 +226,7 @@ def test_tiny_pencil_same_seed_elementwise():
     r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
     print("same-seed t-test", r)
     assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97
-    assert abs(r["bias"]) < 0.005
+    assert abs(r["bias"]) <= BIAS_GATE
     for k in ["compton", "photoelectric", "el_steps", "moller", "brems"]:
         assert st[k] == pytest.approx(led_o[k], rel=0.02, abs=30), k
 
@@ -246,6 +246,7 @@ def test_tiny_pencil_independent_seeds():
     high = d_o > 0.1 * max(d_o.max(), d_g.max())
     se = math.sqrt(np.sum(s_o[high] ** 2 + s_g[high] ** 2)) / np.sum(d_o[high])
     assert abs(r["bias"]) <= max(4 * se, 1e-3)
+    assert 4 * se < BIAS_GATE and abs(r["bias"]) <= BIAS_GATE
 
 
 def test_slab_photon_same_seed():
@@ -259,6 +260,7 @@ def test_slab_photon_same_seed():
     r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
     print("slab photon t-test", r)
     assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97
+    assert abs(r["bias"]) <= BIAS_GATE
 
 
 def test_slab_electron_same_seed():
@@ -272,6 +274,7 @@ def test_slab_electron_same_seed():
     r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
     print("slab electron t-test", r)
     assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97
+    assert abs(r["bias"]) <= BIAS_GATE
 
 
 def test_random_hinge_depth_moment_closed_form():
@@ -462,6 +465,7 @@ def test_ct_imrt_beamlets_same_seed(sampler):
     r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
     print("ct imrt t-test", r)
     assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97
+    assert abs(r["bias"]) <= BIAS_GATE
 
 
 # --------------------------------------------------------------------- physics variants
@@ -481,6 +485,7 @@ def test_sauter_variant_same_seed():
     assert same.mean() > 0.99
     r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
     assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97, r
+    assert abs(r["bias"]) <= BIAS_GATE, r
 
 
 def test_icru_lung_slab_same_seed():
@@ -497,3 +502,4 @@ def test_icru_lung_slab_same_seed():
     assert same.mean() > 0.99
     r = t_test(d_o, s_o, d_g, s_g, high_frac=0.1)
     assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97, r
+    assert abs(r["bias"]) <= BIAS_GATE, r
