@@ -10,12 +10,20 @@ def sigma_over_dmax(dose, sigma, frac=0.5):
     return float(np.mean(sigma[sel]) / dmax)
 
 
-def t_test(d1, s1, d2, s2, high_frac=0.1, threshold=2.0):
+def t_test(d1, s1, d2, s2, high_frac=0.1, threshold=2.0, mask=None):
     """Per-voxel two-sample test t = (D1-D2)/sqrt(s1^2+s2^2) (Sec. 3.1).
     Returns dict(P_high, P_all, bias, mean_abs_rel).  P_high is over voxels
-    with D1 > high_frac*Dmax; zero-variance voxels pass iff D1 == D2."""
+    with D1 > high_frac*Dmax; zero-variance voxels pass iff D1 == D2.  With
+    `mask` (booleans per voxel) only those voxels count, Dmax included: in a
+    phantom with air, tissue-like voxels (density >= 0.05 g/cm3), as for the
+    Sec. 3.1 metric, since an air voxel's tiny mass turns one deposit into a
+    huge dose."""
     d1 = np.asarray(d1, np.float64); d2 = np.asarray(d2, np.float64)
-    s = np.sqrt(np.asarray(s1, np.float64) ** 2 + np.asarray(s2, np.float64) ** 2)
+    s1 = np.asarray(s1, np.float64); s2 = np.asarray(s2, np.float64)
+    if mask is not None:
+        mask = np.asarray(mask, bool)
+        d1, d2, s1, s2 = d1[mask], d2[mask], s1[mask], s2[mask]
+    s = np.sqrt(s1 ** 2 + s2 ** 2)
     diff = d1 - d2
     ok = np.where(s > 0, np.abs(diff) <= threshold * s, diff == 0)
     dmax = max(float(d1.max()), float(d2.max()))

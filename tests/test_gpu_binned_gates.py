@@ -8,12 +8,12 @@ sigma is a few tenths of a percent, and then the curves must agree to 0.5 %
 on average over the bins above 10 % of the curve's maximum, with a signed
 bias within 0.5 % (gate 1 on the binned curve).
 
-Bins (0.25 cm voxels): the depth dose averages a central column (6 x 6 cm
-for 6 MV, 4 x 4 cm for 20 MeV electrons) over 1 cm (6 MV) or 0.5 cm (20 MeV)
-of depth; each lateral profile averages 1 cm in x over a central band in y
-and a band of depth.  The oracle runs as one single-thread process per host
-core on its own random stream; each process is one batch of the binned
-estimate.  The GPU runs ten times the histories, split into 16 runs on their
+Bins (0.25 cm voxels): the depth dose averages a central column (8 x 8 cm
+for 6 MV, 6 x 6 cm for 20 MeV electrons) over 1 cm (6 MV) or 0.5 cm (20 MeV)
+of depth; each lateral profile averages 2 cm in x over a central band in y
+(10 or 8 cm) and a band of depth.  The oracle runs as one single-thread
+process per host core on its own random stream; each process is one batch
+of the binned estimate.  The GPU runs ten times the histories, split into 16 runs on their
 own streams, so its sigma adds about 5 % to the oracle's.  With the oracle's
 mean per-bin sigma at <= 0.3 %, pure noise gives a mean |dD|/D of about
 1.18 x 0.3 % = 0.35 %.
@@ -39,17 +39,18 @@ def _band(c0_cm, c1_cm):
 CASES = {
     # depth: column half width (cm), depth bin (voxels); lateral: (z band, y half width)
     "6MV": dict(make=lambda n, nb: W.slab_photon_problem(n_histories=n, n_batches=nb),
-                n_oracle=12_000_000, half=3.0, dz_bin=4,
-                lateral=[((1.0, 3.0), 4.0), ((14.0, 18.0), 4.0)]),
+                n_oracle=20_000_000, half=4.0, dz_bin=4,
+                lateral=[((0.5, 3.0), 5.0), ((14.0, 18.0), 5.0)]),
     "e20": dict(make=lambda n, nb: W.slab_electron_problem(n_histories=n, n_batches=nb),
-                n_oracle=600_000, half=2.0, dz_bin=2,
-                lateral=[((1.0, 3.0), 3.0), ((5.0, 9.0), 3.0)]),
+                n_oracle=1_200_000, half=3.0, dz_bin=2,
+                lateral=[((1.0, 3.0), 4.0), ((3.0, 9.0), 4.0)]),
 }
+X_BIN = 8                  # lateral bins of 2 cm
 
 
 def binned_curves(d, case):
     """Mean dose of each bin: the central-axis depth dose and the lateral
-    profiles (x in 1 cm bins) of the case.  d: flat x-fastest grid."""
+    profiles (x in 2 cm bins) of the case.  d: flat x-fastest grid."""
     g = np.asarray(d, np.float64).reshape(N, N, N)           # [z, y, x]
     cfg = CASES[case]
     col = _band(16.0 - cfg["half"], 16.0 + cfg["half"])
@@ -57,7 +58,7 @@ def binned_curves(d, case):
     out = {"depth": depth.reshape(-1, cfg["dz_bin"]).mean(axis=1)}
     for (z0, z1), hy in cfg["lateral"]:
         sub = g[_band(z0, z1), _band(16.0 - hy, 16.0 + hy), :]
-        out["x@z%.0f-%.0f" % (z0, z1)] = sub.mean(axis=(0, 1)).reshape(-1, 4).mean(axis=1)
+        out["x@z%g-%g" % (z0, z1)] = sub.mean(axis=(0, 1)).reshape(-1, X_BIN).mean(axis=1)
     return out
 
 
@@ -93,24 +94,27 @@ def test_binned_depth_dose_and_profiles_agree(case):
         eng.close()
     mg, sg = mean_and_sigma(est)
 
-    all_t, all_rel = [], []
+    all_t, all_rel, rows = [], [], []
     for k in mo:
         sel = mo[k] > 0.1 * mo[k].max()
         srel = so[k][sel] / mo[k][sel]
         rel = np.abs(mo[k] - mg[k])[sel] / mo[k][sel]
         bias = float((mo[k] - mg[k])[sel].sum() / mo[k][sel].sum())
         t = (mo[k] - mg[k])[sel] / np.sqrt(so[k][sel] ** 2 + sg[k][sel] ** 2)
-        print("%s %-9s bins %3d  oracle sigma_rel mean %.4f%% max %.4f%%  mean|dD|/D %.4f%%  "
+        print("%s %-10s bins %3d  oracle sigma_rel mean %.4f%% max %.4f%%  mean|dD|/D %.4f%%  "
               "max %.4f%%  bias %+.4f%%  |t|<=2 %.3f"
               % (case, k, sel.sum(), 100 * srel.mean(), 100 * srel.max(), 100 * rel.mean(),
                  100 * rel.max(), 100 * bias, np.mean(np.abs(t) <= 2)))
-        assert sel.sum() >= 8, k
-        assert srel.mean() <= 0.003, (k, srel.mean())         # the precision the gate needs
-        assert rel.mean() <= 0.005, (k, rel.mean())           # gate 2
-        assert abs(bias) <= BIAS_GATE, (k, bias)              # gate 1 on the binned curve
+        rows.append((k, int(sel.sum()), float(srel.mean()), float(rel.mean()), bias))
         all_t.append(t)
         all_rel.append(rel)
+    for k, nsel, srel_mean, rel_mean, bias in rows:
+        assert nsel >= 5, k
+        assert srel_mean <= 0.003, (k, srel_mean)             # the precision the gate needs
+        assert rel_mean <= 0.005, (k, rel_mean)               # gate 2
+        assert abs(bias) <= BIAS_GATE, (k, bias)              # gate 1 on the binned curve
     every = np.concatenate(all_t)
-    # with 15 degrees of freedom per sigma, P(|t| <= 2) is about 0.94
-    assert np.mean(np.abs(every) <= 2.0) >= 0.85, np.mean(np.abs(every) <= 2.0)
+    # with 15 degrees of freedom per sigma, P(|t| <= 2) is about 0.94; over
+    # about 40 bins its standard deviation is 0.04
+    assert np.mean(np.abs(every) <= 2.0) >= 0.80, np.mean(np.abs(every) <= 2.0)
     assert np.concatenate(all_rel).mean() <= 0.005
