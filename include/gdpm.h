@@ -187,10 +187,15 @@ enum {
                                         device until nothing is left (no host checks); 0: the host
                                         loop (default).  Profiling (GDPM_PARAM_PROFILE) uses the
                                         host loop. */
-    GDPM_PARAM_MAX_ITERS = 19        /* loop trips a warp may take in one transport phase
+    GDPM_PARAM_MAX_ITERS = 19,       /* loop trips a warp may take in one transport phase
                                         (1..2^31, default 2^22, far above real use).  A warp
                                         that reaches it abandons its particles and the call
                                         returns GDPM_E_TIMEOUT; the next call starts clean. */
+    GDPM_PARAM_ELECTRON_WALK = 20    /* electron phase form, same results either way: 1
+                                        (default) resumable steps, whose voxel walk takes at
+                                        most 3 trips per loop iteration and resumes in the next,
+                                        so a track with many voxel crossings does not hold its
+                                        warp; 0 a whole condensed-history step per iteration */
 };
 
 /* ------------------------------------------------------------------ inputs */

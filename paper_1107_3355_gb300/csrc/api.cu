@@ -1074,6 +1074,10 @@ int gdpm_set_param(gdpm_ctx* ctx, int param, double v) {
         if (v != 0 && v != 1) return GDPM_E_ARG;
         ctx->use_graph = int(v);
         return GDPM_OK;
+    case GDPM_PARAM_ELECTRON_WALK:
+        if (v != 0 && v != 1) return GDPM_E_ARG;
+        ctx->electron_walk = int(v);
+        return GDPM_OK;
     case GDPM_PARAM_MAX_ITERS:
         if (v < 1 || v > 2147483648.0) return GDPM_E_ARG;
         ctx->max_iters = uint32_t(v);

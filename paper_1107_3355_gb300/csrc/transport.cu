@@ -454,75 +454,152 @@ struct ElSmem {
     const float* atab;
 };
 
-// Straight segment of mass thickness `mass` through the voxel grid (3-D
-// DDA), depositing dpm MeV per g/cm2 in each voxel; with defer_last the
-// final piece is left to the caller.  True if the particle left the phantom.
-// rho_cur is the density of the particle's current voxel, known on entry
-// (no load before the first segment) and kept up to date on exit.
-// pend is energy already owed to the current voxel but not yet tallied: it
-// goes out with the first piece tallied on leaving the voxel, so a track
-// issues one atomic per voxel it visits rather than one per piece.  dep
-// counts this step's energy (tallied or added to pend).
-__device__ bool walk(const SimParams& P, Part& p, float mass, float dpm, float& dep, bool defer_last,
-                     uint32_t& crossings, float& rho_cur, float& pend) {
-    if (!(mass > 0.f)) return false;
-    const float iu = p.u != 0.f ? 1.f / p.u : 0.f;
-    const float iv = p.v != 0.f ? 1.f / p.v : 0.f;
-    const float iw = p.w != 0.f ? 1.f / p.w : 0.f;
-    const int sx = p.u > 0.f ? 1 : -1, sy = p.v > 0.f ? 1 : -1, sz = p.w > 0.f ? 1 : -1;
-    uint32_t vox = vox_of(P, p.ix, p.iy, p.iz);
-    float left = mass;
-    for (int guard = 0; guard < (1 << 20); ++guard) {
-        const float tx = p.u != 0.f ? (float(p.ix + (sx > 0)) * P.dx - p.x) * iu : kInf;
-        const float ty = p.v != 0.f ? (float(p.iy + (sy > 0)) * P.dy - p.y) * iv : kInf;
-        const float tz = p.w != 0.f ? (float(p.iz + (sz > 0)) * P.dz - p.z) * iw : kInf;
-        float tb;
-        int ab;
-        if (tx <= ty && tx <= tz) { tb = tx; ab = 0; }
-        else if (ty <= tz) { tb = ty; ab = 1; }
-        else { tb = tz; ab = 2; }
-        tb = fmaxf(tb, 0.f);
-        const float rho = rho_cur;
-        if (rho * tb >= left) {
-            const float t = left / rho;
-            p.x = fmaf(t, p.u, p.x);
-            p.y = fmaf(t, p.v, p.y);
-            p.z = fmaf(t, p.w, p.z);
-            if (!defer_last) {
-                pend += dpm * left;
-                dep += dpm * left;
-            }
-            return false;
-        }
-        p.x = fmaf(tb, p.u, p.x);
-        p.y = fmaf(tb, p.v, p.y);
-        p.z = fmaf(tb, p.w, p.z);
-        const float piece = rho * tb;
-        const float e = dpm * piece;
-        if (e + pend > 0.f) tally(P, p.flags, vox, e + pend);
-        dep += e;
-        pend = 0.f;
-        left -= piece;
-        ++crossings;
-        if (ab == 0) {
-            p.ix += sx;
-            if (p.ix < 0 || p.ix >= P.nx) return true;
-            vox += sx;
-        } else if (ab == 1) {
-            p.iy += sy;
-            if (p.iy < 0 || p.iy >= P.ny) return true;
-            vox = sy > 0 ? vox + P.nx : vox - P.nx;
-        } else {
-            p.iz += sz;
-            if (p.iz < 0 || p.iz >= P.nz) return true;
-            const uint32_t plane = uint32_t(P.nx) * uint32_t(P.ny);
-            vox = sz > 0 ? vox + plane : vox - plane;
-        }
-        vox = GDPM_IDX(P.status, vox, n_voxels(P), ST_B_VOXEL);
-        rho_cur = __ldg(&P.rho[vox]);
+// The electron phase runs in one of two forms with identical arithmetic
+// (GDPM_PARAM_ELECTRON_WALK): a lane takes a whole condensed-history step
+// per iteration of the phase loop (kernel k_phase<1>), or a resumable step
+// whose voxel walk takes at most kWalkTrips trips of the DDA loop per
+// iteration and resumes in the next (k_phase<2>).  The resumable form keeps
+// a lane with many voxel crossings from holding its warp while the other
+// lanes' steps end and they are refilled; it pays for that with step state
+// that lives across the loop top.
+constexpr int kWalkTrips = 3;
+
+// An electron step in progress: the CH step of Sec. 2.1 is set up once
+// (limits, end energy, hinge deflection), then its straight legs are walked
+// through the voxels over one or more loop iterations.
+struct ElStep {
+    float left;        // mass thickness left in the current leg (g/cm2)
+    float m1;          // mass thickness of the second leg
+    float dpm;         // energy loss per unit mass thickness along the step
+    float u1, v1, w1;  // resumable form: the direction after the hinge; whole-step
+                       // form: the deflection cos(theta), cos(phi), sin(phi)
+    float Tend;        // energy at the end of the step
+    float dep;         // energy of the step tallied or owed to a voxel so far
+    float rho;         // density of the particle's current voxel
+    int leg;           // 0: no step in progress; 1 or 2: walking that leg
+    int lim_m;         // what ends the step (bits 0-1), start material (bits 2+)
+};
+
+// Voxel walk (3-D DDA) of the step in progress, depositing dpm MeV per
+// g/cm2 in each voxel: along leg 1 (zeta x_s), turn to the deflected
+// direction at the hinge, along leg 2 ((1 - zeta) x_s).  pend is energy
+// already owed to the current voxel but not yet tallied: it goes out with
+// the first piece tallied on leaving the voxel, so a track issues one atomic
+// per voxel it visits rather than one per piece; the last piece of leg 2 is
+// left to the caller.  Returns 0 when the trip budget ran out (resumable
+// form), 1 at the end of leg 2, 2 when the particle left the phantom.
+//
+// One DDA trip: the particle either ends its leg inside the current voxel
+// (1) or moves to the voxel's exit face, tallies, and crosses (0, or 2 when
+// it leaves the phantom).
+__device__ __forceinline__ int walk_trip(const SimParams& P, Part& p, ElStep& s, float iu, float iv,
+                                         float iw, int sx, int sy, int sz, uint32_t& vox,
+                                         uint32_t& crossings, float& pend) {
+    const float tx = p.u != 0.f ? (float(p.ix + (sx > 0)) * P.dx - p.x) * iu : kInf;
+    const float ty = p.v != 0.f ? (float(p.iy + (sy > 0)) * P.dy - p.y) * iv : kInf;
+    const float tz = p.w != 0.f ? (float(p.iz + (sz > 0)) * P.dz - p.z) * iw : kInf;
+    float tb;
+    int ab;
+    if (tx <= ty && tx <= tz) { tb = tx; ab = 0; }
+    else if (ty <= tz) { tb = ty; ab = 1; }
+    else { tb = tz; ab = 2; }
+    tb = fmaxf(tb, 0.f);
+    const float rho = s.rho;
+    if (rho * tb >= s.left) {
+        // the leg ends in this voxel
+        const float t = s.left / rho;
+        p.x = fmaf(t, p.u, p.x);
+        p.y = fmaf(t, p.v, p.y);
+        p.z = fmaf(t, p.w, p.z);
+        return 1;
     }
-    atomicOr(P.status, ST_ITER_CAP);
-    return true;
+    p.x = fmaf(tb, p.u, p.x);
+    p.y = fmaf(tb, p.v, p.y);
+    p.z = fmaf(tb, p.w, p.z);
+    const float piece = rho * tb;
+    const float e = s.dpm * piece;
+    if (e + pend > 0.f) tally(P, p.flags, vox, e + pend);
+    s.dep += e;
+    pend = 0.f;
+    s.left -= piece;
+    ++crossings;
+    if (ab == 0) {
+        p.ix += sx;
+        if (p.ix < 0 || p.ix >= P.nx) return 2;
+        vox += sx;
+    } else if (ab == 1) {
+        p.iy += sy;
+        if (p.iy < 0 || p.iy >= P.ny) return 2;
+        vox = sy > 0 ? vox + P.nx : vox - P.nx;
+    } else {
+        p.iz += sz;
+        if (p.iz < 0 || p.iz >= P.nz) return 2;
+        const uint32_t plane = uint32_t(P.nx) * uint32_t(P.ny);
+        vox = sz > 0 ? vox + plane : vox - plane;
+    }
+    vox = GDPM_IDX(P.status, uint32_t(vox), n_voxels(P), ST_B_VOXEL);
+    s.rho = __ldg(&P.rho[vox]);
+    return 0;
+}
+
+// The hinge: the rest of leg 1 stays owed to the current voxel, then the
+// particle turns to the deflected direction (precomputed by the resumable
+// form, rotated here by the whole-step form) and starts leg 2.
+template <bool RESUME>
+__device__ __forceinline__ void hinge(Part& p, ElStep& s, float& pend) {
+    pend += s.dpm * s.left;
+    s.dep += s.dpm * s.left;
+    if (RESUME) {
+        p.u = s.u1; p.v = s.v1; p.w = s.w1;
+    } else {
+        rotate(p.u, p.v, p.w, s.u1, s.v1, s.w1);
+    }
+    s.leg = 2;
+    s.left = s.m1;
+}
+
+// Whole-step form: the legs one after another, with the warp's lanes
+// finishing leg 1 together before any turns.
+__device__ int walk_whole(const SimParams& P, Part& p, ElStep& s, uint32_t& crossings, float& pend) {
+#pragma unroll 1
+    for (;;) {
+        const float iu = p.u != 0.f ? 1.f / p.u : 0.f;
+        const float iv = p.v != 0.f ? 1.f / p.v : 0.f;
+        const float iw = p.w != 0.f ? 1.f / p.w : 0.f;
+        const int sx = p.u > 0.f ? 1 : -1, sy = p.v > 0.f ? 1 : -1, sz = p.w > 0.f ? 1 : -1;
+        uint32_t vox = vox_of(P, p.ix, p.iy, p.iz);
+        int res;
+#pragma unroll 1
+        do {
+            res = walk_trip(P, p, s, iu, iv, iw, sx, sy, sz, vox, crossings, pend);
+        } while (res == 0);
+        if (res == 2 || s.leg == 2) return res;
+        hinge<false>(p, s, pend);
+    }
+}
+
+// Resumable form: at most kWalkTrips trips, turning at the hinge within the
+// budget.
+__device__ int walk_resumable(const SimParams& P, Part& p, ElStep& s, uint32_t& crossings,
+                              float& pend) {
+    float iu = p.u != 0.f ? 1.f / p.u : 0.f;
+    float iv = p.v != 0.f ? 1.f / p.v : 0.f;
+    float iw = p.w != 0.f ? 1.f / p.w : 0.f;
+    int sx = p.u > 0.f ? 1 : -1, sy = p.v > 0.f ? 1 : -1, sz = p.w > 0.f ? 1 : -1;
+    uint32_t vox = vox_of(P, p.ix, p.iy, p.iz);
+#pragma unroll 1
+    for (int trip = 0; trip < kWalkTrips; ++trip) {
+        const int res = walk_trip(P, p, s, iu, iv, iw, sx, sy, sz, vox, crossings, pend);
+        if (res == 2 || (res == 1 && s.leg == 2)) return res;
+        if (res == 1) {
+            hinge<true>(p, s, pend);
+            iu = p.u != 0.f ? 1.f / p.u : 0.f;
+            iv = p.v != 0.f ? 1.f / p.v : 0.f;
+            iw = p.w != 0.f ? 1.f / p.w : 0.f;
+            sx = p.u > 0.f ? 1 : -1; sy = p.v > 0.f ? 1 : -1; sz = p.w > 0.f ? 1 : -1;
+        }
+    }
+    return 0;
 }
 
 __device__ void electron_escape(const SimParams& P, Part& p, float energy, Acc& acc) {
@@ -536,86 +613,108 @@ __device__ void electron_escape(const SimParams& P, Part& p, float energy, Acc& 
 }
 
 // One condensed-history step of an electron or positron (Sec. 2.1), or its
-// absorption.
-__device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool& active, Acc& acc,
-                              Ev& ev, Sec& sec, float& pend) {
+// absorption.  Whole-step form (RESUME false): set up, walk and end in one
+// call.  Resumable form: the step is set up when none is in progress, its
+// voxel walk may take several calls (several iterations of the phase loop),
+// and the step's end (escape, absorption, hard-event candidate) runs in the
+// call whose walk reaches it.
+template <bool RESUME>
+__device__ __forceinline__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool& active,
+                                              Acc& acc, Ev& ev, Sec& sec, float& pend, ElStep& carried) {
     const DevTables& T = P.T;
-    bool absorb = p.E < T.eabs_el;
+    // the whole-step form keeps its step state local to this call
+    ElStep local;
+    ElStep& st = RESUME ? carried : local;
+    if (!RESUME) st.leg = 0;
+    bool absorb = false;
+    if (st.leg == 0) {
+        absorb = p.E < T.eabs_el;
+        if (!absorb) {
+            const float4 r = draw(p, P.key0, P.key1);
+            ev.b += EV_STEP;
+            hist_count(P, p.hist, 1);
+            // material and density of the start voxel, loaded together
+            const uint32_t vox0 = GDPM_IDX(P.status, vox_of(P, p.ix, p.iy, p.iz), n_voxels(P), ST_B_VOXEL);
+            const int m = GDPM_IDX(P.status, int(__ldg(&P.mat[vox0])), T.n_mat, ST_B_TABLE);
+            st.rho = __ldg(&P.rho[vox0]);
+            int i;
+            float f;
+            grid_pos(T, p.E, i, f);
+            const int mi = m * T.n_e + i;
+            const float4 a0 = S.el[mi], a1 = S.el[mi + 1];
+            // step limits as mass thickness in the start material: reach E_abs,
+            // hard-event candidate, or the multiple-scattering step
+            const float R0 = lerpf(a0.x, a1.x, f);
+            const float xms = lerpf(a0.y, a1.y, f);
+            const float xcut = R0 - T.r_eabs[m];
+            const float xhard = (T.flags & GDPM_FLAG_NO_HARD) ? kInf : -__logf(r.x) * T.inv_sigmax[m];
+            int lim;   // what ends the step: 0 reach E_abs, 1 hard candidate, 2 MS step
+            float xs;
+            if (xcut <= xms && xcut <= xhard) { lim = 0; xs = xcut; }
+            else if (xhard <= xms) { lim = 1; xs = xhard; }
+            else { lim = 2; xs = xms; }
+            xs = fmaxf(xs, 0.f);
+            float Tend;
+            if (lim == 0) {
+                Tend = T.eabs_el;
+            } else {
+                const float rr = (R0 - xs - T.rinv_lo[m]) * T.rinv_idr[m];
+                const int j = min(max(int(floorf(rr)), 0), T.n_r - 2);
+                const float g = fminf(fmaxf(rr - float(j), 0.f), 1.f);
+                const float* ri = S.rinv + m * T.n_r;
+                Tend = fminf(lerpf(ri[j], ri[j + 1], g), p.E);
+            }
+            const float Tk = p.E;
+            const float dT = Tk - Tend;
+            if (P.hrec) hist_add(P, p.hist, 1, double(xs));
+            // multiple scattering at the mid-step energy
+            const float Tm = 0.5f * (Tk + Tend);
+            const float pbc = Tm * (Tm + 2.f * kMC2f) / (Tm + kMC2f);
+            const float q = kEs / pbc;
+            const float G1 = xs * q * q * 0.5f * T.inv_x0[m];
+            float mu;
+            if (G1 >= 1.f) {
+                mu = 2.f * r.z - 1.f;
+            } else {
+                const float Asc = screening_A(T, S.atab, G1);
+                mu = 1.f - 2.f * Asc * r.z / (1.f - r.z + Asc);
+            }
+            float cp, sp;
+            cossin_2pi(r.w, cp, sp);
+            if (RESUME) {
+                // the direction after the hinge: leg 1 keeps the step's start
+                // direction, so the deflection is applied to it here, with all
+                // lanes that start a step together
+                st.u1 = p.u; st.v1 = p.v; st.w1 = p.w;
+                rotate(st.u1, st.v1, st.w1, mu, cp, sp);
+            } else {
+                st.u1 = mu; st.v1 = cp; st.w1 = sp;
+            }
+            st.dpm = xs > 0.f ? dT / xs : 0.f;
+            st.dep = 0.f;
+            st.Tend = Tend;
+            // random hinge: zeta x_s straight, deflect, (1 - zeta) x_s straight
+            st.left = r.y * xs;
+            st.m1 = (1.f - r.y) * xs;
+            st.leg = 1;
+            st.lim_m = lim | (m << 2);
+        }
+    }
     if (!absorb) {
-        const float4 r = draw(p, P.key0, P.key1);
-        ev.b += EV_STEP;
-        hist_count(P, p.hist, 1);
-        // material and density of the start voxel, loaded together
-        const uint32_t vox0 = GDPM_IDX(P.status, vox_of(P, p.ix, p.iy, p.iz), n_voxels(P), ST_B_VOXEL);
-        const int m = GDPM_IDX(P.status, int(__ldg(&P.mat[vox0])), T.n_mat, ST_B_TABLE);
-        float rho_cur = __ldg(&P.rho[vox0]);
-        int i;
-        float f;
-        grid_pos(T, p.E, i, f);
-        const int mi = m * T.n_e + i;
-        float4 a0 = S.el[mi], a1 = S.el[mi + 1];
-        // step limits as mass thickness in the start material: reach E_abs,
-        // hard-event candidate, or the multiple-scattering step
-        const float R0 = lerpf(a0.x, a1.x, f);
-        const float xms = lerpf(a0.y, a1.y, f);
-        const float xcut = R0 - T.r_eabs[m];
-        const float xhard = (T.flags & GDPM_FLAG_NO_HARD) ? kInf : -__logf(r.x) * T.inv_sigmax[m];
-        int lim;   // what ends the step: 0 reach E_abs, 1 hard candidate, 2 MS step
-        float xs;
-        if (xcut <= xms && xcut <= xhard) { lim = 0; xs = xcut; }
-        else if (xhard <= xms) { lim = 1; xs = xhard; }
-        else { lim = 2; xs = xms; }
-        xs = fmaxf(xs, 0.f);
-        float Tend;
-        if (lim == 0) {
-            Tend = T.eabs_el;
-        } else {
-            const float rr = (R0 - xs - T.rinv_lo[m]) * T.rinv_idr[m];
-            const int j = min(max(int(floorf(rr)), 0), T.n_r - 2);
-            const float g = fminf(fmaxf(rr - float(j), 0.f), 1.f);
-            const float* ri = S.rinv + m * T.n_r;
-            Tend = fminf(lerpf(ri[j], ri[j + 1], g), p.E);
-        }
+        const int res = RESUME ? walk_resumable(P, p, st, ev.n, pend) : walk_whole(P, p, st, ev.n, pend);
+        if (res == 0) return;            // the walk goes on in the next iteration
+        st.leg = 0;
         const float Tk = p.E;
-        const float dT = Tk - Tend;
-        if (P.hrec) hist_add(P, p.hist, 1, double(xs));
-        // multiple scattering at the mid-step energy
-        const float Tm = 0.5f * (Tk + Tend);
-        const float pbc = Tm * (Tm + 2.f * kMC2f) / (Tm + kMC2f);
-        const float q = kEs / pbc;
-        const float G1 = xs * q * q * 0.5f * T.inv_x0[m];
-        float mu;
-        if (G1 >= 1.f) {
-            mu = 2.f * r.z - 1.f;
-        } else {
-            const float Asc = screening_A(T, S.atab, G1);
-            mu = 1.f - 2.f * Asc * r.z / (1.f - r.z + Asc);
-        }
-        float cp, sp;
-        cossin_2pi(r.w, cp, sp);
-        const float dpm = xs > 0.f ? dT / xs : 0.f;
-        float dep = 0.f;
-        // random hinge: zeta*xs straight, deflect, (1-zeta)*xs straight.  One
-        // walk call site in a two-pass loop keeps a single copy of the voxel
-        // walk in the kernel (two inlined copies overflow the instruction
-        // cache and stall the warps on instruction fetch).
-        bool out = false;
-#pragma unroll 1
-        for (int leg = 0; leg < 2; ++leg) {
-            out = walk(P, p, leg ? (1.f - r.y) * xs : r.y * xs, dpm, dep, leg == 1, ev.n, rho_cur,
-                       pend);
-            if (out || leg == 1) break;
-            rotate(p.u, p.v, p.w, mu, cp, sp);
-        }
-        if (out) {
-            electron_escape(P, p, Tk - dep, acc);
+        if (res == 2) {
+            electron_escape(P, p, Tk - st.dep, acc);
             ev.b += EV_TERM;
             active = false;
             return;
         }
         // the step's remainder stays owed to the voxel the step ends in
-        pend += dT - dep;
-        p.E = Tend;
+        pend += (Tk - st.Tend) - st.dep;
+        p.E = st.Tend;
+        const int lim = st.lim_m & 3, m = st.lim_m >> 2;
         if (lim == 0) {
             absorb = true;
         } else if (lim == 1) {
@@ -624,10 +723,11 @@ __device__ void electron_step(const SimParams& P, const ElSmem& S, Part& p, bool
             const float Tn = p.E, wcc = T.eabs_el, wcb = T.eabs_ph;
             float sm = 0.f, sb = 0.f;
             if (Tn > wcb || Tn > 2.f * wcc) {
+                int i;
+                float f;
                 grid_pos(T, Tn, i, f);
                 const int mj = m * T.n_e + i;
-                a0 = S.el[mj];
-                a1 = S.el[mj + 1];
+                const float4 a0 = S.el[mj], a1 = S.el[mj + 1];
                 if (Tn > 2.f * wcc) sm = lerpf(a0.z, a1.z, f);
                 if (Tn > wcb) sb = lerpf(a0.w, a1.w, f);
             }
@@ -845,7 +945,8 @@ constexpr uint32_t kGrab = 128u;
 // One transport phase (Sec. 2.2.1 Step 3): a persistent loop per warp.
 // Loop top (whole warp): fold event counters now and then, bank the
 // secondaries of the last step, refill lanes whose particle ended.  Then
-// each lane takes one step of its own particle.
+// each lane takes one step of its own particle.  PT: 0 photons, 1 electrons
+// a whole step per iteration, 2 electrons with resumable steps.
 template <int PT>
 __device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -891,6 +992,7 @@ __device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A
     Slots sl[2] = {{0u, 0u}, {0u, 0u}};
     bool active = false, exhausted = false;
     float pend = 0.f;   // electron energy owed to its current voxel (see walk)
+    ElStep est{};       // electron step in progress (leg 0: none)
     // the warp's block of work indices [st_base, st_base + st_left); near
     // the end of the phase (less than two per lane of the grid left) the
     // warp takes exactly what it needs, so no warp sits on spare work
@@ -950,11 +1052,11 @@ __device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A
         // ---- each lane on its own: one step
         if (active) {
             if (PT == 0) photon_step(P, ps, p, active, acc, ev, sec);
-            else electron_step(P, es, p, active, acc, ev, sec, pend);
+            else electron_step<PT == 2>(P, es, p, active, acc, ev, sec, pend, est);
         }
     }
     // only a phase stopped by its iteration cap leaves a track unfinished
-    if (PT == 1 && pend != 0.f) tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), pend);
+    if (PT != 0 && pend != 0.f) tally(P, p.flags, vox_of(P, p.ix, p.iy, p.iz), pend);
     flush_events<PT>(ev, s_cnt);
     flush_warp_counts<PT>(wc, s_cnt);
     // reserved queue slots never written: mark them empty for the consumer
@@ -1109,7 +1211,9 @@ __device__ __forceinline__ PhaseArgs phase_args(const LoopArgs& L, uint32_t k) {
 }
 
 // One pass of the device-driven loop runs photon phase k and electron
-// phase k+1, k = *L.k (even); PT selects which of the two this launch is.
+// phase k+1, k = *L.k (even); PT selects which of the two this launch is
+// (0 the photon phase; 1 or 2 the electron phase in its whole-step or
+// resumable form).
 // The phase's arguments are derived in shared memory from k.  (A kernel of
 // its own: the host loop's k_phase takes them as kernel parameters, which
 // keeps more registers for the transport loop.)
@@ -1117,7 +1221,7 @@ template <int PT>
 __global__ void __launch_bounds__(256, PT == 0 ? GDPM_MIN_CTAS_PHOTON : GDPM_MIN_CTAS_ELECTRON)
 k_phase_loop(const SimParams P, const LoopArgs L) {
     __shared__ PhaseArgs sA;
-    if (threadIdx.x == 0) sA = phase_args(L, *L.k + uint32_t(PT));
+    if (threadIdx.x == 0) sA = phase_args(L, *L.k + (PT == 0 ? 0u : 1u));
     __syncthreads();
     phase_run<PT>(P, sA);
 }
@@ -1308,7 +1412,10 @@ int transport_smem(const gdpm_tables* t, int particle) { return int(smem_of(t->d
 int launch_phase(gdpm_ctx* ctx, cudaStream_t st, int particle, const SimParams& P,
                  const PhaseArgs& A, uint32_t n_items_hint, uint32_t share) {
     const size_t smem = smem_of(P.T, particle);
-    const void* fn = particle == GDPM_PHOTON ? (const void*)k_phase<0> : (const void*)k_phase<1>;
+    const bool resumable = particle != GDPM_PHOTON && ctx->electron_walk == 1;
+    const void* fn = particle == GDPM_PHOTON ? (const void*)k_phase<0>
+                     : resumable              ? (const void*)k_phase<2>
+                                              : (const void*)k_phase<1>;
     GDPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int bps = ctx->blocks_per_sm;
     if (bps <= 0) {
@@ -1331,6 +1438,8 @@ int launch_phase(gdpm_ctx* ctx, cudaStream_t st, int particle, const SimParams& 
     B.bank_block = bb >= 8u ? uint32_t(bb) : 0u;
     if (particle == GDPM_PHOTON)
         k_phase<0><<<grid, ctx->block_threads, smem, st>>>(P, B);
+    else if (resumable)
+        k_phase<2><<<grid, ctx->block_threads, smem, st>>>(P, B);
     else
         k_phase<1><<<grid, ctx->block_threads, smem, st>>>(P, B);
     GDPM_CUDA_TRY(cudaGetLastError());
@@ -1373,7 +1482,9 @@ int build_loop_graph(gdpm_ctx* ctx, const SimParams& P, LoopArgs& L, bool metrop
     *exec = nullptr;
     uint32_t grid[2];
     size_t smem[2];
-    const void* fn[2] = {(const void*)k_phase_loop<0>, (const void*)k_phase_loop<1>};
+    const void* fn[2] = {(const void*)k_phase_loop<0>,
+                         ctx->electron_walk == 1 ? (const void*)k_phase_loop<2>
+                                                 : (const void*)k_phase_loop<1>};
     for (int t = 0; t < 2; ++t) {
         smem[t] = smem_of(P.T, t == 0 ? GDPM_PHOTON : GDPM_ELECTRON);
         GDPM_CUDA_TRY(cudaFuncSetAttribute(fn[t], cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem[t])));

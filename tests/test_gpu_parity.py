@@ -343,6 +343,28 @@ def test_batch_modes_agree(tally):
     assert st_con["phases"] < st_seq["phases"]
 
 
+@pytest.mark.parametrize("case", ["slab_photon", "slab_electron"])
+def test_electron_walk_forms_agree(case):
+    """Whole electron steps per loop iteration, or resumable steps whose
+    voxel walk is spread over iterations: the same arithmetic per history,
+    so the same event records, doses up to FP64 summation order, and
+    counts."""
+    if case == "slab_photon":
+        prob = W.slab_photon_problem(n_histories=40_000, n_batches=10, shape=(64, 64, 128))
+    else:
+        prob = W.slab_electron_problem(n_histories=4_000, n_batches=10, shape=(64, 64, 128))
+    out = {}
+    for form in (0, 1):
+        out[form] = run_gpu(prob, params={G.GDPM_PARAM_ELECTRON_WALK: form}, records=True)
+    (d0, s0, st0, r0, rd0), (d1, s1, st1, r1, rd1) = out[0], out[1]
+    assert np.array_equal(r0, r1)
+    np.testing.assert_allclose(d1, d0, rtol=1e-9, atol=1e-12 * d0.max())
+    np.testing.assert_allclose(s1, s0, rtol=1e-6, atol=1e-9 * s0.max())
+    np.testing.assert_allclose(rd1, rd0, rtol=1e-9, atol=1e-12)
+    for k in ("compton", "el_steps", "moller", "brems", "crossings", "pushes", "pops"):
+        assert st1[k] == st0[k], k
+
+
 def test_host_outputs_equal_device_outputs():
     prob = W.tiny_problem(n_histories=20_000, n_batches=10)
     eng = G.Engine(prob)
