@@ -98,7 +98,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # that kernel.  They hold while the kernel sources hash to `sha1`; otherwise
 # traffic is null.
 TRAFFIC_SOURCES = ("transport.cu", "common.cuh", "internal.h")
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/dram_k_phase_ct256_imrt7_2e6hist.md: 2e6 histories, 10 batches
+    # side by side, 4 launches of each phase kernel
+    "ct256_imrt7": {"tally": "fp64", "sha1": "665393ca923d96f40e03e90bae2cc8a9205e6cca",
+                    "bytes_per_history": {"electron phase": 324.7, "photon phase": 366.0}},
+}
 
 
 def sources_sha1():
@@ -135,6 +140,9 @@ def parse():
                     help="batches (default 100; 10 for the paper's cases)")
     ap.add_argument("--tally", default="fp64", choices=["fp64", "fp32pair"],
                     help="dose tally: FP64 atomics, or FP32 hi/lo compensated pairs")
+    ap.add_argument("--electron-walk", type=int, default=None, choices=[0, 1],
+                    help="electron phase form (GDPM_PARAM_ELECTRON_WALK): 1 resumable steps "
+                         "(the library's default), 0 a whole step per loop iteration")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -592,8 +600,11 @@ def main():
     dev = torch.device("cuda", local)
 
     prob = make(n_hist, args.batches).with_(request_id=rank)
-    eng = G.Engine(prob, device=local, params={G.GDPM_PARAM_PROFILE: 1,
-                                               G.GDPM_PARAM_TALLY_MODE: 1 if args.tally == "fp32pair" else 0})
+    params = {G.GDPM_PARAM_PROFILE: 1, G.GDPM_PARAM_TALLY_MODE: 1 if args.tally == "fp32pair" else 0}
+    if args.electron_walk is not None:
+        params[G.GDPM_PARAM_ELECTRON_WALK] = args.electron_walk
+        config["electron_walk"] = args.electron_walk
+    eng = G.Engine(prob, device=local, params=params)
     V = prob.phantom.n_voxels
     dose = torch.empty(V, dtype=torch.float64, device=dev)
     sigma = torch.empty(V, dtype=torch.float64, device=dev)

