@@ -143,6 +143,9 @@ def parse():
     ap.add_argument("--electron-walk", type=int, default=None, choices=[0, 1],
                     help="electron phase form (GDPM_PARAM_ELECTRON_WALK): 1 resumable steps "
                          "(the library's default), 0 a whole step per loop iteration")
+    ap.add_argument("--autotune-ms", type=float, default=0.0,
+                    help="run gdpm_autotune on the step's calculation for this wall-clock "
+                         "budget before the warm-up, and time the configuration it sets")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -605,6 +608,13 @@ def main():
         params[G.GDPM_PARAM_ELECTRON_WALK] = args.electron_walk
         config["electron_walk"] = args.electron_walk
     eng = G.Engine(prob, device=local, params=params)
+    if args.autotune_ms > 0:
+        tuned = G.gdpm_autotune(eng.ctx, eng.phantom, eng.tables, n_hist, args.batches,
+                                budget_ms=args.autotune_ms)
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_PROFILE, 1)
+        config["autotuned"] = {k: tuned[k] for k in ("batch_mode", "source_chunk", "speculative",
+                                                     "electron_walk", "block_threads",
+                                                     "queue_capacity", "graph")}
     V = prob.phantom.n_voxels
     dose = torch.empty(V, dtype=torch.float64, device=dev)
     sigma = torch.empty(V, dtype=torch.float64, device=dev)

@@ -320,15 +320,28 @@ typedef struct {
     int speculative;           /* GDPM_PARAM_SPECULATIVE: phase pairs per host check */
     int candidates_tried;
     double histories_per_s;    /* of the best candidate (wall clock, whole call) */
+    int electron_walk;         /* GDPM_PARAM_ELECTRON_WALK: 1 resumable steps, 0 whole steps */
+    int block_threads;         /* GDPM_PARAM_BLOCK_THREADS of the transport kernels */
+    uint32_t queue_capacity;   /* GDPM_PARAM_QUEUE_CAPACITY (0: 8 per primary of a phase + 65536) */
+    int graph;                 /* GDPM_PARAM_GRAPH: 1 device-driven phase loop */
 } gdpm_tune_result;
 
 /* Autotuner for the launch configuration of the Sec. 2.2.1 transport loop:
- * run the calculation gdpm_simulate(ph, tb, n_histories,
- * n_batches) with the current source under each candidate launch
- * configuration -- batches side by side (when their grids fit) or one after
- * another, 1M / 4M primaries per phase or the side-by-side default (8M or
- * more), 1 / 2 / 4 phase pairs per host check -- until the wall-clock budget is spent, keep the fastest, and set
- * it on the context (GDPM_PARAM_BATCH_MODE, _SOURCE_CHUNK, _SPECULATIVE).
+ * run the calculation gdpm_simulate(ph, tb, n_histories, n_batches) with the
+ * current source under candidate launch configurations until the wall-clock
+ * budget is spent, keep the fastest, and set it on the context.  After one
+ * untimed run (allocations), stage 1 tries every combination of batches side
+ * by side (when their grids fit) or one after another, 1M / 4M primaries per
+ * phase or the side-by-side default (8M or more), and 1 / 2 / 4 phase pairs
+ * per host check.  Then, one dimension at a time from the best so far
+ * (kept only when more than 1 % faster): the other electron phase form
+ * (GDPM_PARAM_ELECTRON_WALK), blocks of 128 / 192 / 256 threads, half the
+ * default queue capacity (4 slots per primary of a phase + 65536; a
+ * candidate whose queues overflow is skipped), and for batches side by side
+ * the device-driven phase loop (GDPM_PARAM_GRAPH).  The primaries per phase
+ * also set the default queue capacity (8 per primary + 65536).  Energy-bin
+ * sorting of the queues is not a candidate: measured, it made the electron
+ * phase 10 % slower, so the engine does not offer it.
  * Results do not depend on the configuration (per-history random streams),
  * only the time does.  `out` is a host struct.
  * Errors: those of gdpm_simulate; GDPM_E_ARG (budget_ms <= 0, NULL out). */

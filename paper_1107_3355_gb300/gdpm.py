@@ -314,7 +314,9 @@ def gdpm_simulate_beamlets(ctx, phantom, tables, n_histories, n_batches, dose_ou
 
 class gdpm_tune_result(C.Structure):
     _fields_ = [("batch_mode", C.c_int), ("source_chunk", C.c_uint32), ("speculative", C.c_int),
-                ("candidates_tried", C.c_int), ("histories_per_s", C.c_double)]
+                ("candidates_tried", C.c_int), ("histories_per_s", C.c_double),
+                ("electron_walk", C.c_int), ("block_threads", C.c_int),
+                ("queue_capacity", C.c_uint32), ("graph", C.c_int)]
 
 
 def gdpm_autotune(ctx, phantom, tables, n_histories, n_batches, budget_ms=2000.0):

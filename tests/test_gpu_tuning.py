@@ -28,6 +28,31 @@ def test_autotune_sets_a_valid_configuration_and_keeps_results():
         assert r["speculative"] in (1, 2, 4)
         assert 1 <= r["source_chunk"] <= prob.n_histories
         assert r["candidates_tried"] >= 1 and r["histories_per_s"] > 0
+        assert r["electron_walk"] in (0, 1)
+        assert r["block_threads"] in (128, 192, 256)
+        assert r["queue_capacity"] in (0, 4 * r["source_chunk"] + 65536)
+        assert r["graph"] in (0, 1) and (r["graph"] == 0 or r["batch_mode"] == 2)
+        _, _, st = eng.run()
+        for k in KEYS:
+            assert st[k] == ref[k], k
+        assert st["deposited"] == pytest.approx(ref["deposited"], rel=1e-9)
+    finally:
+        eng.close()
+
+
+@pytest.mark.parametrize("walk,threads,cap", [(0, 128, 0), (1, 192, 4 * 300_000 + 65536),
+                                              (1, 256, 0)])
+def test_tuned_dimensions_keep_results(walk, threads, cap):
+    """Each dimension the autotuner sets beyond the phase layout -- electron
+    phase form, block shape, queue capacity -- changes only the launch: the
+    integer event counts and the energy ledger equal the defaults'."""
+    prob = W.slab_electron_problem(n_histories=300_000, n_batches=10, shape=(64, 64, 128))
+    eng = G.Engine(prob)
+    try:
+        _, _, ref = eng.run()
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_ELECTRON_WALK, walk)
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_BLOCK_THREADS, threads)
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_QUEUE_CAPACITY, cap)
         _, _, st = eng.run()
         for k in KEYS:
             assert st[k] == ref[k], k
