@@ -159,6 +159,9 @@ def parse():
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-arc-histories", type=float, default=5e8)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-big-slots", type=int, default=1)
+    ap.add_argument("--serve-phase-cap", type=float, default=0.0)
+    ap.add_argument("--serve-share", type=int, default=7)
     ap.add_argument("--serve-seed", type=int, default=3)
     args = ap.parse_args()
     h, nb = DEFAULT_SIZE.get(args.workload, (1e8, 100))
@@ -351,16 +354,26 @@ def serve_bench(args):
     V = ph.n_voxels
     dose = torch.empty(V, dtype=torch.float64, device="cuda")
     sig = torch.empty(V, dtype=torch.float64, device="cuda")
-    # calibrate service rate for the arrival process
-    G.gdpm_source_set(ctx, reqs[0][1])
-    G.gdpm_simulate(ctx, eng.phantom, eng.tables, 1_000_000, 10, dose, sig)
-    t0 = time.perf_counter()
-    G.gdpm_simulate(ctx, eng.phantom, eng.tables, 5_000_000, 10, dose, sig)
-    rate = 5_000_000 / (time.perf_counter() - t0)
-    mean_hist = np.mean([n for _, _, n in reqs])
+    # capacity of the mix for the arrival process: one request of each kind
+    # served alone (after a warm-up), weighted by how often the stream holds it
+    service = {}
+    for kind in ("beamlet", "beam", "arc"):
+        sample = next(((src, n) for k, src, n in reqs if k == kind), None)
+        if sample is None:
+            continue
+        G.gdpm_source_set(ctx, sample[0])
+        G.gdpm_simulate(ctx, eng.phantom, eng.tables, min(sample[1], 2_000_000), 10, dose, sig)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.gdpm_simulate(ctx, eng.phantom, eng.tables, sample[1], 10, dose, sig)
+        torch.cuda.synchronize()
+        service[kind] = time.perf_counter() - t0
+    busy = sum(service[k] for k, _, _ in reqs)
+    total_hist = sum(n for _, _, n in reqs)
+    rate = total_hist / busy                       # histories/s of the mix served alone
+    mean_hist = total_hist / len(reqs)
     lam = args.serve_load * rate / mean_hist
     arrivals = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
-    total_hist = sum(n for _, _, n in reqs)
 
     # (a) one at a time, plain gdpm_simulate calls in arrival order
     lat_a = []
@@ -376,6 +389,9 @@ def serve_bench(args):
 
     # (b) continuous batching through the request loop
     G.gdpm_set_param(ctx, G.GDPM_PARAM_SERVE_SLOTS, args.serve_slots)
+    G.gdpm_set_param(ctx, G.GDPM_PARAM_SERVE_BIG_SLOTS, args.serve_big_slots)
+    G.gdpm_set_param(ctx, G.GDPM_PARAM_SERVE_PHASE_CAP, args.serve_phase_cap)
+    G.gdpm_set_param(ctx, G.GDPM_PARAM_SERVE_SHARE, args.serve_share)
     import threading
     ids = [None] * len(reqs)
     done_at = [None] * len(reqs)
@@ -421,7 +437,11 @@ def serve_bench(args):
             "data": "synthetic",
             "config": {"workload": "ct256_serving_mix", "requests": len(reqs),
                        "mix": "60%% beamlet 1e5, 30%% beam 1e7, 10%% VMAT arc %.0e" % args.serve_arc_histories,
-                       "load": args.serve_load, "slots": args.serve_slots, "batches": 10},
+                       "load": args.serve_load, "slots": args.serve_slots,
+                       "big_slots": args.serve_big_slots, "phase_cap": args.serve_phase_cap,
+                       "share_eighths": args.serve_share, "batches": 10,
+                       "load_basis": "offered histories/s over the mix's capacity, each kind "
+                                     "timed once alone: %s s" % {k: round(v, 4) for k, v in service.items()}},
             "continuous": {"p50_ms": pct(lat_b, 50), "p99_ms": pct(lat_b, 99),
                            "histories_per_s": total_hist / span_b, "makespan_s": span_b,
                            "by_kind": by_kind(lat_b)},

@@ -191,11 +191,24 @@ enum {
                                         (1..2^31, default 2^22, far above real use).  A warp
                                         that reaches it abandons its particles and the call
                                         returns GDPM_E_TIMEOUT; the next call starts clean. */
-    GDPM_PARAM_ELECTRON_WALK = 20    /* electron phase form, same results either way: 1
+    GDPM_PARAM_ELECTRON_WALK = 20,   /* electron phase form, same results either way: 1
                                         (default) resumable steps, whose voxel walk takes at
                                         most 3 trips per loop iteration and resumes in the next,
                                         so a track with many voxel crossings does not hold its
                                         warp; 0 a whole condensed-history step per iteration */
+    GDPM_PARAM_SERVE_BIG_SLOTS = 21, /* serving slots for large requests, in arrival order
+                                        (1..15, fewer than GDPM_PARAM_SERVE_SLOTS; default 1);
+                                        the other slots serve small requests.  Set before the
+                                        first gdpm_request_submit. */
+    GDPM_PARAM_SERVE_SMALL_HIST = 22,/* requests of at most this many histories are small
+                                        (default 1e6): they run on high-priority streams */
+    GDPM_PARAM_SERVE_PHASE_CAP = 23, /* primaries per transport phase of a served request
+                                        (0 = as gdpm_simulate, the default).  A persistent
+                                        phase holds its SMs until it drains: shorter phases let
+                                        small requests that arrive meanwhile start sooner, at
+                                        some throughput of the large ones. */
+    GDPM_PARAM_SERVE_SHARE = 24      /* eighths of the SMs (1..8, default 7) a large request's
+                                        phases launch on while small requests run */
 };
 
 /* ------------------------------------------------------------------ inputs */

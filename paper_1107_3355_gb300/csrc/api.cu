@@ -405,14 +405,15 @@ static int validate_run(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, const 
 // to ctx->auto_chunk primaries, sized from the device's memory): a phase
 // ends with a tail in which lanes run out of particles, and longer phases
 // make the tail a smaller share.  Batches one after another have one batch
-// per phase, up to 2^20 primaries.  A served request keeps phases of at
-// most 2^23 primaries: a persistent phase holds its SMs until it drains, and
-// shorter phases let the small requests that arrive meanwhile get SMs sooner.
+// per phase, up to 2^20 primaries.  A served request may keep shorter phases
+// (GDPM_PARAM_SERVE_PHASE_CAP): a persistent phase holds its SMs until it
+// drains, and shorter phases let the small requests that arrive meanwhile
+// get SMs sooner.
 static uint32_t chunk_of(gdpm_ctx* ctx, uint64_t n_per_run, int parts, bool concurrent,
                          bool serving = false) {
     const uint64_t per = (n_per_run + parts - 1) / parts;
     uint32_t chunk = ctx->source_chunk ? ctx->source_chunk : concurrent ? ctx->auto_chunk : (1u << 20);
-    if (serving && !ctx->source_chunk) chunk = std::min(chunk, 1u << 23);
+    if (serving && !ctx->source_chunk && ctx->serve_phase_cap) chunk = std::min(chunk, ctx->serve_phase_cap);
     return uint32_t(std::min<uint64_t>(chunk, per));
 }
 static uint32_t capacity_of(gdpm_ctx* ctx, uint32_t chunk) {
@@ -585,7 +586,8 @@ static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_s
         }
         const uint32_t hint = A.in_count ? 0u : A.n_src;
         const size_t pi = prof_begin(ctx, r, s, ph ? 0 : 1);
-        const uint32_t share = (r.serving && !r.small && ctx->small_running.load() > 0) ? 4u : 1u;
+        const uint32_t share = (r.serving && !r.small && ctx->small_running.load() > 0)
+                                   ? uint32_t(ctx->serve_share8) : 8u;
         int rc = launch_phase(ctx, s, ph ? GDPM_PHOTON : GDPM_ELECTRON, P, A, hint, share);
         prof_end(ctx, r, s, pi);
         if (rc) return rc;
@@ -1101,6 +1103,25 @@ int gdpm_set_param(gdpm_ctx* ctx, int param, double v) {
         ctx->serve_slots = int(v);
         return GDPM_OK;
     }
+    case GDPM_PARAM_SERVE_BIG_SLOTS: {
+        if (v < 1 || v > 15) return GDPM_E_ARG;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (!ctx->workers.empty()) return GDPM_E_STATE;
+        ctx->serve_big_slots = int(v);
+        return GDPM_OK;
+    }
+    case GDPM_PARAM_SERVE_SMALL_HIST:
+        if (v < 0 || v > 4.0e9) return GDPM_E_ARG;
+        ctx->serve_small_hist = uint64_t(v);
+        return GDPM_OK;
+    case GDPM_PARAM_SERVE_PHASE_CAP:
+        if (v < 0 || v > double(1u << 28)) return GDPM_E_ARG;
+        ctx->serve_phase_cap = uint32_t(v);
+        return GDPM_OK;
+    case GDPM_PARAM_SERVE_SHARE:
+        if (v < 1 || v > 8 || v != double(int(v))) return GDPM_E_ARG;
+        ctx->serve_share8 = int(v);
+        return GDPM_OK;
     case GDPM_PARAM_METRIC_MIN_DENSITY:
         if (v < 0 || v > 100) return GDPM_E_ARG;
         ctx->metric_min_rho = float(v);

@@ -1406,11 +1406,11 @@ static size_t smem_of(const DevTables& T, int particle) {
 int transport_smem(const gdpm_tables* t, int particle) { return int(smem_of(t->dev, particle)); }
 
 // Persistent grid: SM count x resident CTAs per SM for this shared-memory size.
-// share = 4 gives the grid three quarters of the GPU: a large request that
-// runs while small ones are active leaves SMs free for them, since
-// persistent CTAs do not yield until their phase's input is drained.
+// share_eighths < 8 gives the grid that many eighths of the GPU: a large
+// request that runs while small ones are active leaves SMs free for them,
+// since persistent CTAs do not yield until their phase's input is drained.
 int launch_phase(gdpm_ctx* ctx, cudaStream_t st, int particle, const SimParams& P,
-                 const PhaseArgs& A, uint32_t n_items_hint, uint32_t share) {
+                 const PhaseArgs& A, uint32_t n_items_hint, uint32_t share_eighths) {
     const size_t smem = smem_of(P.T, particle);
     const bool resumable = particle != GDPM_PHOTON && ctx->electron_walk == 1;
     const void* fn = particle == GDPM_PHOTON ? (const void*)k_phase<0>
@@ -1423,7 +1423,7 @@ int launch_phase(gdpm_ctx* ctx, cudaStream_t st, int particle, const SimParams& 
         if (bps < 1) return GDPM_E_ARG;
     }
     uint32_t grid = uint32_t(ctx->sm_count) * uint32_t(bps);
-    if (share == 4) grid = std::max<uint32_t>(uint32_t(ctx->sm_count), grid * 3 / 4);
+    if (share_eighths < 8) grid = std::max<uint32_t>(uint32_t(ctx->sm_count), grid * share_eighths / 8);
     if (n_items_hint > 0) {
         const uint32_t need = (n_items_hint + ctx->block_threads - 1) / ctx->block_threads;
         grid = need < grid ? need : grid;

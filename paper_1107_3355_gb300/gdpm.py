@@ -42,6 +42,10 @@ GDPM_PARAM_CONCURRENT_MAX_MB = 17
 GDPM_PARAM_GRAPH = 18
 GDPM_PARAM_MAX_ITERS = 19
 GDPM_PARAM_ELECTRON_WALK = 20
+GDPM_PARAM_SERVE_BIG_SLOTS = 21
+GDPM_PARAM_SERVE_SMALL_HIST = 22
+GDPM_PARAM_SERVE_PHASE_CAP = 23
+GDPM_PARAM_SERVE_SHARE = 24
 MICROBENCH = {"red_f64": 0, "red_f32": 1, "atom_f32": 2, "ffma": 3, "dfma": 4, "mufu_lg2": 5}
 MAX_EL, MAX_MAT, MAX_BINS = 16, 8, 256
 
