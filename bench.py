@@ -155,6 +155,9 @@ def parse():
                                                              "resources"])
     ap.add_argument("--matrix-beamlets", type=int, default=400)
     ap.add_argument("--matrix-batches", type=int, default=2)
+    ap.add_argument("--graph", type=int, default=0, choices=[0, 1],
+                    help="beamlet mode: run the phases as one CUDA graph with a conditional "
+                         "WHILE node (GDPM_PARAM_GRAPH; per-kernel times are then not taken)")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-arc-histories", type=float, default=5e8)
@@ -465,7 +468,8 @@ def beamlet_matrix_bench(args):
     nb = args.matrix_batches
     prob = W.beamlet_matrix_problem(n_beamlets=args.matrix_beamlets, n_batches=nb)
     K, V, total = len(prob.sub_histories), prob.phantom.n_voxels, prob.n_histories
-    eng = G.Engine(prob, params={G.GDPM_PARAM_PROFILE: 1})
+    eng = G.Engine(prob, params={G.GDPM_PARAM_PROFILE: 0 if args.graph else 1,
+                                 G.GDPM_PARAM_GRAPH: args.graph})
     dose = torch.empty((K, V), dtype=torch.float64, device="cuda")
     sigma = torch.empty((K, V), dtype=torch.float64, device="cuda") if nb >= 2 else None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -509,7 +513,8 @@ def beamlet_matrix_bench(args):
             "config": {"workload": "slab128_beamlet_matrix", "beamlets": K, "histories": total,
                        "batches": nb, "outputs": "dose and sigma per beamlet" if nb >= 2 else "dose per beamlet",
                        "tally": "%d FP64 grids per beamlet (%.1f GB)" % (nb, nb * K * V * 8 / 1e9),
-                       "l2": "flushed between steps (256 MB write)"},
+                       "l2": "flushed between steps (256 MB write)",
+                       "phase_loop": "CUDA graph (conditional WHILE node)" if args.graph else "host"},
             "one_beamlet_at_a_time": {"value": serial, "unit": "histories/s",
                                       "calls": K, "batches_per_call": 2},
             "kernel_ms_per_step": list(st["kernel_ms"]),

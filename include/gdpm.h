@@ -192,10 +192,13 @@ enum {
                                         that reaches it abandons its particles and the call
                                         returns GDPM_E_TIMEOUT; the next call starts clean. */
     GDPM_PARAM_ELECTRON_WALK = 20,   /* electron phase form, same results either way: 1
-                                        (default) resumable steps, whose voxel walk takes at
-                                        most 3 trips per loop iteration and resumes in the next,
-                                        so a track with many voxel crossings does not hold its
-                                        warp; 0 a whole condensed-history step per iteration */
+                                        resumable steps, whose voxel walk takes at most 3 trips
+                                        per loop iteration and resumes in the next, so a track
+                                        with many voxel crossings does not hold its warp; 0 a
+                                        whole condensed-history step per iteration; 2 (default)
+                                        resumable where the phantom holds voxels below 0.05
+                                        g/cm3 (air: electrons there take steps hundreds of
+                                        voxels long), whole steps otherwise */
     GDPM_PARAM_SERVE_BIG_SLOTS = 21, /* serving slots for large requests, in arrival order
                                         (1..15, fewer than GDPM_PARAM_SERVE_SLOTS; default 1);
                                         the other slots serve small requests.  Set before the

@@ -361,6 +361,17 @@ static int get_majorant(gdpm_ctx* ctx, cudaStream_t st, gdpm_phantom* ph, gdpm_t
     return GDPM_OK;
 }
 
+// The electron phase form of a run (GDPM_PARAM_ELECTRON_WALK): automatic
+// (2) takes resumable steps where the phantom holds air-like voxels.  An
+// electron that reaches air takes a step hundreds of voxels long, and in
+// whole steps that one lane holds its warp for the whole walk; without air
+// the walks are short and the whole-step form, with less state to carry
+// across the loop top, is faster.
+int walk_form(const gdpm_ctx* ctx, const gdpm_phantom* ph) {
+    if (ctx->electron_walk != 2) return ctx->electron_walk;
+    return ph->rhomin_host < kAirDensity ? 1 : 0;
+}
+
 static SimParams base_params(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint32_t request_id) {
     SimParams P{};
     P.nx = ph->nx; P.ny = ph->ny; P.nz = ph->nz;
@@ -375,6 +386,7 @@ static SimParams base_params(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, u
     P.key0 = uint32_t(ctx->seed);
     P.key1 = uint32_t(ctx->seed >> 32) ^ request_id;
     P.tally_mode = ctx->tally_mode;
+    P.walk_resumable = walk_form(ctx, ph);
     P.max_iters = ctx->max_iters;   // loop trips per warp and phase (GDPM_PARAM_MAX_ITERS)
     P.tally_lo = 0;
     P.tally_hi = uint64_t(ph->nx) * ph->ny * ph->nz;   // one grid; widened by batched runs
@@ -1077,7 +1089,7 @@ int gdpm_set_param(gdpm_ctx* ctx, int param, double v) {
         ctx->use_graph = int(v);
         return GDPM_OK;
     case GDPM_PARAM_ELECTRON_WALK:
-        if (v != 0 && v != 1) return GDPM_E_ARG;
+        if (v != 0 && v != 1 && v != 2) return GDPM_E_ARG;
         ctx->electron_walk = int(v);
         return GDPM_OK;
     case GDPM_PARAM_MAX_ITERS:
@@ -1522,7 +1534,7 @@ int gdpm_autotune(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint64_t n_h
             if (cc == last) continue;               // the same phases as the previous candidate
             last = cc;
             for (int spec : {1, 2, 4})
-                cands.push_back({mode, cc, spec, saved.walk, saved.threads, 0u, 0});
+                cands.push_back({mode, cc, spec, walk_form(ctx, ph), saved.threads, 0u, 0});
         }
     }
     // an untimed first run: allocations and module loading stay out of the comparison

@@ -237,6 +237,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     P.key0 = uint32_t(ctx->seed);
     P.key1 = uint32_t(ctx->seed >> 32) ^ ctx->request_id;
     P.tally_mode = ctx->tally_mode;
+    P.walk_resumable = walk_form(ctx, ph);
     P.max_iters = ctx->max_iters;
     P.tally_lo = 0;
     P.tally_hi = V;

@@ -10,25 +10,32 @@
 namespace gdpm {
 namespace {
 
-// Largest density per material index (positive floats order like their bit
-// patterns, so an integer atomicMax on the bits is exact); counts voxels whose
-// density is not a positive finite number (zero, negative, NaN or infinite).
+// Largest density per material index and the smallest density overall
+// (positive floats order like their bit patterns, so integer atomicMax and
+// atomicMin on the bits are exact); counts voxels whose density is not a
+// positive finite number (zero, negative, NaN or infinite).
 __global__ void k_rhomax(const uint8_t* __restrict__ mat, const float* __restrict__ rho, size_t V,
-                         int* rmax_bits, unsigned int* n_bad) {
+                         int* rmax_bits, unsigned int* n_bad, int* rmin_bits) {
     __shared__ int s_max[256];
+    __shared__ int s_min;
     for (int k = threadIdx.x; k < 256; k += blockDim.x) s_max[k] = 0;
+    if (threadIdx.x == 0) s_min = 0x7f7fffff;
     __syncthreads();
     unsigned int bad = 0;
+    int mn = 0x7f7fffff;
     for (size_t v = blockIdx.x * size_t(blockDim.x) + threadIdx.x; v < V;
          v += size_t(gridDim.x) * blockDim.x) {
         const float r = rho[v];
         if (!(r > 0.f) || isinf(r)) { ++bad; continue; }
         atomicMax(&s_max[mat[v]], __float_as_int(r));
+        mn = min(mn, __float_as_int(r));
     }
     if (bad) atomicAdd(n_bad, bad);
+    atomicMin(&s_min, mn);
     __syncthreads();
     for (int k = threadIdx.x; k < 256; k += blockDim.x)
         if (s_max[k]) atomicMax(&rmax_bits[k], s_max[k]);
+    if (threadIdx.x == 0) atomicMin(rmin_bits, s_min);
 }
 
 // mu_max(E_i) = (1 + 1e-6) max_m mu_m(E_i) rho_max,m over the materials
@@ -283,14 +290,18 @@ int phantom_density_max(gdpm_ctx* ctx, gdpm_phantom* ph) {
     GDPM_CUDA_TRY(cudaMemsetAsync(ph->rhomax.p, 0, 256 * sizeof(float) + 16, ctx->stream));
     int* bits = static_cast<int*>(ph->rhomax.p);
     unsigned int* bad = reinterpret_cast<unsigned int*>(bits + 256);
+    int* rmin = bits + 257;
+    const int big = 0x7f7fffff;                 // FLT_MAX: the minimum's starting value
+    GDPM_CUDA_TRY(cudaMemcpyAsync(rmin, &big, 4, cudaMemcpyHostToDevice, ctx->stream));
     k_rhomax<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(static_cast<const uint8_t*>(ph->mat.p),
                                                           static_cast<const float*>(ph->rho.p), V,
-                                                          bits, bad);
+                                                          bits, bad, rmin);
     GDPM_CUDA_TRY(cudaGetLastError());
     unsigned int h[260];
-    GDPM_CUDA_TRY(cudaMemcpyAsync(h, ph->rhomax.p, 257 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GDPM_CUDA_TRY(cudaMemcpyAsync(h, ph->rhomax.p, 258 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     GDPM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     if (h[256] != 0) return GDPM_E_ARG;
+    std::memcpy(&ph->rhomin_host, &h[257], 4);
     for (int k = 0; k < 256; ++k) {
         float f;
         std::memcpy(&f, &h[k], 4);

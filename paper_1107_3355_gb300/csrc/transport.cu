@@ -1412,7 +1412,7 @@ int transport_smem(const gdpm_tables* t, int particle) { return int(smem_of(t->d
 int launch_phase(gdpm_ctx* ctx, cudaStream_t st, int particle, const SimParams& P,
                  const PhaseArgs& A, uint32_t n_items_hint, uint32_t share_eighths) {
     const size_t smem = smem_of(P.T, particle);
-    const bool resumable = particle != GDPM_PHOTON && ctx->electron_walk == 1;
+    const bool resumable = particle != GDPM_PHOTON && P.walk_resumable;
     const void* fn = particle == GDPM_PHOTON ? (const void*)k_phase<0>
                      : resumable              ? (const void*)k_phase<2>
                                               : (const void*)k_phase<1>;
@@ -1483,8 +1483,8 @@ int build_loop_graph(gdpm_ctx* ctx, const SimParams& P, LoopArgs& L, bool metrop
     uint32_t grid[2];
     size_t smem[2];
     const void* fn[2] = {(const void*)k_phase_loop<0>,
-                         ctx->electron_walk == 1 ? (const void*)k_phase_loop<2>
-                                                 : (const void*)k_phase_loop<1>};
+                         P.walk_resumable ? (const void*)k_phase_loop<2>
+                                          : (const void*)k_phase_loop<1>};
     for (int t = 0; t < 2; ++t) {
         smem[t] = smem_of(P.T, t == 0 ? GDPM_PHOTON : GDPM_ELECTRON);
         GDPM_CUDA_TRY(cudaFuncSetAttribute(fn[t], cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem[t])));
