@@ -14,7 +14,7 @@ from oracle import oracle as O
 from paper_1107_3355_gb300 import gdpm as G
 from paper_1107_3355_gb300 import workloads as W
 from tests._stats import BIAS_GATE, signed_bias
-from tests.test_gpu_parity import check_ledger, run_gpu
+from tests.test_gpu_parity import LEDGER_TOL, check_ledger, run_gpu
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -28,7 +28,7 @@ def problem(phantom, source, n=20_000, nb=10, eabs_photon=0.01, eabs_electron=0.
 def same_seed(prob, min_identical=0.99):
     d_o, s_o, led_o, rec_o, _ = O.run(prob, per_history=True)
     d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
-    check_ledger(st, prob.n_histories, 1e-5)
+    check_ledger(st, prob.n_histories, LEDGER_TOL)
     same = np.all(rec_o == rec_g, axis=1).mean()
     assert same >= min_identical, same
     assert st["source_energy"] == pytest.approx(led_o["source_energy"], rel=1e-6)

@@ -45,7 +45,15 @@ def run_gpu(prob, params=None, records=False, seed=None):
         eng.close()
 
 
-def check_ledger(st, n_hist, tol):
+# Relative closure of the energy ledger the transport tests demand.  Every
+# deposit is an FP32 difference of FP32 energies; summed in FP64 over many
+# histories the rounding averages out (measured below 1e-9 on runs of 2e5 to
+# 2e6 histories, tests/test_gpu_ledger.py), while a run of a few histories
+# keeps a few FP32 roundings of its own.
+LEDGER_TOL = 1e-6
+
+
+def check_ledger(st, n_hist, tol=LEDGER_TOL):
     bal = st["deposited"] + st["escaped"] + st["discarded"]
     assert abs(bal - st["source_energy"]) <= tol * st["source_energy"], st
     assert st["n_primary"] == n_hist
@@ -217,7 +225,7 @@ def test_tiny_pencil_same_seed_elementwise():
     prob = W.tiny_problem(n_histories=100_000)
     d_o, s_o, led_o, rec_o, recd_o = O.run(prob, per_history=True)
     d_g, s_g, st, rec_g, recd_g = run_gpu(prob, records=True)
-    check_ledger(st, prob.n_histories, 1e-5)
+    check_ledger(st, prob.n_histories, LEDGER_TOL)
     same = np.all(rec_o == rec_g, axis=1)
     print("identical history records: %.5f" % same.mean())
     assert same.mean() > 0.98
@@ -271,7 +279,7 @@ def test_slab_photon_same_seed():
     prob = W.slab_photon_problem(n_histories=40_000, n_batches=20, shape=(64, 64, 128))
     d_o, s_o, led_o, rec_o, _ = O.run(prob, per_history=True)
     d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
-    check_ledger(st, prob.n_histories, 1e-5)
+    check_ledger(st, prob.n_histories, LEDGER_TOL)
     same = np.all(rec_o == rec_g, axis=1)
     print("slab photon identical records: %.5f" % same.mean())
     assert same.mean() > 0.97
@@ -285,7 +293,7 @@ def test_slab_electron_same_seed():
     prob = W.slab_electron_problem(n_histories=4_000, n_batches=20, shape=(64, 64, 128))
     d_o, s_o, led_o, rec_o, _ = O.run(prob, per_history=True)
     d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
-    check_ledger(st, prob.n_histories, 1e-5)
+    check_ledger(st, prob.n_histories, LEDGER_TOL)
     same = np.all(rec_o == rec_g, axis=1)
     print("slab electron identical records: %.5f" % same.mean())
     assert same.mean() > 0.9
@@ -306,7 +314,7 @@ def test_random_hinge_depth_moment_closed_form():
     for rid in range(8):
         prob = H.problem(100_000, request_id=rid)
         d, _, st = run_gpu(prob)
-        check_ledger(st, prob.n_histories, 1e-5)
+        check_ledger(st, prob.n_histories, LEDGER_TOL)
         assert st["escaped"] == 0.0
         z, e = H.depth_moment(d)
         assert e == pytest.approx(H.T0, rel=1e-4)
@@ -473,7 +481,7 @@ def test_full_size_slab_sampled_histories():
     hold at any size."""
     prob = W.slab_photon_problem(n_histories=10_000_000, n_batches=10)
     d_g, s_g, st, rec_g, recd_g = run_gpu(prob, records=True)
-    check_ledger(st, prob.n_histories, 1e-5)
+    check_ledger(st, prob.n_histories, LEDGER_TOL)
     rng = np.random.default_rng(0)
     for first in sorted(rng.choice(prob.n_histories - 300, 4, replace=False)):
         rec_o, recd_o = O.history_records(prob, int(first), 300)
@@ -501,7 +509,7 @@ def test_ct_imrt_beamlets_same_seed(sampler):
                      e_min=0.005, e_max=6.5)
     d_o, s_o, led_o, rec_o, _ = O.run(prob, per_history=True)
     d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
-    check_ledger(st, prob.n_histories, 1e-5)
+    check_ledger(st, prob.n_histories, LEDGER_TOL)
     same = np.all(rec_o == rec_g, axis=1)
     print("ct imrt identical records: %.5f" % same.mean())
     assert same.mean() > 0.97
@@ -522,7 +530,7 @@ def test_sauter_variant_same_seed():
                      eabs_electron=0.01, e_min=0.002, e_max=0.1, flags=W.FLAG_SAUTER)
     d_o, s_o, led_o, rec_o, _ = O.run(prob, per_history=True)
     d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
-    check_ledger(st, prob.n_histories, 1e-5)
+    check_ledger(st, prob.n_histories, LEDGER_TOL)
     assert st["photoelectric"] == pytest.approx(led_o["photoelectric"], rel=1e-3)
     same = np.all(rec_o == rec_g, axis=1)
     print("sauter identical records: %.5f" % same.mean())
@@ -540,7 +548,7 @@ def test_icru_lung_slab_same_seed():
                      eabs_photon=0.05, eabs_electron=0.2, e_min=0.005, e_max=6.5)
     d_o, s_o, _, rec_o, _ = O.run(prob, per_history=True)
     d_g, s_g, st, rec_g, _ = run_gpu(prob, records=True)
-    check_ledger(st, prob.n_histories, 1e-5)
+    check_ledger(st, prob.n_histories, LEDGER_TOL)
     same = np.all(rec_o == rec_g, axis=1)
     print("icru lung identical records: %.5f" % same.mean())
     assert same.mean() > 0.99
