@@ -35,14 +35,26 @@ constexpr float kEs = 21.2f;            // Rossi-Greisen scattering energy, MeV
 constexpr uint32_t kFull = 0xffffffffu;
 
 // Resident 256-thread CTAs per SM the phase kernels are compiled for: the
-// photon kernel fits 64 registers (4 CTAs); the electron kernel's step has
-// more live state and runs best with up to 85 registers (3 CTAs).
+// photon kernel fits 64 registers (4 CTAs); so does the whole-step electron
+// kernel, with a few spilled words, and the extra warps hide more latency
+// than the spills cost (6 MV slab electron phase -4.6 %); the resumable
+// electron kernel keeps its step state across the loop top and runs best
+// with up to 85 registers (3 CTAs; at 4 it spills that state, +12 %).
 #ifndef GDPM_MIN_CTAS_PHOTON
 #define GDPM_MIN_CTAS_PHOTON 4
+#endif
+#ifndef GDPM_MIN_CTAS_ELECTRON_WHOLE
+#define GDPM_MIN_CTAS_ELECTRON_WHOLE 4
 #endif
 #ifndef GDPM_MIN_CTAS_ELECTRON
 #define GDPM_MIN_CTAS_ELECTRON 3
 #endif
+template <int PT>
+struct MinCtas {
+    static constexpr int value = PT == 0 ? GDPM_MIN_CTAS_PHOTON
+                                 : PT == 1 ? GDPM_MIN_CTAS_ELECTRON_WHOLE
+                                           : GDPM_MIN_CTAS_ELECTRON;
+};
 
 // ---------------------------------------------------------------- ledger/tally
 struct Acc {
@@ -310,18 +322,27 @@ __device__ bool make_primary(const SimParams& P, const PhaseArgs& A, uint32_t id
         p.x = S.origin[0]; p.y = S.origin[1]; p.z = S.origin[2];
         p.u = S.direction[0]; p.v = S.direction[1]; p.w = S.direction[2];
     } else {
-        const float *src, *cen, *au, *av;
+        float src[3], cen[3], au[3], av[3];
         float a0, a1, b0, b1;
         if (S.geometry == GDPM_GEO_POINT_FIELD) {
-            src = S.origin; cen = S.center; au = S.axis_u; av = S.axis_v;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                src[a] = S.origin[a]; cen[a] = S.center[a]; au[a] = S.axis_u[a]; av[a] = S.axis_v[a];
+            }
             a0 = -S.half_u; a1 = S.half_u; b0 = -S.half_v; b1 = S.half_v;
         } else {
             // a dose-matrix sub-problem is its own beamlet; otherwise sample one
             const int kb = A.n_sub ? int(k)
                                    : pick_beamlet(S, A, idx, h, r.w, P.key0, P.key1, cdf_tab ? cdf_tab : S.bl_cdf);
-            const float* row = S.beamlets + size_t(GDPM_IDX(P.status, kb, S.n_beamlets, ST_B_TABLE)) * 16;
-            src = row; cen = row + 3; au = row + 6; av = row + 9;
-            a0 = row[12]; a1 = row[13]; b0 = row[14]; b1 = row[15];
+            // a row is 16 floats, 64 bytes from a 16-byte aligned base: four vector loads
+            const float4* row = reinterpret_cast<const float4*>(S.beamlets) +
+                                size_t(GDPM_IDX(P.status, kb, S.n_beamlets, ST_B_TABLE)) * 4;
+            const float4 q0 = __ldg(row), q1 = __ldg(row + 1), q2 = __ldg(row + 2), q3 = __ldg(row + 3);
+            src[0] = q0.x; src[1] = q0.y; src[2] = q0.z;
+            cen[0] = q0.w; cen[1] = q1.x; cen[2] = q1.y;
+            au[0] = q1.z; au[1] = q1.w; au[2] = q2.x;
+            av[0] = q2.y; av[1] = q2.z; av[2] = q2.w;
+            a0 = q3.x; a1 = q3.y; b0 = q3.z; b1 = q3.w;
         }
         const float su = fmaf(a1 - a0, r.x, a0), sv = fmaf(b1 - b0, r.y, b0);
         const float ax = cen[0] + su * au[0] + sv * av[0];
@@ -1096,7 +1117,7 @@ __device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A
 }
 
 template <int PT>
-__global__ void __launch_bounds__(256, PT == 0 ? GDPM_MIN_CTAS_PHOTON : GDPM_MIN_CTAS_ELECTRON)
+__global__ void __launch_bounds__(256, MinCtas<PT>::value)
 k_phase(const SimParams P, const PhaseArgs A) {
     phase_run<PT>(P, A);
 }
@@ -1231,7 +1252,7 @@ __device__ __forceinline__ PhaseArgs phase_args(const LoopArgs& L, uint32_t k) {
 // its own: the host loop's k_phase takes them as kernel parameters, which
 // keeps more registers for the transport loop.)
 template <int PT>
-__global__ void __launch_bounds__(256, PT == 0 ? GDPM_MIN_CTAS_PHOTON : GDPM_MIN_CTAS_ELECTRON)
+__global__ void __launch_bounds__(256, MinCtas<PT>::value)
 k_phase_loop(const SimParams P, const LoopArgs L) {
     __shared__ PhaseArgs sA;
     if (threadIdx.x == 0) sA = phase_args(L, *L.k + (PT == 0 ? 0u : 1u));
