@@ -101,8 +101,8 @@ TRAFFIC_SOURCES = ("transport.cu", "common.cuh", "internal.h")
 TRAFFIC = {
     # profiles/dram_k_phase_ct256_imrt7_2e6hist.md: 2e6 histories, 10 batches
     # side by side, 4 launches of each phase kernel
-    "ct256_imrt7": {"tally": "fp64", "sha1": "d67be7ca7dac0ed862bb853a7cd5c43e18524699",
-                    "bytes_per_history": {"electron phase": 323.5, "photon phase": 366.0}},
+    "ct256_imrt7": {"tally": "fp64", "sha1": "cce72e206c1b9403b62c68376944c20fd246b111",
+                    "bytes_per_history": {"electron phase": 323.7, "photon phase": 366.0}},
 }
 
 
