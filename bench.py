@@ -8,7 +8,10 @@ beamlets with seeded intensities, 6 MV-like spectrum (Kramers thick target,
 24 equal intervals), SAD 100 cm, cutoffs 50 keV / 200 keV, 1e8 histories in
 100 batches, FP32 transport with FP64 tallies.  One step = one full dose
 calculation of that workload (all batches, statistics and sigma/Dmax); the
-line also carries the time to sigma/Dmax = 1 % measured by running to it.
+line also carries the time to sigma/Dmax = 1 % measured by running to it and,
+under "serving", the request latency (p50/p99) and histories/s of a serving
+mix on the same phantom at 130 % of its capacity, served continuously and one
+request at a time (``--no-serve`` leaves it out).
 ``--workload slab128_6MV`` is the 128^3 water/lung/bone/water slab with a
 10x10 cm field at SSD 100 cm.
 
@@ -147,6 +150,10 @@ def parse():
                     help="run gdpm_autotune on the step's calculation for this wall-clock "
                          "budget before the warm-up, and time the configuration it sets")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-serve", action="store_true",
+                    help="leave out the serving comparison the default line carries")
+    ap.add_argument("--serve-line-requests", type=int, default=120,
+                    help="requests of the serving comparison on the default line (130 %% load)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-run-to-1pct", action="store_true",
@@ -329,6 +336,12 @@ def serve_bench(args):
     10 % VMAT arcs (180 control points, MLC apertures).  Served with
     continuous batching (gdpm_request_submit/poll, several slots) and one at a
     time with plain gdpm_simulate calls; same requests, same histories."""
+    print(json.dumps(serve_measure(args, args.serve_requests, args.serve_load)))
+
+
+def serve_measure(args, n_requests, load):
+    """The serving comparison of serve_bench for n_requests at offered load
+    `load` (relative to the mix's capacity); returns its JSON object."""
     import numpy as np
     import torch
     from paper_1107_3355_gb300 import gdpm as G
@@ -339,7 +352,7 @@ def serve_bench(args):
                      eabs_electron=0.2, e_min=0.005, e_max=6.5)
     iso = tuple(e / 2 for e in ph.extent)
     reqs = []
-    for k in range(args.serve_requests):
+    for k in range(n_requests):
         r = rng.uniform()
         ang = float(rng.uniform(0, 360))
         if r < 0.6:
@@ -375,7 +388,7 @@ def serve_bench(args):
     total_hist = sum(n for _, _, n in reqs)
     rate = total_hist / busy                       # histories/s of the mix served alone
     mean_hist = total_hist / len(reqs)
-    lam = args.serve_load * rate / mean_hist
+    lam = load * rate / mean_hist
     arrivals = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
 
     # (a) one at a time, plain gdpm_simulate calls in arrival order
@@ -440,7 +453,7 @@ def serve_bench(args):
             "data": "synthetic",
             "config": {"workload": "ct256_serving_mix", "requests": len(reqs),
                        "mix": "60%% beamlet 1e5, 30%% beam 1e7, 10%% VMAT arc %.0e" % args.serve_arc_histories,
-                       "load": args.serve_load, "slots": args.serve_slots,
+                       "load": load, "slots": args.serve_slots,
                        "big_slots": args.serve_big_slots, "phase_cap": args.serve_phase_cap,
                        "share_eighths": args.serve_share, "batches": 10,
                        "load_basis": "offered histories/s over the mix's capacity, each kind "
@@ -452,7 +465,7 @@ def serve_bench(args):
                               "histories_per_s": total_hist / span_a, "makespan_s": span_a,
                               "by_kind": by_kind(lat_a)},
             "calibrated_histories_per_s": rate, "total_histories": int(total_hist)}
-    print(json.dumps(line))
+    return line
 
 
 def beamlet_matrix_bench(args):
@@ -811,9 +824,23 @@ def main():
                                           "10 batches, disjoint streams" % (procs, per, args.workload),
                                 "single_core_value": n / dt,
                                 "single_core_sample": "%d histories, one thread" % n}
+    eng.close()
+    if rank == 0 and world == 1 and not args.no_serve and args.workload == "ct256_imrt7":
+        # the metric's request latency: the serving mix on the same phantom at
+        # saturation (130 % of the mix's capacity), served continuously and
+        # one request at a time
+        del dose, sigma, flush
+        torch.cuda.empty_cache()
+        sv = serve_measure(args, args.serve_line_requests, 1.3)
+        line["serving"] = {"p50_ms": sv["continuous"]["p50_ms"], "p99_ms": sv["continuous"]["p99_ms"],
+                           "histories_per_s": sv["continuous"]["histories_per_s"],
+                           "one_at_a_time": {k: sv["one_at_a_time"][k] for k in
+                                             ("p50_ms", "p99_ms", "histories_per_s")},
+                           "by_kind": sv["continuous"]["by_kind"],
+                           "config": dict(sv["config"], load_basis=None),
+                           "capacity_histories_per_s": sv["calibrated_histories_per_s"]}
     if rank == 0:
         print(json.dumps(line))
-    eng.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
