@@ -199,3 +199,45 @@ def test_served_vmat_arc_matches_the_oracle_history_by_history():
     print("served VMAT arc t-test", r)
     assert r["P_high"] >= 0.95 and r["P_all"] >= 0.97
     assert abs(r["bias"]) <= BIAS_GATE
+
+
+@pytest.mark.parametrize("big,share,cap", [(2, 6, 0), (1, 8, 1 << 20)])
+def test_serving_layouts_keep_results(big, share, cap):
+    """Two slots for large requests, another SM share while small requests
+    run, a phase cap for served requests: each changes when the work runs,
+    never what it computes -- a request equals gdpm_simulate with its stream
+    id, in a mix of large and small requests."""
+    prob = W.slab_photon_problem(n_histories=300_000, n_batches=10, shape=(64, 64, 128))
+    eng = G.Engine(prob)
+    V = prob.phantom.n_voxels
+    try:
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_REQUEST_ID, 91)
+        d_sim, _, st_sim = eng.run()
+        d_sim = d_sim.cpu().numpy()
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_SERVE_SMALL_HIST, 200_000)
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_SERVE_BIG_SLOTS, big)
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_SERVE_SHARE, share)
+        G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_SERVE_PHASE_CAP, cap)
+        ph = prob.phantom
+        ids = [G.gdpm_request_submit(eng.ctx, eng.phantom, eng.tables, prob.source, 400_000, 10)]
+        rid = G.gdpm_request_submit(eng.ctx, eng.phantom, eng.tables, prob.source, 300_000, 10,
+                                    stream_id=91)
+        ids += [G.gdpm_request_submit(eng.ctx, eng.phantom, eng.tables,
+                                      W.single_beamlet(ph, 30.0 * k, -1.0, 0.0, 1.0), 50_000, 10)
+                for k in range(4)]
+        d, _, st = wait(eng.ctx, rid, V)
+        for r in ids:
+            wait(eng.ctx, r, V)
+        with pytest.raises(G.GdpmError) as e:        # the slots are running now
+            G.gdpm_set_param(eng.ctx, G.GDPM_PARAM_SERVE_BIG_SLOTS, 1)
+        assert e.value.code == G.GDPM_E_STATE
+        for param, bad in ((G.GDPM_PARAM_SERVE_SHARE, 0), (G.GDPM_PARAM_SERVE_SHARE, 9),
+                           (G.GDPM_PARAM_SERVE_SHARE, 6.5), (G.GDPM_PARAM_SERVE_PHASE_CAP, -1)):
+            with pytest.raises(G.GdpmError) as e:
+                G.gdpm_set_param(eng.ctx, param, bad)
+            assert e.value.code == G.GDPM_E_ARG
+    finally:
+        eng.close()
+    np.testing.assert_allclose(d, d_sim, rtol=1e-9, atol=1e-12 * d_sim.max())
+    for k in ("compton", "el_steps", "crossings"):
+        assert st[k] == st_sim[k], k
