@@ -867,8 +867,9 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
 // serve_small_hist histories) in arrival order and run them on the whole
 // GPU, one at a time per slot; the other slots take small requests, which
 // therefore never wait behind a large one.  While a small request runs,
-// large requests launch on three quarters of the SMs and the small one runs
-// on a high-priority stream, so it gets the SMs left free.  A request is
+// large requests launch their phases on serve_share8 eighths of the SMs (7
+// by default) and the small one runs on a high-priority stream, so it gets
+// the SMs left free.  A request is
 // admitted when its slot is free and device memory allows (continuous
 // batching: requests join as they arrive, their work overlaps on the GPU).
 // Result buffers of served requests come from a pool: cudaFree synchronizes
