@@ -445,10 +445,16 @@ static int prepare_workspace(gdpm_ctx* ctx, Runner& r, size_t V, uint32_t cap, u
                              int n_batches, int n_bins, bool concurrent) {
     Workspace& ws = r.ws;
     int rc;
+    const size_t clean = ws.edep_clean;
+    ws.edep_clean = 0;
+    ws.edep_zero = 0;
     if ((rc = ensure(ws.s1, V * 8)) || (rc = ensure(ws.s2, V * 8))) return rc;
     if (concurrent) {
         // one grid per batch: V*n_batches doubles, or hi and lo halves of floats
-        if ((rc = ensure(ws.edep, V * size_t(n_batches) * 8))) return rc;
+        const size_t want = V * size_t(n_batches) * 8;
+        const bool kept = ws.edep.p && ws.edep.bytes >= want;   // ensure keeps it and its contents
+        if ((rc = ensure(ws.edep, want))) return rc;
+        ws.edep_zero = kept ? clean : 0;
     } else if (ctx->tally_mode == 0) {
         if ((rc = ensure(ws.edep, V * 8)) || (rc = ensure(ws.edep2, V * 8))) return rc;
     } else {
@@ -739,8 +745,10 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
     P.n_records = hrec ? ctx->hrec_n : 0;
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.s1.p, 0, V * 8, s));
     GDPM_CUDA_TRY(cudaMemsetAsync(ws.s2.p, 0, V * 8, s));
+    const size_t grids = V * size_t(n_batches) * 8;
     if (conc) {
-        GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep.p, 0, V * size_t(n_batches) * 8, s));
+        // the previous calculation's fold cleared the grids it read
+        if (ws.edep_zero < grids) GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep.p, 0, grids, s));
     } else if (ctx->tally_mode == 0) {
         GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep.p, 0, V * 8, s));
         GDPM_CUDA_TRY(cudaMemsetAsync(ws.edep2.p, 0, V * 8, s));
@@ -825,13 +833,18 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
     const bool dev_out = dose_out && sigma_out && is_device_ptr(dose_out) && is_device_ptr(sigma_out);
     double *dd = dose_out, *ds = sigma_out;
     if (!dev_out) {
-        if ((rc = ensure(ws.stage, V * 16))) return rc;
+        if ((rc = ensure(ws.stage, V * 16))) {
+            cudaStreamSynchronize(s);       // the fold may still be clearing the grids
+            return rc;
+        }
         dd = static_cast<double*>(ws.stage.p);
         ds = dd + V;
     }
     if ((rc = launch_finalize_into(ctx, s, P, V, n_batches, static_cast<const double*>(ws.s1.p),
-                                   static_cast<const double*>(ws.s2.p), dd, ds)))
+                                   static_cast<const double*>(ws.s2.p), dd, ds))) {
+        cudaStreamSynchronize(s);
         return rc;
+    }
     if (!dev_out) {
         if (dose_out) GDPM_CUDA_TRY(cudaMemcpyAsync(dose_out, dd, V * 8, cudaMemcpyDefault, s));
         if (sigma_out) GDPM_CUDA_TRY(cudaMemcpyAsync(sigma_out, ds, V * 8, cudaMemcpyDefault, s));
@@ -844,6 +857,7 @@ int simulate_impl(gdpm_ctx* ctx, Runner& r, gdpm_phantom* ph, gdpm_tables* tb,
     GDPM_CUDA_TRY(cudaMemcpyAsync(hl, ws.ledger.p, L_NLEDGER * 8, cudaMemcpyDeviceToHost, s));
     GDPM_CUDA_TRY(cudaMemcpyAsync(hs, ws.status.p, 4, cudaMemcpyDeviceToHost, s));
     GDPM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (conc) ws.edep_clean = grids;        // the fold has cleared every grid of this calculation
     if (st) {
         std::memset(st, 0, sizeof(*st));
         fill_stats(hc, hl, st);

@@ -142,7 +142,11 @@ __global__ void __launch_bounds__(256) k_fold(SimParams P, size_t V, double inv_
 // Sums of a voxel's batch tallies b in [b0, b1) of grids of V cells
 // starting at slot `first`: sum e and sum e^2, two FP64 operations per
 // tally.  GB300's FP64 rate (about 5e11 FMA/s), not HBM, bounds the fold,
-// so the batch weights are applied once per voxel, not per tally.
+// so the batch weights are applied once per voxel, not per tally.  CLEAR
+// then zeroes the tallies, leaving the grids ready for the next
+// calculation; the stores come after all the loads, which a store between
+// them would serialise (the compiler cannot tell the addresses apart).
+template <bool CLEAR>
 __device__ __forceinline__ void batch_sums(const SimParams& P, size_t V, size_t first, size_t v,
                                            int b0, int b1, double& se, double& sq) {
     for (int b = b0; b < b1; ++b) {
@@ -151,11 +155,23 @@ __device__ __forceinline__ void batch_sums(const SimParams& P, size_t V, size_t 
         se += e;
         sq = fma(e, e, sq);
     }
+    if (CLEAR) {
+        for (int b = b0; b < b1; ++b) {
+            const size_t k = (first + size_t(b)) * V + v;
+            if (P.tally_mode == 0) {
+                P.edep[k] = 0.0;
+            } else {
+                P.edep_hi[k] = 0.f;
+                P.edep_lo[k] = 0.f;
+            }
+        }
+    }
 }
 
 // All batches at once (batches run side by side, one tally grid each):
 // s1 += sum_b E_b/n_b, s2 += sum_b (E_b/n_b)^2 per voxel (the sums of a run
 // in parts accumulate).  The first n_big batches hold one history more.
+// The grids are left zeroed.
 __global__ void __launch_bounds__(256) k_fold_batches(SimParams P, size_t V, int nbatch,
                                                       double inv_big, double inv_small, int n_big,
                                                       double* __restrict__ s1, double* __restrict__ s2) {
@@ -165,8 +181,8 @@ __global__ void __launch_bounds__(256) k_fold_batches(SimParams P, size_t V, int
     for (size_t v = blockIdx.x * size_t(blockDim.x) + threadIdx.x; v < V;
          v += size_t(gridDim.x) * blockDim.x) {
         double eb = 0.0, qb = 0.0, es = 0.0, qs = 0.0;
-        batch_sums(P, V, 0, v, 0, nbig, eb, qb);
-        batch_sums(P, V, 0, v, nbig, nbatch, es, qs);
+        batch_sums<true>(P, V, 0, v, 0, nbig, eb, qb);
+        batch_sums<true>(P, V, 0, v, nbig, nbatch, es, qs);
         dep += eb + es;
         s1[v] += fma(eb, inv_big, es * inv_small);
         s2[v] += fma(qb, inv_big * inv_big, qs * (inv_small * inv_small));
@@ -194,8 +210,8 @@ __global__ void __launch_bounds__(256) k_fold_sub(SimParams P, size_t V, uint32_
     for (size_t v = blockIdx.x * size_t(blockDim.x) + threadIdx.x; v < V;
          v += size_t(gridDim.x) * blockDim.x) {
         double eb = 0.0, qb = 0.0, es = 0.0, qs = 0.0;
-        batch_sums(P, V, size_t(k) * nb, v, 0, nbg, eb, qb);
-        batch_sums(P, V, size_t(k) * nb, v, nbg, nb, es, qs);
+        batch_sums<false>(P, V, size_t(k) * nb, v, 0, nbg, eb, qb);
+        batch_sums<false>(P, V, size_t(k) * nb, v, nbg, nb, es, qs);
         dep += eb + es;
         const double a1 = fma(eb, ib, es * is);
         const double a2 = fma(qb, ib * ib, qs * (is * is));
