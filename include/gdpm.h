@@ -512,7 +512,7 @@ int gdpm_debug_beamlets(gdpm_ctx *ctx, uint64_t first, uint64_t n, int32_t *out)
  * GDPM_NOALLOC_SCRATCH_BYTES (about 4.0 MB).  Every GPU that loads this
  * library holds that array until the process exits.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) for that
- * device; make that first call before any stream capture begins.
+ * device.
  *
  * Limits (GDPM_E_ARG beyond them): nx*ny*nz <= GDPM_NOALLOC_MAX_VOXELS, at
  * most GDPM_NOALLOC_QUEUE_CAPACITY banked particles per queue fill (more is
@@ -537,7 +537,7 @@ int gdpm_debug_beamlets(gdpm_ctx *ctx, uint64_t first, uint64_t n, int32_t *out)
 #define GDPM_NOALLOC_MAX_PREFIX 65536
 #define GDPM_NOALLOC_MAX_BEAMLETS 1024
 #define GDPM_NOALLOC_MAX_CHAINS 65536
-#define GDPM_NOALLOC_SCRATCH_BYTES 4130816
+#define GDPM_NOALLOC_SCRATCH_BYTES 4098048
 int gdpm_simulate_noalloc(gdpm_ctx *ctx, gdpm_phantom *ph, gdpm_tables *tb, uint64_t n_histories,
                           int n_batches, double *dose_out, double *sigma_out,
                           gdpm_stats *stats_out);

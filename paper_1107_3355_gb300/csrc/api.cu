@@ -169,6 +169,17 @@ static Queue make_queue(const Buffer& b, uint32_t cap) {
     q.capacity = cap;
     return q;
 }
+// The source queue: x y z u v w E, ctr, flags (kSourceWords arrays).
+static Queue make_source_queue(const Buffer& b, uint32_t cap) {
+    Queue q{};
+    uint32_t* base = static_cast<uint32_t*>(b.p);
+    float** fs[7] = {&q.x, &q.y, &q.z, &q.u, &q.v, &q.w, &q.E};
+    for (int k = 0; k < 7; ++k) *fs[k] = reinterpret_cast<float*>(base + size_t(k) * cap);
+    q.ctr = base + size_t(7) * cap;
+    q.flags = base + size_t(8) * cap;
+    q.capacity = cap;
+    return q;
+}
 
 static bool is_device_ptr(const void* p) {
     if (!p) return false;
@@ -466,7 +477,7 @@ static int prepare_workspace(gdpm_ctx* ctx, Runner& r, size_t V, uint32_t cap, u
     if ((rc = ensure(ws.qph, qb)) || (rc = ensure(ws.qel0, qb)) || (rc = ensure(ws.qel1, qb))) return rc;
     ws.cap_ph = ws.cap_el = cap;
     // primaries of one phase: at most a chunk
-    if ((rc = ensure(ws.qsrc, size_t(chunk) * kQueueWords * 4))) return rc;
+    if ((rc = ensure(ws.qsrc, size_t(chunk) * kSourceWords * 4))) return rc;
     ws.cap_src = chunk;
     if ((rc = ensure(ws.ctl, size_t(ctx->max_phases + 4) * 16)) ||
         (rc = ensure(ws.prefix, size_t(n_batches) * (n_bins + 1) * 4)) ||
@@ -494,7 +505,7 @@ static size_t bytes_needed(gdpm_ctx* ctx, const Runner& r, size_t V, uint64_t n_
     n += conc ? grow(w.edep, V * size_t(n_batches) * 8) : grow(w.edep, V * 8) + grow(w.edep2, V * 8);
     const size_t qb = size_t(cap) * kQueueWords * 4;
     n += grow(w.qph, qb) + grow(w.qel0, qb) + grow(w.qel1, qb);
-    n += grow(w.qsrc, size_t(chunk) * kQueueWords * 4);
+    n += grow(w.qsrc, size_t(chunk) * kSourceWords * 4);
     if (with_result) n += V * 16;
     return n;
 }
@@ -517,7 +528,7 @@ static LoopArgs loop_args(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gd
     L.qph = make_queue(ws.qph, ws.cap_ph);
     L.qe0 = make_queue(ws.qel0, ws.cap_el);
     L.qe1 = make_queue(ws.qel1, ws.cap_el);
-    L.qsrc = make_queue(ws.qsrc, ws.cap_src);
+    L.qsrc = make_source_queue(ws.qsrc, ws.cap_src);
     L.ctl = static_cast<uint32_t*>(ws.ctl.p);
     L.status = P.status;
     L.bin_prefix = static_cast<const uint32_t*>(ws.prefix.p);
@@ -581,7 +592,7 @@ static int run_phases(gdpm_ctx* ctx, Runner& r, const SimParams& P, const gdpm_s
                 ++aux;
             }
             // this phase's primaries, made before it runs
-            A.src = make_queue(ws.qsrc, ws.cap_src);
+            A.src = make_source_queue(ws.qsrc, ws.cap_src);
             if (int rc = launch_sources(ctx, s, P, A)) return rc;
             prof_end(ctx, r, s, ps);
             ++aux;
@@ -1030,7 +1041,7 @@ int gdpm_context_create(gdpm_ctx** out, int device, void* cuda_stream, uint64_t 
     // to 2^25 primaries whose queues (three of capacity_of(chunk) slots and
     // the source queue) take at most a quarter of the device's memory
     {
-        const double per_primary = (3.0 * 8.0 + 1.0) * kQueueWords * 4;
+        const double per_primary = (3.0 * 8.0 * kQueueWords + kSourceWords) * 4;
         uint32_t ch = 1u << 25;
         while (ch > (1u << 20) && per_primary * ch > 0.25 * double(prop.totalGlobalMem)) ch >>= 1;
         c->auto_chunk = ch;

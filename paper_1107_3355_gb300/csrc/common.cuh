@@ -133,6 +133,9 @@ struct Queue {
     uint32_t capacity;
 };
 constexpr int kQueueWords = 13;
+// A phase's source queue holds only x y z u v w E, draw counter and flags
+// (source_store); its other four arrays are null.
+constexpr int kSourceWords = 9;
 
 __device__ __forceinline__ void queue_store(const Queue& q, uint32_t s, const Part& p) {
     q.x[s] = p.x; q.y[s] = p.y; q.z[s] = p.z;
@@ -140,6 +143,19 @@ __device__ __forceinline__ void queue_store(const Queue& q, uint32_t s, const Pa
     q.vox[s] = uint32_t(p.ix) | (uint32_t(p.iy) << 10) | (uint32_t(p.iz) << 20);
     q.hist[s] = p.hist; q.pidlo[s] = p.pidlo; q.pidhi[s] = p.pidhi;
     q.ctr[s] = p.ctr; q.flags[s] = p.flags;
+}
+// A primary in its phase's source queue keeps 9 of the words: its history is
+// the phase's first plus its slot, its particle id 1 and its voxel follows
+// from its position.
+__device__ __forceinline__ void source_store(const Queue& q, uint32_t s, const Part& p) {
+    q.x[s] = p.x; q.y[s] = p.y; q.z[s] = p.z;
+    q.u[s] = p.u; q.v[s] = p.v; q.w[s] = p.w; q.E[s] = p.E;
+    q.ctr[s] = p.ctr; q.flags[s] = p.flags;
+}
+__device__ __forceinline__ void source_load(const Queue& q, uint32_t s, Part& p) {
+    p.x = q.x[s]; p.y = q.y[s]; p.z = q.z[s];
+    p.u = q.u[s]; p.v = q.v[s]; p.w = q.w[s]; p.E = q.E[s];
+    p.ctr = q.ctr[s]; p.flags = q.flags[s];
 }
 __device__ __forceinline__ void queue_load(const Queue& q, uint32_t s, Part& p) {
     p.x = q.x[s]; p.y = q.y[s]; p.z = q.z[s];

@@ -51,7 +51,7 @@ constexpr size_t kOffAlias = kOffCut + al(size_t(kNaMaxBeamlets) * 8);
 constexpr size_t kOffChains = kOffAlias + al(size_t(kNaMaxBeamlets) * 4);
 constexpr size_t kOffPick = kOffChains + al(size_t(kNaMaxChains) * 4);
 constexpr size_t kOffSrc = kOffPick + al(size_t(kNaChunk) * 4);
-constexpr size_t kScratchBytes = kOffSrc + al(size_t(kNaChunk) * kQueueWords * 4);
+constexpr size_t kScratchBytes = kOffSrc + al(size_t(kNaChunk) * kSourceWords * 4);
 static_assert(kScratchBytes == GDPM_NOALLOC_SCRATCH_BYTES, "header and layout disagree");
 
 // The scratch.  In host code `g_scratch` only names a host-side stand-in; its
@@ -86,6 +86,17 @@ Queue queue_at(unsigned char* base, uint32_t cap) {
     for (int k = 0; k < 7; ++k) *fs[k] = reinterpret_cast<float*>(w + size_t(k) * cap);
     uint32_t** us[6] = {&q.vox, &q.hist, &q.pidlo, &q.pidhi, &q.ctr, &q.flags};
     for (int k = 0; k < 6; ++k) *us[k] = w + size_t(7 + k) * cap;
+    q.capacity = cap;
+    return q;
+}
+// A phase's primaries: x y z u v w E, draw counter, flags.
+Queue source_queue_at(unsigned char* base, uint32_t cap) {
+    Queue q{};
+    float* f = reinterpret_cast<float*>(base);
+    float** fs[7] = {&q.x, &q.y, &q.z, &q.u, &q.v, &q.w, &q.E};
+    for (int k = 0; k < 7; ++k) *fs[k] = f + size_t(k) * cap;
+    q.ctr = reinterpret_cast<uint32_t*>(f + size_t(7) * cap);
+    q.flags = reinterpret_cast<uint32_t*>(f + size_t(8) * cap);
     q.capacity = cap;
     return q;
 }
@@ -187,7 +198,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     int* al_alias = reinterpret_cast<int*>(base + kOffAlias);
     uint32_t* chains = reinterpret_cast<uint32_t*>(base + kOffChains);
     uint32_t* pick = reinterpret_cast<uint32_t*>(base + kOffPick);
-    const Queue qsrc = queue_at(base + kOffSrc, kNaChunk);
+    const Queue qsrc = source_queue_at(base + kOffSrc, kNaChunk);
 
     // source arrays and majorant into the scratch
     std::vector<float> ef(src.edges.begin(), src.edges.end());

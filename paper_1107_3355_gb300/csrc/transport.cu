@@ -1070,8 +1070,14 @@ __device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A
                 if (idx < A.n_src) {
                     // made by k_sources; a primary that missed the phantom
                     // left its slot empty (E < 0) and is accounted there
-                    queue_load(A.src, GDPM_IDX(P.status, idx, A.src.capacity, ST_B_QUEUE), p);
+                    source_load(A.src, GDPM_IDX(P.status, idx, A.src.capacity, ST_B_QUEUE), p);
                     active = p.E >= 0.f;
+                    if (active) {
+                        p.hist = A.src_first + idx;
+                        p.pidlo = 1u;
+                        p.pidhi = 0u;
+                        voxel_of(P, p);
+                    }
                 } else if (idx < total) {
                     queue_load(A.in, GDPM_IDX(P.status, idx - A.n_src, A.in.capacity, ST_B_QUEUE), p);
                     // a slot reserved but never written holds E < 0
@@ -1153,7 +1159,7 @@ __device__ __forceinline__ void make_sources(const SimParams& P, const PhaseArgs
          idx += gridDim.x * blockDim.x) {
         Part p{};
         if (make_primary(P, A, idx, p, acc, ptab, ctab)) {
-            queue_store(A.src, GDPM_IDX(P.status, idx, A.src.capacity, ST_B_QUEUE), p);
+            source_store(A.src, GDPM_IDX(P.status, idx, A.src.capacity, ST_B_QUEUE), p);
         } else {
             A.src.E[GDPM_IDX(P.status, idx, A.src.capacity, ST_B_QUEUE)] = -1.f;
             ++missed;
