@@ -2,7 +2,8 @@
 
 Beams that never reach the phantom, sources below the absorption energies,
 a one-voxel phantom, an air-filled phantom, a phantom at the largest
-extent per axis, one history per batch, and a ragged history count.  Same
+extent per axis and at the largest volume, one history per batch, and a
+ragged history count.  Same
 seed on both sides, so each history's event record must agree (Sec. 2.2.1
 transport; records differ only where FP32 and FP64 arithmetic part ways),
 and the energy ledger must balance.
@@ -114,3 +115,49 @@ def test_phantom_rejects_densities_that_are_not_positive_and_finite(bad):
         assert e.value.code == G.GDPM_E_ARG
     finally:
         G.gdpm_context_destroy(ctx)
+
+
+def test_largest_phantom_volume():
+    """1024^3 voxels, the largest grid (2^30 voxels: 5.4 GB of phantom and
+    8.6 GB per tally grid, so batches run one after another).  A 64^3 water
+    cube in the far corner of a near-vacuum phantom (1e-9 g/cm3) must get the
+    dose that a 64^3 water phantom alone gets from the same pencil beam,
+    which starts on the cube's face at a voxel centre.  A particle that
+    leaves the convex cube never comes back, so each history is the same in
+    both geometries up to the FP32 rounding of larger coordinates; a tally
+    or index that goes wrong beyond 2^31 bytes or voxels moves dose out of
+    the cube."""
+    n, m, dx = 1024, 64, 0.0625                    # dx a power of two: exact voxel edges
+    c0 = n - m
+    rho = np.full((n, n, n), 1e-9, np.float32)
+    rho[c0:, c0:, c0:] = 1.0
+    big = W.Phantom((n, n, n), (dx, dx, dx), np.zeros(n ** 3, np.uint8), rho.reshape(-1), [W.WATER])
+    del rho
+    small = W.homogeneous_phantom((m, m, m), (dx, dx, dx), W.WATER, 1.0)
+    spec = W.mono_spectrum(1.0)
+    off = (m // 2 + 0.5) * dx
+    src_big = W.Source(W.PHOTON, spec, "pencil", (c0 * dx + off, c0 * dx + off, c0 * dx), (0.0, 0.0, 1.0))
+    src_small = W.Source(W.PHOTON, spec, "pencil", (off, off, 0.0), (0.0, 0.0, 1.0))
+    res = {}
+    for name, ph, src in (("big", big, src_big), ("small", small, src_small)):
+        prob = problem(ph, src, n=100_000, nb=10, e_max=1.5)
+        eng = G.Engine(prob)
+        try:
+            d, s, st = eng.run()
+            if name == "big":
+                d = d.view(n, n, n)[c0:, c0:, c0:].contiguous()
+                assert bool(torch.isfinite(s).all())
+            res[name] = (d.cpu().numpy().reshape(-1), st)
+        finally:
+            eng.close()
+        del d, s
+        torch.cuda.empty_cache()
+        check_ledger(st, prob.n_histories, LEDGER_TOL)
+    (d_b, st_b), (d_s, st_s) = res["big"], res["small"]
+    for k in ("compton", "el_steps"):
+        assert st_b[k] == pytest.approx(st_s[k], rel=5e-3), k
+    assert abs(signed_bias(d_s, d_b)) <= BIAS_GATE
+    # all of the cube's energy is in the cube: the rest of the big grid holds
+    # only the near-vacuum's share
+    e_cube = float((d_b.astype(np.float64) * 1.0 * dx ** 3).sum())
+    assert e_cube == pytest.approx(st_b["deposited"] / st_b["n_primary"], rel=1e-3)
