@@ -159,7 +159,9 @@ int gdpm_context_destroy(gdpm_ctx *ctx);
 int gdpm_set_param(gdpm_ctx *ctx, int param, double value);
 enum {
     GDPM_PARAM_QUEUE_CAPACITY = 1,   /* particles per queue buffer (0 = automatic), <= 2^31 */
-    GDPM_PARAM_BLOCK_THREADS = 2,    /* 64..256, multiple of 32 (default 256) */
+    GDPM_PARAM_BLOCK_THREADS = 2,    /* threads per block of every transport phase kernel:
+                                        64..256, multiple of 32; 0 (default): each kernel's
+                                        own shape (256; 448 for resumable electron steps) */
     GDPM_PARAM_BLOCKS_PER_SM = 3,    /* persistent CTAs per SM (0 = occupancy) */
     GDPM_PARAM_TALLY_MODE = 4,       /* 0: FP64 atomics; 1: FP32 compensated hi/lo pair */
     GDPM_PARAM_SOURCE_CHUNK = 5,     /* max primaries per transport phase (0 = auto), <= 2^28 */
@@ -337,7 +339,8 @@ typedef struct {
     int candidates_tried;
     double histories_per_s;    /* of the best candidate (wall clock, whole call) */
     int electron_walk;         /* GDPM_PARAM_ELECTRON_WALK: 1 resumable steps, 0 whole steps */
-    int block_threads;         /* GDPM_PARAM_BLOCK_THREADS of the transport kernels */
+    int block_threads;         /* GDPM_PARAM_BLOCK_THREADS of the transport kernels
+                                  (0: each kernel's own shape) */
     uint32_t queue_capacity;   /* GDPM_PARAM_QUEUE_CAPACITY (0: 8 per primary of a phase + 65536) */
     int graph;                 /* GDPM_PARAM_GRAPH: 1 device-driven phase loop */
 } gdpm_tune_result;
@@ -351,7 +354,8 @@ typedef struct {
  * phase or the side-by-side default (8M or more), and 1 / 2 / 4 phase pairs
  * per host check.  Then, one dimension at a time from the best so far
  * (kept only when more than 1 % faster): the other electron phase form
- * (GDPM_PARAM_ELECTRON_WALK), blocks of 128 / 192 / 256 threads, half the
+ * (GDPM_PARAM_ELECTRON_WALK), blocks of 128 / 192 / 256 threads for every
+ * phase kernel instead of each kernel's own shape, half the
  * default queue capacity (4 slots per primary of a phase + 65536; a
  * candidate whose queues overflow is skipped), and for batches side by side
  * the device-driven phase loop (GDPM_PARAM_GRAPH).  The primaries per phase

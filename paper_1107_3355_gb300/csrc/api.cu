@@ -1086,7 +1086,7 @@ int gdpm_set_param(gdpm_ctx* ctx, int param, double v) {
         ctx->queue_capacity = uint32_t(v);
         return GDPM_OK;
     case GDPM_PARAM_BLOCK_THREADS:
-        if (v < 64 || v > 256 || int(v) % 32) return GDPM_E_ARG;
+        if (v != 0 && (v < 64 || v > 256 || int(v) % 32)) return GDPM_E_ARG;
         ctx->block_threads = int(v);
         return GDPM_OK;
     case GDPM_PARAM_BLOCKS_PER_SM:

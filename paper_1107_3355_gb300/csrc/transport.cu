@@ -34,27 +34,41 @@ constexpr float kInf = FLT_MAX;
 constexpr float kEs = 21.2f;            // Rossi-Greisen scattering energy, MeV
 constexpr uint32_t kFull = 0xffffffffu;
 
-// Resident 256-thread CTAs per SM the phase kernels are compiled for: the
-// photon kernel fits 64 registers (4 CTAs); so does the whole-step electron
-// kernel, with a few spilled words, and the extra warps hide more latency
-// than the spills cost (6 MV slab electron phase -4.6 %); the resumable
-// electron kernel keeps its step state across the loop top and runs best
-// with up to 85 registers (3 CTAs; at 4 it spills that state, +12 %).
+// CTA shape each phase kernel is compiled for: threads per CTA and the
+// resident CTAs per SM that fix its register budget.  The photon kernel fits
+// 64 registers at 4 x 256 threads; so does the whole-step electron kernel,
+// with a few spilled words, and the extra warps hide more latency than the
+// spills cost (6 MV slab electron phase -4.6 %).  The resumable electron
+// kernel keeps its step state across the loop top: at 2 x 448 threads (72
+// registers, 24 bytes spilled, 28 warps per SM) it beats 3 x 256 (80
+// registers, no spill, 24 warps) by 2.7 % on the CT plan; at 4 x 256 (64
+// registers) it spills that state, +12 %.
 #ifndef GDPM_MIN_CTAS_PHOTON
 #define GDPM_MIN_CTAS_PHOTON 4
 #endif
 #ifndef GDPM_MIN_CTAS_ELECTRON_WHOLE
 #define GDPM_MIN_CTAS_ELECTRON_WHOLE 4
 #endif
+#ifndef GDPM_THREADS_ELECTRON
+#define GDPM_THREADS_ELECTRON 448
+#endif
 #ifndef GDPM_MIN_CTAS_ELECTRON
-#define GDPM_MIN_CTAS_ELECTRON 3
+#define GDPM_MIN_CTAS_ELECTRON 2
 #endif
 template <int PT>
-struct MinCtas {
-    static constexpr int value = PT == 0 ? GDPM_MIN_CTAS_PHOTON
-                                 : PT == 1 ? GDPM_MIN_CTAS_ELECTRON_WHOLE
-                                           : GDPM_MIN_CTAS_ELECTRON;
+struct PhaseShape {
+    static constexpr int threads = PT == 2 ? GDPM_THREADS_ELECTRON : 256;
+    static constexpr int ctas = PT == 0 ? GDPM_MIN_CTAS_PHOTON
+                                : PT == 1 ? GDPM_MIN_CTAS_ELECTRON_WHOLE
+                                          : GDPM_MIN_CTAS_ELECTRON;
 };
+
+// Threads per CTA of phase kernel PT: its own shape, or the context's
+// GDPM_PARAM_BLOCK_THREADS when set (at most 256, within every kernel's bound).
+int phase_threads(const gdpm_ctx* ctx, int pt) {
+    if (ctx->block_threads > 0) return ctx->block_threads;
+    return pt == 0 ? PhaseShape<0>::threads : pt == 1 ? PhaseShape<1>::threads : PhaseShape<2>::threads;
+}
 
 // ---------------------------------------------------------------- ledger/tally
 struct Acc {
@@ -1128,7 +1142,7 @@ __device__ __forceinline__ void phase_run(const SimParams& P, const PhaseArgs& A
 }
 
 template <int PT>
-__global__ void __launch_bounds__(256, MinCtas<PT>::value)
+__global__ void __launch_bounds__(PhaseShape<PT>::threads, PhaseShape<PT>::ctas)
 k_phase(const SimParams P, const PhaseArgs A) {
     phase_run<PT>(P, A);
 }
@@ -1263,7 +1277,7 @@ __device__ __forceinline__ PhaseArgs phase_args(const LoopArgs& L, uint32_t k) {
 // its own: the host loop's k_phase takes them as kernel parameters, which
 // keeps more registers for the transport loop.)
 template <int PT>
-__global__ void __launch_bounds__(256, MinCtas<PT>::value)
+__global__ void __launch_bounds__(PhaseShape<PT>::threads, PhaseShape<PT>::ctas)
 k_phase_loop(const SimParams P, const LoopArgs L) {
     __shared__ PhaseArgs sA;
     if (threadIdx.x == 0) sA = phase_args(L, *L.k + (PT == 0 ? 0u : 1u));
@@ -1458,35 +1472,36 @@ int launch_phase(gdpm_ctx* ctx, cudaStream_t st, int particle, const SimParams& 
                  const PhaseArgs& A, uint32_t n_items_hint, uint32_t share_eighths) {
     const size_t smem = smem_of(P.T, particle);
     const bool resumable = particle != GDPM_PHOTON && P.walk_resumable;
+    const int thr = phase_threads(ctx, particle == GDPM_PHOTON ? 0 : resumable ? 2 : 1);
     const void* fn = particle == GDPM_PHOTON ? (const void*)k_phase<0>
                      : resumable              ? (const void*)k_phase<2>
                                               : (const void*)k_phase<1>;
     GDPM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int bps = ctx->blocks_per_sm;
     if (bps <= 0) {
-        GDPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, ctx->block_threads, smem));
+        GDPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, thr, smem));
         if (bps < 1) return GDPM_E_ARG;
     }
     uint32_t grid = uint32_t(ctx->sm_count) * uint32_t(bps);
     if (share_eighths < 8) grid = std::max<uint32_t>(uint32_t(ctx->sm_count), grid * share_eighths / 8);
     if (n_items_hint > 0) {
-        const uint32_t need = (n_items_hint + ctx->block_threads - 1) / ctx->block_threads;
+        const uint32_t need = (n_items_hint + thr - 1) / thr;
         grid = need < grid ? need : grid;
     }
     if (grid == 0) grid = 1;
     // queue slots a warp reserves at a time: up to 32, while all warps'
     // spare slots stay below an eighth of the queue; exact below 8
     PhaseArgs B = A;
-    const uint64_t warps = uint64_t(grid) * uint64_t(ctx->block_threads / 32);
+    const uint64_t warps = uint64_t(grid) * uint64_t(thr / 32);
     const uint64_t cap = std::min(A.out_el.capacity, A.out_ph.capacity);
     const uint64_t bb = std::min<uint64_t>(32u, cap / (8u * warps));
     B.bank_block = bb >= 8u ? uint32_t(bb) : 0u;
     if (particle == GDPM_PHOTON)
-        k_phase<0><<<grid, ctx->block_threads, smem, st>>>(P, B);
+        k_phase<0><<<grid, thr, smem, st>>>(P, B);
     else if (resumable)
-        k_phase<2><<<grid, ctx->block_threads, smem, st>>>(P, B);
+        k_phase<2><<<grid, thr, smem, st>>>(P, B);
     else
-        k_phase<1><<<grid, ctx->block_threads, smem, st>>>(P, B);
+        k_phase<1><<<grid, thr, smem, st>>>(P, B);
     GDPM_CUDA_TRY(cudaGetLastError());
     return GDPM_OK;
 }
@@ -1530,17 +1545,19 @@ int build_loop_graph(gdpm_ctx* ctx, const SimParams& P, LoopArgs& L, bool metrop
     const void* fn[2] = {(const void*)k_phase_loop<0>,
                          P.walk_resumable ? (const void*)k_phase_loop<2>
                                           : (const void*)k_phase_loop<1>};
+    const int thr[2] = {phase_threads(ctx, 0), phase_threads(ctx, P.walk_resumable ? 2 : 1)};
+    uint64_t warps = 0;
     for (int t = 0; t < 2; ++t) {
         smem[t] = smem_of(P.T, t == 0 ? GDPM_PHOTON : GDPM_ELECTRON);
         GDPM_CUDA_TRY(cudaFuncSetAttribute(fn[t], cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem[t])));
         int bps = ctx->blocks_per_sm;
         if (bps <= 0) {
-            GDPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn[t], ctx->block_threads, smem[t]));
+            GDPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn[t], thr[t], smem[t]));
             if (bps < 1) return GDPM_E_ARG;
         }
         grid[t] = uint32_t(ctx->sm_count) * uint32_t(bps);
+        warps = std::max<uint64_t>(warps, uint64_t(grid[t]) * uint64_t(thr[t] / 32));
     }
-    const uint64_t warps = uint64_t(std::max(grid[0], grid[1])) * uint64_t(ctx->block_threads / 32);
     const uint64_t cap = std::min(L.qph.capacity, L.qe0.capacity);
     const uint64_t bb = std::min<uint64_t>(32u, cap / (8u * warps));
     L.bank_block = bb >= 8u ? uint32_t(bb) : 0u;
@@ -1593,8 +1610,8 @@ int build_loop_graph(gdpm_ctx* ctx, const SimParams& P, LoopArgs& L, bool metrop
         if (e == cudaSuccess) e = cudaFuncSetAttribute(sf, cudaFuncAttributeMaxDynamicSharedMemorySize, int(src_sm));
         add(sf, dim3(sg), dim3(256), src_sm, src_args_v);
     }
-    add(fn[0], dim3(grid[0]), dim3(ctx->block_threads), smem[0], phase_args_v);
-    add(fn[1], dim3(grid[1]), dim3(ctx->block_threads), smem[1], phase_args_v);
+    add(fn[0], dim3(grid[0]), dim3(thr[0]), smem[0], phase_args_v);
+    add(fn[1], dim3(grid[1]), dim3(thr[1]), smem[1], phase_args_v);
     add((const void*)k_loop_ctl, dim3(1), dim3(1), 0, ctl_args_v);
     cudaGraphExec_t x = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
