@@ -44,19 +44,20 @@ def test_checked_build_exports_the_same_symbols():
     assert set(declared_functions()) <= set(re.findall(r"\bT (gdpm_\w+)", out))
 
 
-def build_c_example(out_dir):
-    """Compile examples/slab_dose.c with plain gcc against the header and
+def build_c_example(out_dir, name="slab_dose"):
+    """Compile examples/<name>.c with plain gcc against the header and
     libgdpm.so: the C ABI needs neither Python nor PyTorch."""
     lib = B.build()
-    exe = os.path.join(str(out_dir), "slab_dose")
+    exe = os.path.join(str(out_dir), name)
     subprocess.check_call(["gcc", "-O2", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
-                           os.path.join(ROOT, "examples", "slab_dose.c"), "-L", os.path.dirname(lib),
-                           "-lgdpm", "-Wl,-rpath," + os.path.dirname(lib), "-o", exe])
+                           os.path.join(ROOT, "examples", name + ".c"), "-L", os.path.dirname(lib),
+                           "-lgdpm", "-lm", "-Wl,-rpath," + os.path.dirname(lib), "-o", exe])
     return exe
 
 
-def test_c_example_compiles_and_links(tmp_path):
-    assert os.access(build_c_example(tmp_path), os.X_OK)
+@pytest.mark.parametrize("name", ["slab_dose", "serve_requests"])
+def test_c_example_compiles_and_links(tmp_path, name):
+    assert os.access(build_c_example(tmp_path, name), os.X_OK)
 
 
 def test_strerror_needs_no_device():

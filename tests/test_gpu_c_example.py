@@ -1,5 +1,7 @@
-"""The C example (examples/slab_dose.c) runs a dose calculation through the
-C ABI alone and reports a balanced energy ledger."""
+"""The C examples run through the C ABI alone: examples/slab_dose.c a dose
+calculation with a balanced energy ledger, examples/serve_requests.c
+several requests served side by side, each finishing with its own balanced
+ledger."""
 import re
 import subprocess
 
@@ -20,3 +22,15 @@ def test_c_example_runs(tmp_path):
     assert abs(bal) < 1e-5
     sig = float(re.search(r"sigma/Dmax (\S+) %", r.stdout).group(1))
     assert 0 < sig < 20
+
+
+def test_c_serving_example_runs(tmp_path):
+    exe = build_c_example(tmp_path, "serve_requests")
+    r = subprocess.run([exe, "8"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    print(r.stdout)
+    rows = [ln.split() for ln in r.stdout.splitlines()[1:] if ln.strip()]
+    assert sorted(int(x[0]) for x in rows) == list(range(8))
+    for x in rows:
+        assert int(x[2]) == (200000 if int(x[0]) % 2 == 0 else 2000000)
+        assert abs(float(x[5])) < 1e-5
