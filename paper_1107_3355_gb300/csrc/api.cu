@@ -47,7 +47,7 @@ void release(Buffer& b) {
 // Histories of one batch allotted to the spectrum intervals by weight:
 // floor, then the remainder one by one to the largest fractional parts
 // (ties to the lower interval) (Sec. 2.3.2).  Writes n_bins+1 prefix counts.
-static void allot_prefix(const std::vector<double>& w, uint64_t nb, uint32_t* prefix) {
+void allot_prefix(const std::vector<double>& w, uint64_t nb, uint32_t* prefix) {
     const int K = int(w.size());
     double ws = 0;
     for (double x : w) ws += x;
@@ -159,29 +159,32 @@ static void prof_collect(Runner& r, gdpm_stats* st) {
     r.prof_kind.clear();
 }
 
-static Queue make_queue(const Buffer& b, uint32_t cap) {
+// A particle queue of `cap` slots laid out from `base`: 13 arrays (Queue).
+Queue queue_view(void* base, uint32_t cap) {
     Queue q{};
-    uint32_t* base = static_cast<uint32_t*>(b.p);
+    uint32_t* w = static_cast<uint32_t*>(base);
     float** fs[7] = {&q.x, &q.y, &q.z, &q.u, &q.v, &q.w, &q.E};
-    for (int k = 0; k < 7; ++k) *fs[k] = reinterpret_cast<float*>(base + size_t(k) * cap);
+    for (int k = 0; k < 7; ++k) *fs[k] = reinterpret_cast<float*>(w + size_t(k) * cap);
     uint32_t** us[6] = {&q.vox, &q.hist, &q.pidlo, &q.pidhi, &q.ctr, &q.flags};
-    for (int k = 0; k < 6; ++k) *us[k] = base + size_t(7 + k) * cap;
+    for (int k = 0; k < 6; ++k) *us[k] = w + size_t(7 + k) * cap;
     q.capacity = cap;
     return q;
 }
-// The source queue: x y z u v w E, ctr, flags (kSourceWords arrays).
-static Queue make_source_queue(const Buffer& b, uint32_t cap) {
+// A phase's source queue from `base`: x y z u v w E, ctr, flags (kSourceWords arrays).
+Queue source_queue_view(void* base, uint32_t cap) {
     Queue q{};
-    uint32_t* base = static_cast<uint32_t*>(b.p);
+    uint32_t* w = static_cast<uint32_t*>(base);
     float** fs[7] = {&q.x, &q.y, &q.z, &q.u, &q.v, &q.w, &q.E};
-    for (int k = 0; k < 7; ++k) *fs[k] = reinterpret_cast<float*>(base + size_t(k) * cap);
-    q.ctr = base + size_t(7) * cap;
-    q.flags = base + size_t(8) * cap;
+    for (int k = 0; k < 7; ++k) *fs[k] = reinterpret_cast<float*>(w + size_t(k) * cap);
+    q.ctr = w + size_t(7) * cap;
+    q.flags = w + size_t(8) * cap;
     q.capacity = cap;
     return q;
 }
+static Queue make_queue(const Buffer& b, uint32_t cap) { return queue_view(b.p, cap); }
+static Queue make_source_queue(const Buffer& b, uint32_t cap) { return source_queue_view(b.p, cap); }
 
-static bool is_device_ptr(const void* p) {
+bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {

@@ -79,64 +79,6 @@ int scratch_address(int device, unsigned char** out) {
     return GDPM_OK;
 }
 
-Queue queue_at(unsigned char* base, uint32_t cap) {
-    Queue q{};
-    uint32_t* w = reinterpret_cast<uint32_t*>(base);
-    float** fs[7] = {&q.x, &q.y, &q.z, &q.u, &q.v, &q.w, &q.E};
-    for (int k = 0; k < 7; ++k) *fs[k] = reinterpret_cast<float*>(w + size_t(k) * cap);
-    uint32_t** us[6] = {&q.vox, &q.hist, &q.pidlo, &q.pidhi, &q.ctr, &q.flags};
-    for (int k = 0; k < 6; ++k) *us[k] = w + size_t(7 + k) * cap;
-    q.capacity = cap;
-    return q;
-}
-// A phase's primaries: x y z u v w E, draw counter, flags.
-Queue source_queue_at(unsigned char* base, uint32_t cap) {
-    Queue q{};
-    float* f = reinterpret_cast<float*>(base);
-    float** fs[7] = {&q.x, &q.y, &q.z, &q.u, &q.v, &q.w, &q.E};
-    for (int k = 0; k < 7; ++k) *fs[k] = f + size_t(k) * cap;
-    q.ctr = reinterpret_cast<uint32_t*>(f + size_t(7) * cap);
-    q.flags = reinterpret_cast<uint32_t*>(f + size_t(8) * cap);
-    q.capacity = cap;
-    return q;
-}
-
-bool on_device(const void* p) {
-    cudaPointerAttributes a{};
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-// Floor plus largest remainder allotment of nb histories to the spectrum
-// intervals (the same rule gdpm_simulate applies).
-void allot(const std::vector<double>& w, uint64_t nb, uint32_t* prefix) {
-    const int K = int(w.size());
-    double ws = 0;
-    for (double x : w) ws += x;
-    std::vector<uint64_t> c(K);
-    std::vector<double> frac(K);
-    uint64_t given = 0;
-    for (int j = 0; j < K; ++j) {
-        const double q = double(nb) * (w[j] / ws);
-        c[j] = uint64_t(std::floor(q));
-        frac[j] = q - std::floor(q);
-        given += c[j];
-    }
-    while (given < nb) {
-        int best = -1;
-        for (int j = 0; j < K; ++j)
-            if (w[j] > 0 && (best < 0 || frac[j] > frac[best])) best = j;
-        ++c[best];
-        frac[best] = -1.0;
-        ++given;
-    }
-    prefix[0] = 0;
-    for (int j = 0; j < K; ++j) prefix[j + 1] = prefix[j] + uint32_t(c[j]);
-}
-
 }  // namespace
 }  // namespace gdpm
 
@@ -160,7 +102,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
         size_t(n_batches) * (n_bins + 1) > kNaMaxPrefix)
         return GDPM_E_ARG;
     if (n_batches < 2 || n_hist < uint64_t(n_batches) || n_hist >= (1ull << 32)) return GDPM_E_ARG;
-    if ((dose_out && !on_device(dose_out)) || (sigma_out && !on_device(sigma_out))) return GDPM_E_ARG;
+    if ((dose_out && !is_device_ptr(dose_out)) || (sigma_out && !is_device_ptr(sigma_out))) return GDPM_E_ARG;
     for (int m = tb->n_mat; m < 256; ++m)
         if (ph->rhomax_host[m] > 0.f) return GDPM_E_ARG;
     double emin = 1e300, emax = 0.0;
@@ -180,9 +122,9 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     double* edep = reinterpret_cast<double*>(base + kOffEdep);
     double* s1 = reinterpret_cast<double*>(base + kOffS1);
     double* s2 = reinterpret_cast<double*>(base + kOffS2);
-    const Queue qph = queue_at(base + kOffQ, kNaQueueCap);
-    const Queue qe[2] = {queue_at(base + kOffQ + kQBytes, kNaQueueCap),
-                         queue_at(base + kOffQ + 2 * kQBytes, kNaQueueCap)};
+    const Queue qph = queue_view(base + kOffQ, kNaQueueCap);
+    const Queue qe[2] = {queue_view(base + kOffQ + kQBytes, kNaQueueCap),
+                         queue_view(base + kOffQ + 2 * kQBytes, kNaQueueCap)};
     uint32_t* ctl = reinterpret_cast<uint32_t*>(base + kOffCtl);
     uint32_t* prefix_d = reinterpret_cast<uint32_t*>(base + kOffPrefix);
     unsigned long long* counters = reinterpret_cast<unsigned long long*>(base + kOffCounters);
@@ -198,7 +140,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     int* al_alias = reinterpret_cast<int*>(base + kOffAlias);
     uint32_t* chains = reinterpret_cast<uint32_t*>(base + kOffChains);
     uint32_t* pick = reinterpret_cast<uint32_t*>(base + kOffPick);
-    const Queue qsrc = source_queue_at(base + kOffSrc, kNaChunk);
+    const Queue qsrc = source_queue_view(base + kOffSrc, kNaChunk);
 
     // source arrays and majorant into the scratch
     std::vector<float> ef(src.edges.begin(), src.edges.end());
@@ -215,7 +157,7 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     std::vector<uint32_t> prefix(size_t(n_batches) * (n_bins + 1));
     for (int b = 0; b < n_batches; ++b) {
         const uint64_t nb = n_hist / n_batches + (uint64_t(b) < n_hist % n_batches ? 1 : 0);
-        allot(src.weights, nb, &prefix[size_t(b) * (n_bins + 1)]);
+        allot_prefix(src.weights, nb, &prefix[size_t(b) * (n_bins + 1)]);
     }
     GDPM_CUDA_TRY(cudaMemcpyAsync(prefix_d, prefix.data(), prefix.size() * 4, cudaMemcpyHostToDevice, s));
 
