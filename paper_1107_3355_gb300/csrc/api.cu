@@ -300,7 +300,9 @@ void beamlet_tables_host(const std::vector<double>& rows17, BeamletHost& out, bo
 }
 
 
-static int source_upload(Runner& r, const gdpm_source_state& s, DevSource& d, bool all_rows = false) {
+// The source's scalar fields (geometry, spectrum size, sampler); its device
+// arrays are left unset.
+void source_fields(const gdpm_source_state& s, DevSource& d) {
     const gdpm_source_desc& g = s.desc;
     d.particle = g.particle;
     d.geometry = g.geometry;
@@ -320,17 +322,23 @@ static int source_upload(Runner& r, const gdpm_source_state& s, DevSource& d, bo
     for (int a = 0; a < 3; ++a) d.direction[a] = dn > 0 ? float(g.direction[a] / dn) : 0.f;
     d.half_u = float(g.half_u);
     d.half_v = float(g.half_v);
-    std::vector<float> e(s.edges.begin(), s.edges.end());
-    int rc = ensure(r.ws.edges, e.size() * 4);
-    if (rc) return rc;
-    GDPM_CUDA_TRY(cudaMemcpyAsync(r.ws.edges.p, e.data(), e.size() * 4, cudaMemcpyHostToDevice, r.stream));
-    d.edges = static_cast<const float*>(r.ws.edges.p);
+    d.edges = nullptr;
     d.beamlets = nullptr;
     d.bl_cdf = nullptr;
     d.bl_row = nullptr;
     d.bl_f = nullptr;
     d.al_cut = nullptr;
     d.al_alias = nullptr;
+}
+
+static int source_upload(Runner& r, const gdpm_source_state& s, DevSource& d, bool all_rows = false) {
+    const gdpm_source_desc& g = s.desc;
+    source_fields(s, d);
+    std::vector<float> e(s.edges.begin(), s.edges.end());
+    int rc = ensure(r.ws.edges, e.size() * 4);
+    if (rc) return rc;
+    GDPM_CUDA_TRY(cudaMemcpyAsync(r.ws.edges.p, e.data(), e.size() * 4, cudaMemcpyHostToDevice, r.stream));
+    d.edges = static_cast<const float*>(r.ws.edges.p);
     BeamletHost bh;
     if (g.geometry == GDPM_GEO_BEAMLETS) beamlet_tables_host(s.beamlets, bh, all_rows);
     if (!bh.f.empty()) {
@@ -386,7 +394,7 @@ int walk_form(const gdpm_ctx* ctx, const gdpm_phantom* ph) {
     return ph->rhomin_host < kAirDensity ? 1 : 0;
 }
 
-static SimParams base_params(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint32_t request_id) {
+SimParams base_params(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_tables* tb, uint32_t request_id) {
     SimParams P{};
     P.nx = ph->nx; P.ny = ph->ny; P.nz = ph->nz;
     P.dx = ph->dx; P.dy = ph->dy; P.dz = ph->dz;

@@ -9,7 +9,6 @@
 // fixed-size array in device memory that exists for as long as the library
 // is loaded; the caller passes the phantom, tables and output arrays.
 #include <algorithm>
-#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -176,25 +175,8 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     GDPM_CUDA_TRY(cudaMemsetAsync(ledger, 0, L_NLEDGER * 8, s));
     GDPM_CUDA_TRY(cudaMemsetAsync(status, 0, 16, s));
 
-    SimParams P{};
-    P.nx = ph->nx; P.ny = ph->ny; P.nz = ph->nz;
-    P.dx = ph->dx; P.dy = ph->dy; P.dz = ph->dz;
-    P.inv_dx = 1.f / ph->dx; P.inv_dy = 1.f / ph->dy; P.inv_dz = 1.f / ph->dz;
-    P.Lx = float(double(ph->nx) * ph->dx);
-    P.Ly = float(double(ph->ny) * ph->dy);
-    P.Lz = float(double(ph->nz) * ph->dz);
-    P.mat = static_cast<const uint8_t*>(ph->mat.p);
-    P.rho = static_cast<const float*>(ph->rho.p);
+    SimParams P = base_params(ctx, ph, tb, ctx->request_id);
     P.maj = maj;
-    P.T = tb->dev;
-    P.key0 = uint32_t(ctx->seed);
-    P.key1 = uint32_t(ctx->seed >> 32) ^ ctx->request_id;
-    P.tally_mode = ctx->tally_mode;
-    P.walk_resumable = walk_form(ctx, ph);
-    P.max_iters = ctx->max_iters;
-    P.tally_lo = 0;
-    P.tally_hi = V;
-    P.n_records = 0;
     P.edep = edep;
     P.edep_hi = reinterpret_cast<float*>(edep);            // FP32 pair mode: hi, then lo
     P.edep_lo = reinterpret_cast<float*>(base + kOffEdep + lo_off);
@@ -204,18 +186,8 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     P.status = status;
     DevSource& S = P.S;
     const gdpm_source_desc& g = src.desc;
-    S.particle = g.particle; S.geometry = g.geometry; S.annihilation = g.annihilation ? 1 : 0;
-    S.n_bins = n_bins; S.n_beamlets = n_bl;
-    const double dn = std::sqrt(g.direction[0] * g.direction[0] + g.direction[1] * g.direction[1] +
-                                g.direction[2] * g.direction[2]);
-    for (int a = 0; a < 3; ++a) {
-        S.origin[a] = float(g.origin[a]);
-        S.direction[a] = float(g.direction[a] / dn);
-        S.center[a] = float(g.center[a]);
-        S.axis_u[a] = float(g.axis_u[a]);
-        S.axis_v[a] = float(g.axis_v[a]);
-    }
-    S.half_u = float(g.half_u); S.half_v = float(g.half_v);
+    source_fields(src, S);
+    S.n_beamlets = n_bl;
     S.edges = edges;
     S.beamlets = n_bl ? bl : nullptr;
     S.bl_cdf = n_bl ? cdf : nullptr;
@@ -223,8 +195,6 @@ extern "C" int gdpm_simulate_noalloc(gdpm_ctx* ctx, gdpm_phantom* ph, gdpm_table
     S.bl_f = n_bl ? bl_f : nullptr;
     S.al_cut = n_bl ? al_cut : nullptr;
     S.al_alias = n_bl ? al_alias : nullptr;
-    S.sampler = g.beamlet_sampler;
-    S.n_chains = uint32_t(g.metropolis_chains);
     int64_t aux = 0;
     if (metro) {
         if ((rc = launch_metropolis_init(s, P, chains))) return rc;

@@ -49,6 +49,41 @@ def test_noalloc_matches_simulate_on_two_calls():
         eng.close()
 
 
+@pytest.mark.parametrize("kind", ["point_field", "beamlets_cdf", "beamlets_metropolis"])
+def test_noalloc_matches_simulate_for_field_and_beamlet_sources(kind):
+    """A point-source field, and a fluence map of 16 beamlets drawn by the
+    cumulative sampler and by the Metropolis chains, through the
+    allocation-free entry: gdpm_simulate's events and dose (its batches run
+    one after another in small phases, gdpm_simulate's side by side)."""
+    if kind == "point_field":
+        prob = W.slab_photon_problem(n_histories=100_000, n_batches=10, shape=(32, 32, 32),
+                                     voxel=(1.0, 1.0, 1.0))
+    else:
+        prob = W.beamlet_matrix_problem(n_beamlets=16, n_batches=10, hist_range=(4000, 8000),
+                                        shape=(32, 32, 32), voxel=(1.0, 1.0, 1.0))
+        if kind == "beamlets_metropolis":
+            prob.source.sampler = "metropolis"
+    eng = G.Engine(prob)
+    try:
+        V = prob.phantom.n_voxels
+        d_ref, s_ref, st_ref = eng.run()
+        d_ref = d_ref.cpu().numpy()
+        s_ref = s_ref.cpu().numpy()
+        d = torch.full((V,), -1.0, dtype=torch.float64, device="cuda")
+        s = torch.full((V,), -1.0, dtype=torch.float64, device="cuda")
+        st = G.gdpm_simulate_noalloc(eng.ctx, eng.phantom, eng.tables, prob.n_histories,
+                                     prob.n_batches, d, s)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(d.cpu().numpy(), d_ref, rtol=1e-9, atol=1e-12 * d_ref.max())
+        np.testing.assert_allclose(s.cpu().numpy(), s_ref, rtol=1e-6, atol=1e-9 * s_ref.max())
+        for k in ("n_primary", "compton", "photoelectric", "el_steps", "moller", "brems",
+                  "el_created", "ph_created", "crossings"):
+            assert st[k] == st_ref[k], k
+        assert st["deposited"] == pytest.approx(st_ref["deposited"], rel=1e-9)
+    finally:
+        eng.close()
+
+
 def test_noalloc_fp32_pair_tally_on_odd_grid():
     """The compensated FP32 tally keeps two float halves in the scratch; on a
     grid with an odd voxel count (31^3) the low half must still be read as
