@@ -513,7 +513,7 @@ int gdpm_debug_beamlets(gdpm_ctx *ctx, uint64_t first, uint64_t n, int32_t *out)
  *
  * All work buffers (batch tally, batch sums, particle queues, counters,
  * source arrays, Woodcock majorant) come from one file-scope device array of
- * GDPM_NOALLOC_SCRATCH_BYTES (about 4.0 MB).  Every GPU that loads this
+ * GDPM_NOALLOC_SCRATCH_BYTES (about 4.1 MB).  Every GPU that loads this
  * library holds that array until the process exits.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) for that
  * device.
